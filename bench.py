@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-voxel rasterizer hot path on one GB300 per rank.
+
+Workload (default ``shell1m``): the ~1M-voxel adaptive octree around a noisy
+sphere shell (levels 4..9, seed 0), one 1280x840 orbit camera per rank, K = 3,
+t_stop = 1e-4.  A step is one pass of the whole path: svr_preprocess,
+svr_bin_sort (no host sync), svr_render_fwd and svr_render_bwd with seeded
+upstream gradients, everything resident in HBM.  The reported value is
+forward+backward steps/s over all ranks; the forward alone (preprocess, sort,
+render) is timed too.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded pixel sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd frames/s & fwd+bwd steps/s, 1M voxels 1280x840; % HBM roofline"
+L2_FLUSH_BYTES = 256 << 20           # > 129 MB L2
+FP32_LANES_PER_SM = 128
+# FP32 operations of the path, per unit of counted work:
+OPS_CAND = 12                         # slab test of one candidate entry
+OPS_HIT = {1: 42, 2: 71, 3: 100}      # one composited segment (forward)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=["shell1m", "dense5"], default="shell1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-pixels", type=int, default=1536)
+    return ap.parse_args()
+
+
+def workload(name, rank):
+    import synth
+    if name == "dense5":
+        scene = synth.dense_scene(5, seed=0)
+        cam = synth.dense_view_camera()
+        return scene, cam, dict(K=1, t_stop=1e-4), "dense level-5 octree, 32768 voxels, 128x128, K=1"
+    scene = synth.shell_scene(seed=0)
+    cam = synth.orbit_camera(100 + rank, 1280, 840)
+    desc = (f"adaptive octree around a noisy sphere shell, {scene.n_vox} voxels (levels 4-9), "
+            "1280x840 orbit camera, K=3, t_stop=1e-4, forward+backward")
+    return scene, cam, dict(K=3, t_stop=1e-4), desc
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on a bounded pixel sample of the same workload."""
+    import oracle
+    import synth
+    if rank != 0:
+        return
+    scene, cam, kw, desc = workload(args.workload, 0)
+    rng = np.random.default_rng(123)
+    n_px = min(256, cam.width * cam.height)
+    px = np.stack([rng.integers(0, cam.width, n_px), rng.integers(0, cam.height, n_px)], 1)
+    g_rgb = rng.normal(size=(n_px, 3))
+    g_d = rng.normal(size=n_px)
+    g_a = rng.normal(size=n_px)
+    threads = os.cpu_count() or 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.render_grad(scene, cam, g_rgb, g_d, g_a, K=kw["K"], t_stop=kw["t_stop"], pixels=px,
+                           threads=threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    frac = n_px / (cam.width * cam.height)
+    per_step = float(np.mean(times)) / frac
+    value = 1.0 / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n_px} random pixels per step (forward+analytic backward), "
+                                       "scaled to the full frame"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- native
+
+def cpu_baseline(args, scene, cam, kw):
+    """The oracle as it stands, on a bounded pixel sample (forward + backward)."""
+    import oracle
+    rng = np.random.default_rng(7)
+    n_px = min(args.cpu_pixels, cam.width * cam.height)
+    px = np.stack([rng.integers(0, cam.width, n_px), rng.integers(0, cam.height, n_px)], 1)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.render_grad(scene, cam, rng.normal(size=(n_px, 3)), rng.normal(size=n_px),
+                       rng.normal(size=n_px), K=kw["K"], t_stop=kw["t_stop"], pixels=px, threads=threads)
+    dt = time.perf_counter() - t0
+    frac = n_px / (cam.width * cam.height)
+    return {"value": frac / dt, "unit": "steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_px} random pixels, forward + analytic backward ({dt:.1f} s), scaled to the full frame"}
+
+
+def run_native(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_2412_04459_gb300 import DeviceScene, Frame
+    from paper_2412_04459_gb300 import build as gbuild
+
+    gbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scene, cam, kw, desc = workload(args.workload, rank)
+    dscene = DeviceScene.from_host(scene, device=dev)
+    K, t_stop = kw["K"], kw["t_stop"]
+    fr = Frame(dscene, cam, K=K, t_stop=t_stop)
+    fr.render()                               # sizes the workspace (host sync once)
+    P = fr.n_pairs
+    fr.pair_capacity = max(fr.pair_capacity, int(P * 1.1) + 1024)
+    fr.render()
+    H, W = cam.height, cam.width
+    g_rgb, g_depth, g_alpha = (torch.as_tensor(a, device=dev) for a in synth.upstream_grads(1, H, W))
+    d_grid = torch.zeros(scene.n_pts, device=dev)
+    d_sh = torch.empty(scene.n_vox, 48, device=dev)
+    out = fr.forward()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # work counts of the forward (candidates examined, hits) for the roofline
+    st = fr.forward_stats()
+    counts = st["counts"].to(torch.int64).sum(dim=(0, 1)).cpu().numpy()
+    n_cand, n_hit = int(counts[0]), int(counts[1])
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    calls = ("preprocess", "bin_sort", "render_fwd", "render_bwd")
+
+    def step(rec=None):
+        e = [ev() for _ in range(5)] if rec is not None else None
+        if e: e[0].record(stream)
+        fr.preprocess()
+        if e: e[1].record(stream)
+        fr.bin_sort(sync=False)
+        if e: e[2].record(stream)
+        fr.forward(out)
+        if e: e[3].record(stream)
+        d_grid.zero_()
+        fr.backward(g_rgb, g_depth, g_alpha, out, d_grid, d_sh)
+        if e: e[4].record(stream)
+        if rec is not None:
+            rec.append(e)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    recs = []
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # L2 flush between timed steps (outside the events)
+        step(recs)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    per_call = {c: float(np.mean([r[i].elapsed_time(r[i + 1]) for r in recs])) for i, c in enumerate(calls)}
+    ms_step = float(np.mean([r[0].elapsed_time(r[4]) for r in recs]))
+    ms_fwd = float(np.mean([r[0].elapsed_time(r[3]) for r in recs]))
+    # the bwd call also zeroes d_grid (a torch fill) before its kernels; its event
+    # pair brackets both, so report the kernels' share from the launch list.
+    t = torch.tensor([ms_step, ms_fwd], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step, ms_fwd = float(t[0]), float(t[1])
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, scene, cam, kw, dev, world)
+
+    if rank != 0:
+        return
+    value = world * 1000.0 / ms_step
+    fwd_fps = world * 1000.0 / ms_fwd
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm = props.multi_processor_count
+    sm_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
+    alu_peak = sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12          # T FP32 lane-ops/s
+    ops = n_cand * OPS_CAND + n_hit * OPS_HIT[K]
+    achieved = ops / (per_call["render_fwd"] * 1e-3) / 1e12
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    frame_bytes = frame_algorithmic_bytes(scene, P, H, W)
+    n_launch = launches_per_step(fr)
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "voxels": scene.n_vox, "pairs": P, "image": f"{W}x{H}", "K": K,
+                   "l2": "flushed between steps (256 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{world} (one view per rank)"},
+        "fwd_frames_per_s": fwd_fps, "ms_fwd": ms_fwd, "ms_per_call": per_call,
+        "roofline": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": alu_peak,
+                     "unit": "T FP32 lane-ops/s", "frac": achieved / alu_peak, "traffic": None,
+                     "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
+                              "ops_per_hit": OPS_HIT[K]},
+                     "peak_from": f"{sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
+        "frame_hbm": {"algorithmic_bytes": frame_bytes, "achieved_gbs": frame_bytes / (ms_step * 1e-3) / 1e9,
+                      "peak_gbs": hbm, "frac": frame_bytes / (ms_step * 1e-3) / 1e9 / hbm,
+                      "peak_from": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"},
+        "gpu_launches": n_launch * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(args, scene, cam, kw)
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, scene, cam, kw, dev, world):
+    """Same step through the public API, inputs copied from pinned host memory
+    every step and the images and gradients read back."""
+    import torch
+    import synth
+    from paper_2412_04459_gb300 import DeviceScene, Frame
+    host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in (
+        ("centre", scene.centre), ("level", scene.level), ("corner_idx", scene.corner_idx),
+        ("grid", scene.grid), ("sh", scene.sh))}
+    g = [torch.as_tensor(a).pin_memory() for a in synth.upstream_grads(1, cam.height, cam.width)]
+    dsc = DeviceScene.from_host(scene, device=dev)
+    fr = Frame(dsc, cam, K=kw["K"], t_stop=kw["t_stop"])
+    fr.render()
+    fr.pair_capacity = int(fr.n_pairs * 1.1) + 1024
+    H, W = cam.height, cam.width
+    out_host = {"rgb": torch.empty(3, H, W).pin_memory(), "d_grid": torch.empty(scene.n_pts).pin_memory(),
+                "d_sh": torch.empty(scene.n_vox, 48).pin_memory()}
+    gd = [torch.empty_like(x, device=dev) for x in g]
+    d_grid = torch.zeros(scene.n_pts, device=dev)
+    d_sh = torch.empty(scene.n_vox, 48, device=dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(x.numel() * x.element_size() for x in g)
+    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for k, v in host.items():
+            getattr(dsc, k).copy_(v, non_blocking=True)
+        for a, b in zip(gd, g):
+            a.copy_(b, non_blocking=True)
+        out = fr.render(sync=False)
+        d_grid.zero_()
+        fr.backward(gd[0], gd[1], gd[2], out, d_grid, d_sh)
+        out_host["rgb"].copy_(out["rgb"], non_blocking=True)
+        out_host["d_grid"].copy_(d_grid, non_blocking=True)
+        out_host["d_sh"].copy_(d_sh, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(args.steps):
+        step()
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / args.steps
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t[0])
+    return {"value": world * 1000.0 / ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+
+
+def frame_algorithmic_bytes(scene, P, H, W):
+    """Minimal HBM bytes of one forward+backward step (FP32 storage): scene
+    read once, pairs written/sorted/read once, images written and read, the
+    gradients written."""
+    N = scene.n_vox
+    pre = N * (12 + 1 + 32 + 32 + 192) + N * 64          # inputs + per-voxel record
+    pairs = P * 12 * 2 + P * 12                          # emit, one sort read+write, render read
+    img = H * W * (12 + 4 + 4 + 4 + 4)                   # rgb, depth, alpha, T_final, last
+    bwd = H * W * (12 + 4 + 4 + 4 + 4) + P * 12 + N * (64 + 192) + scene.n_pts * 4 * 2
+    return int(pre + pairs + img + bwd)
+
+
+def launches_per_step(fr):
+    """Kernels of ours launched per step (fills/memsets excluded)."""
+    nt = fr.frame.n_tiles_x * fr.frame.n_tiles_y
+    tb = max(0, int(np.ceil(np.log2(nt)))) if nt > 1 else 0
+    lmax = fr.scene.max_level
+    lo = 48 - 3 * (lmax + 1 if lmax < 16 else 16)
+    passes = (48 + tb - lo + 7) // 8 + (1 if lmax == 16 else 0)
+    return 2 + 4 + 3 * passes + 1 + 1 + 2
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_native(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

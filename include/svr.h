@@ -1,0 +1,238 @@
+/*
+ * svr.h - C ABI of the sparse-voxel rasterizer for one GB300 (sm_103a).
+ *
+ * Hot path of SVRaster (Sun et al., "Sparse Voxels Rasterization: Real-time
+ * High-fidelity Radiance Field Rendering", arXiv 2412.04459):
+ *
+ *   svr_preprocess  per view: ray sign masks of the 16x16 tiles and, per
+ *                   voxel, its Morton code, its tile rectangle, its colour
+ *                   and its 8 corner densities (Sec. 3.1.2 "Projection to
+ *                   image space", "Pre-processing voxels"; Sec. A.1, Sec. B.1)
+ *   svr_bin_sort    one (key, value) pair per (voxel, tile, ray sign
+ *                   pattern), sorted by (tile, direction-dependent Morton
+ *                   order), and the range of each tile (Sec. 3.1.2 "Sorting
+ *                   voxels"; Sec. B.1, Sec. B.2)
+ *   svr_render_fwd  per pixel front-to-back compositing of its tile's list
+ *                   (Eq. alpha_blend, Eq. vox_alpha, Eq. vox_color, Sec. A.2,
+ *                   Sec. A.4; early termination, Sec. 3.1.2)
+ *   svr_render_bwd  gradients of the three images with respect to the grid
+ *                   point densities and the SH coefficients (Sec. A.2, A.4)
+ *
+ * Conventions shared by every call
+ *   - Array arguments are DEVICE pointers owned by the caller, row-major and
+ *     contiguous, valid until the last call that uses them has finished on
+ *     the stream.  The library allocates no device or pinned memory: all
+ *     scratch lives in the caller's workspace (svr_workspace_size bytes,
+ *     256-byte aligned).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *     enqueue work, except where a description says it synchronises.
+ *   - Return value: SVR_OK or an SVR_ERR_* code; svr_last_error() gives a
+ *     message for the calling thread.  Argument errors are found on the host
+ *     before anything is enqueued.  Errors found by kernels (an invalid
+ *     voxel, too many pairs) are recorded in the workspace and reported by
+ *     svr_frame_status(), or by svr_bin_sort() when it is asked for the
+ *     pair count.
+ *   - Camera: OpenCV pinhole.  Camera point X = R p + t with w2c = [R | t]
+ *     row-major; pixel (x, y) has its centre at (x + 0.5, y + 0.5); the ray
+ *     of a pixel is r_o + t r_d with r_o = -R^T t and r_d = R^T ((x + .5 -
+ *     cx) / fx, (y + .5 - cy) / fy, 1), so ray distances are camera depths.
+ *   - Voxel (Eq. vox_coord): level l in [1, 16], size v_s = w_s 2^-l, centre
+ *     on the lattice w_c - w_s/2 + v_s (ijk + 1/2) (read as the cell centre).
+ *     Corner j of a voxel has offsets (j>>2 &1, j>>1 &1, j &1) in (x, y, z),
+ *     the V_000 ... V_111 order of Eq. interp.  Grid point values are raw
+ *     densities; explin is applied after trilinear interpolation.
+ *   - SH: degree 3, sh[v][n][c] (16 coefficients x RGB, coefficient-major),
+ *     real orthonormal basis without the Condon-Shortley phase, index n =
+ *     l*l + l + m; colour = max(0, sum_n Y_n(d) sh[v][n][c]) with d =
+ *     normalize(centre - r_o) (Eq. vox_color).
+ */
+#ifndef SVR_H_
+#define SVR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SVR_API __attribute__((visibility("default")))
+#else
+#define SVR_API
+#endif
+
+#define SVR_OK 0
+#define SVR_ERR_INVALID 1  /* bad argument, or a voxel off its lattice / level outside [1, max_level] */
+#define SVR_ERR_LIMIT 2    /* more than 2^29 voxels or 2^16 tiles (the key layout of Sec. B.1) */
+#define SVR_ERR_CAPACITY 3 /* more pairs than the workspace holds; the true count is reported */
+#define SVR_ERR_CUDA 4     /* a CUDA runtime call failed */
+#define SVR_ERR_TIMEOUT 5  /* a bounded device wait gave up */
+
+/* Device-side error flags (svr_frame_status). */
+#define SVR_FLAG_INVALID_VOXEL 1u
+#define SVR_FLAG_CAPACITY 2u
+
+typedef struct svr_camera {
+    float fx, fy, cx, cy;
+    float w2c[12]; /* row-major [R | t] */
+    int32_t width, height;
+} svr_camera;
+
+typedef struct svr_params {
+    int32_t K;      /* samples per ray segment, 1..3 (Eq. K_samp_pts) */
+    float t_stop;   /* stop compositing once T < t_stop (Sec. 3.1.2; 1e-4 in the paper) */
+    int32_t tile;   /* tile edge in pixels; 16 (Sec. B.1) */
+    float bg[3];    /* background colour added as T_final * bg */
+} svr_params;
+
+typedef struct svr_scene {
+    float world_center[3]; /* w_c */
+    float world_size;      /* w_s */
+    int64_t n_vox;         /* N, at most 2^29 */
+    int64_t n_pts;         /* number of grid points */
+    int32_t max_level;     /* upper bound on level[], 1..16; sets the sorted key width */
+    int32_t reserved;
+    const float *centre;       /* [N][3] */
+    const uint8_t *level;      /* [N] */
+    const int32_t *corner_idx; /* [N][8], indices into grid */
+    const float *grid;         /* [n_pts] raw densities */
+    const float *sh;           /* [N][48], 16-byte aligned */
+} svr_scene;
+
+/*
+ * Per-view state, in HOST memory owned by the caller.  svr_preprocess fills
+ * it; svr_bin_sort, svr_render_fwd and svr_render_bwd read it (svr_bin_sort
+ * also updates it).  It points into the workspace and at the scene arrays,
+ * which must stay alive while it is used.  Treat the fields as read-only.
+ */
+typedef struct svr_frame {
+    svr_scene scene;
+    svr_camera cam;
+    svr_params params;
+    void *ws;
+    size_t ws_bytes;
+    int64_t pair_capacity;
+    int64_t n_pairs;    /* pair count, or -1 while it is known only on the device */
+    int32_t n_tiles_x, n_tiles_y;
+    int32_t stage;      /* 1 after svr_preprocess, 2 after svr_bin_sort */
+    int32_t sorted_alt; /* internal: which key buffer holds the sorted pairs */
+    double ray_origin[3];
+    uint64_t offsets[24]; /* internal: byte offsets of the workspace buffers */
+} svr_frame;
+
+/* Device views of the internal buffers of a frame, for inspection. */
+typedef struct svr_buffers {
+    const void *status;       /* uint32[16]: flags, n_pairs (low, high), ... */
+    const uint8_t *tile_mask; /* [n_tiles] bit s set if a pixel of the tile has ray sign bits s */
+    const uint64_t *octpath;  /* [N] Morton code (Sec. A.1) */
+    const int16_t *rect;      /* [N][4] tx0, tx1, ty0, ty1 (empty: tx0 > tx1) */
+    const uint32_t *count;    /* [N] pairs emitted per voxel */
+    const uint32_t *offset;   /* [N] exclusive scan of count */
+    const float *record;      /* [N][16] per-voxel record of the view */
+    const uint64_t *keys;     /* [pair_capacity] sorted keys: tile << 48 | Morton order */
+    const uint32_t *values;   /* [pair_capacity] sorted values: s << 29 | voxel id */
+    const uint32_t *ranges;   /* [n_tiles][2] begin, end of each tile's list */
+} svr_buffers;
+
+/* Workspace bytes needed for n_vox voxels, pair_capacity pairs and this
+ * camera / tile size; 0 if the arguments are invalid.  Host only. */
+SVR_API size_t svr_workspace_size(int64_t n_vox, int64_t pair_capacity,
+                                  const svr_camera *cam, const svr_params *params);
+
+/*
+ * Per-view preprocessing (Sec. 3.1.2 "Projection to image space" and
+ * "Pre-processing voxels").  Enqueues:
+ *   - per tile, the 8-bit mask of ray sign patterns 4(rd.x<0) + 2(rd.y<0) +
+ *     (rd.z<0) of its in-image pixels (Sec. B.2 listing, Sec. B.1);
+ *   - per voxel: lattice index and Morton code (Sec. A.1); the tile
+ *     rectangle of the 2-D bounding box of its 8 projected corners (all
+ *     corners at camera depth <= 1e-3: culled; some: whole image); the pair
+ *     count = sum over the rectangle's tiles of the number of sign patterns
+ *     in the tile mask; its colour (Eq. vox_color) and its 8 gathered corner
+ *     densities.
+ * Fills *frame.  pair_capacity: pairs the workspace was sized for.
+ * Errors: SVR_ERR_INVALID (null pointer, K not in 1..3, tile != 16, bad
+ * camera, misaligned sh or workspace, workspace too small, max_level outside
+ * 1..16), SVR_ERR_LIMIT (N > 2^29, more than 2^16 tiles), SVR_ERR_CUDA.
+ */
+SVR_API int svr_preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cam,
+                           const svr_params *params, void *ws, size_t ws_bytes,
+                           int64_t pair_capacity, void *stream);
+
+/*
+ * Pair emission and sort (Sec. B.1).  Enqueues: the exclusive scan of the
+ * per-voxel counts; one pair per (voxel, tile of its rectangle, sign pattern
+ * s of that tile), key = tile << 48 | (octpath XOR s replicated in all 16
+ * triples) (the direction-dependent Morton order of Sec. B.2), value = s << 29
+ * | voxel id; a stable LSD radix sort over the key bits that can differ
+ * (tile bits and the top 3 (max_level + 1) Morton bits; with max_level = 16
+ * first the value's sign bits), which orders the pairs by (key, value); the
+ * [begin, end) range of every tile.
+ * n_pairs_out: if not NULL, the call synchronises the stream, stores the
+ * true pair count there, and returns SVR_ERR_CAPACITY if it exceeds the
+ * capacity (pairs beyond it were dropped; re-run with a larger workspace) or
+ * SVR_ERR_INVALID if a voxel failed its lattice or level check.  If NULL the
+ * call only enqueues work (CUDA-graph capturable) and such errors are left
+ * for svr_frame_status().
+ */
+SVR_API int svr_bin_sort(svr_frame *frame, int64_t *n_pairs_out, void *stream);
+
+/*
+ * Forward render (Sec. 3.1.2 "Rendering pixels").  Per pixel, its tile's
+ * sorted list is walked front to back; entries with other sign bits are
+ * skipped (Sec. B.1); for a valid ray-AABB segment [a, b] (Sec. A.2) the
+ * voxel alpha uses K samples t_k = a + (k - 1/2)(b - a)/K, trilinear raw
+ * density, explin, alpha = 1 - exp(-(l/K) sum_k explin(v_k)), l = (b - a)|r_d|
+ * (Eq. supp_alpha_comp); the voxel depth is sum_k prod_{j<k}(1 - a_j) a_k t_k
+ * (Sec. A.4); C += T alpha c, D += T d, T *= 1 - alpha; the walk stops after
+ * the voxel that leaves T < t_stop.
+ * Outputs (device, caller-owned): rgb [3][H][W] = C + T_final bg, depth
+ * [H][W], alpha [H][W] = 1 - T_final, T_final [H][W], last [H][W] = index in
+ * the sorted pair list of the voxel that stopped the walk, else the tile's
+ * last entry (-1 for an empty tile).  T_final and last are what
+ * svr_render_bwd needs.  Requires svr_bin_sort first.
+ */
+SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, float *alpha,
+                           float *T_final, int32_t *last, void *stream);
+
+/*
+ * Backward render (Sec. A.2 alpha gradient, Sec. A.4 depth gradients).
+ * Inputs: dL/drgb [3][H][W], dL/ddepth [H][W], dL/dalpha [H][W] (any may be
+ * NULL = zero) and the T_final, last of svr_render_fwd.  Each pixel walks its
+ * list back to front from `last`, recovering T before each voxel as T after
+ * it divided by (1 - alpha); pixels with T_final < 1e-30 redo the walk front
+ * to back instead.  Adds dL/dgrid into d_grid [n_pts] (accumulated: the
+ * caller zeroes it) and writes dL/dsh into d_sh [N][48] (zero for voxels not
+ * in view).  Requires svr_render_fwd's outputs for the same frame.
+ */
+SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const float *d_depth,
+                           const float *d_alpha, const float *T_final, const int32_t *last,
+                           float *d_grid, float *d_sh, void *stream);
+
+/* svr_render_fwd that also writes, per pixel, counts[y][x] = (list entries
+ * with the pixel's sign bits that it examined, hits it composited): the
+ * work the forward did, for throughput accounting.  counts: device int32
+ * [H][W][2], 8-byte aligned.  Slower than svr_render_fwd; same images. */
+SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, float *alpha,
+                             float *T_final, int32_t *last, int32_t *counts, void *stream);
+
+/* Synchronises the stream and reads the device-side error flags
+ * (SVR_FLAG_*) and the pair count of a frame.  Either output may be NULL. */
+SVR_API int svr_frame_status(const svr_frame *frame, uint32_t *flags, int64_t *n_pairs,
+                             void *stream);
+
+/* Device pointers of a frame's internal buffers (valid while the frame is). */
+SVR_API int svr_frame_buffers(const svr_frame *frame, svr_buffers *out);
+
+/* Message of the last error on the calling thread ("" if none). */
+SVR_API const char *svr_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+SVR_API int svr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVR_H_ */

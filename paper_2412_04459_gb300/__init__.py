@@ -1,0 +1,13 @@
+"""GB300-native (sm_103a) hot path of SVRaster (arXiv 2412.04459): sparse-voxel
+rasterization forward and backward behind the C ABI of include/svr.h.
+
+The package holds the CUDA sources (csrc/), their in-tree build (build.py ->
+libsvr.so), the ctypes binding (_native.py) and the PyTorch front end
+(raster.py).  Importing it does not build or load the library; the first call
+that needs it loads libsvr.so and fails loudly if it is missing.
+"""
+from .raster import (DeviceScene, Frame, SVRasterFn, camera_struct, params_struct,  # noqa: F401
+                     rasterize, workspace_size)
+
+__all__ = ["DeviceScene", "Frame", "SVRasterFn", "rasterize", "camera_struct", "params_struct",
+           "workspace_size"]

@@ -1,0 +1,322 @@
+// C ABI of the sparse-voxel rasterizer: argument checks, workspace layout and
+// launch sequencing.  See include/svr.h for the contract of every call.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "svr_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(SVR_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+enum Slot {
+    kStatus, kTileMask, kOctpath, kRect, kCount, kOffset, kRecord, kScanBlocks,
+    kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kTotal, kNumSlots
+};
+
+struct Layout {
+    size_t off[kNumSlots];
+};
+
+Layout make_layout(int64_t n_vox, int64_t cap, int64_t ntiles) {
+    Layout L;
+    size_t o = 0;
+    auto take = [&](Slot s, size_t bytes) {
+        L.off[s] = o;
+        o = align256(o + bytes);
+    };
+    const size_t N = (size_t)n_vox, C = (size_t)cap;
+    take(kStatus, sizeof(svr::Status));
+    take(kTileMask, (size_t)ntiles);
+    take(kOctpath, 8 * N);
+    take(kRect, 8 * N);
+    take(kCount, 4 * N);
+    take(kOffset, 4 * N);
+    take(kRecord, sizeof(svr::Record) * N);
+    take(kScanBlocks, 4 * ((N + svr::kScanTile - 1) / svr::kScanTile + 1));
+    take(kKeys0, 8 * C);
+    take(kKeys1, 8 * C);
+    take(kVals0, 4 * C);
+    take(kVals1, 4 * C);
+    take(kHist, 4 * 256 * ((C + svr::kRadixTile - 1) / svr::kRadixTile + 1));
+    take(kDigitTot, 4 * 256);
+    take(kRanges, 8 * (size_t)ntiles);
+    take(kDcol, 12 * N);
+    L.off[kTotal] = o;
+    return L;
+}
+
+int check_camera(const svr_camera *cam, const svr_params *p, int64_t *ntiles, int *ntx, int *nty) {
+    if (!cam || !p) return fail(SVR_ERR_INVALID, "null camera or params");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 65536 || cam->height > 65536)
+        return fail(SVR_ERR_INVALID, "image size %d x %d", cam->width, cam->height);
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+        return fail(SVR_ERR_INVALID, "bad intrinsics");
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(cam->w2c[i])) return fail(SVR_ERR_INVALID, "non-finite w2c");
+    if (p->tile != 16) return fail(SVR_ERR_INVALID, "tile %d (16 supported)", p->tile);
+    if (p->K < 1 || p->K > 3) return fail(SVR_ERR_INVALID, "K = %d (1..3 supported)", p->K);
+    if (!(p->t_stop >= 0.f) || !(p->t_stop < 1.f)) return fail(SVR_ERR_INVALID, "t_stop %g", p->t_stop);
+    *ntx = (cam->width + p->tile - 1) / p->tile;
+    *nty = (cam->height + p->tile - 1) / p->tile;
+    *ntiles = (int64_t)(*ntx) * (*nty);
+    if (*ntiles > 65536) return fail(SVR_ERR_LIMIT, "%lld tiles > 2^16", (long long)*ntiles);
+    return SVR_OK;
+}
+
+svr::FrameDev frame_dev(const svr_frame *f) {
+    svr::FrameDev d;
+    memset(&d, 0, sizeof(d));
+    const svr_camera &c = f->cam;
+    d.cam.fx = c.fx;
+    d.cam.fy = c.fy;
+    d.cam.cx = c.cx;
+    d.cam.cy = c.cy;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) d.cam.R[3 * i + j] = c.w2c[4 * i + j];
+    for (int i = 0; i < 3; ++i) d.cam.t[i] = c.w2c[4 * i + 3];
+    for (int i = 0; i < 3; ++i) d.cam.ro[i] = (float)f->ray_origin[i];
+    d.cam.W = c.width;
+    d.cam.H = c.height;
+    d.cam.ntx = f->n_tiles_x;
+    d.cam.nty = f->n_tiles_y;
+    d.cam.tile = f->params.tile;
+    char *ws = (char *)f->ws;
+    const uint64_t *o = f->offsets;
+    d.status = (svr::Status *)(ws + o[kStatus]);
+    d.tile_mask = (uint8_t *)(ws + o[kTileMask]);
+    d.octpath = (uint64_t *)(ws + o[kOctpath]);
+    d.rect = (short4 *)(ws + o[kRect]);
+    d.count = (uint32_t *)(ws + o[kCount]);
+    d.offset = (uint32_t *)(ws + o[kOffset]);
+    d.rec = (svr::Record *)(ws + o[kRecord]);
+    d.scan_blocks = (uint32_t *)(ws + o[kScanBlocks]);
+    d.keys[0] = (uint64_t *)(ws + o[kKeys0]);
+    d.keys[1] = (uint64_t *)(ws + o[kKeys1]);
+    d.vals[0] = (uint32_t *)(ws + o[kVals0]);
+    d.vals[1] = (uint32_t *)(ws + o[kVals1]);
+    d.hist = (uint32_t *)(ws + o[kHist]);
+    d.digit_tot = (uint32_t *)(ws + o[kDigitTot]);
+    d.ranges = (uint2 *)(ws + o[kRanges]);
+    d.dcol = (float *)(ws + o[kDcol]);
+    d.n_vox = f->scene.n_vox;
+    d.n_pts = f->scene.n_pts;
+    d.capacity = f->pair_capacity;
+    d.world_size = f->scene.world_size;
+    for (int i = 0; i < 3; ++i) d.world_min[i] = f->scene.world_center[i] - 0.5f * f->scene.world_size;
+    d.max_level = f->scene.max_level;
+    d.K = f->params.K;
+    d.t_stop = f->params.t_stop;
+    for (int i = 0; i < 3; ++i) d.bg[i] = f->params.bg[i];
+    d.centre = f->scene.centre;
+    d.level = f->scene.level;
+    d.corner_idx = f->scene.corner_idx;
+    d.grid = f->scene.grid;
+    d.sh = f->scene.sh;
+    return d;
+}
+
+int tile_bits(int64_t ntiles) {
+    int b = 0;
+    while (((int64_t)1 << b) < ntiles) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+SVR_API const char *svr_last_error(void) { return g_err; }
+
+SVR_API int svr_version(void) { return 100; }
+
+SVR_API size_t svr_workspace_size(int64_t n_vox, int64_t pair_capacity, const svr_camera *cam,
+                                  const svr_params *params) {
+    int64_t ntiles;
+    int ntx, nty;
+    if (n_vox < 0 || n_vox > ((int64_t)1 << 29)) return 0;
+    if (pair_capacity < 0 || pair_capacity > INT32_MAX) return 0;
+    if (check_camera(cam, params, &ntiles, &ntx, &nty) != SVR_OK) return 0;
+    return make_layout(n_vox, pair_capacity, ntiles).off[kTotal];
+}
+
+SVR_API int svr_preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cam,
+                           const svr_params *params, void *ws, size_t ws_bytes, int64_t pair_capacity,
+                           void *stream) {
+    g_err[0] = 0;
+    if (!frame || !scene) return fail(SVR_ERR_INVALID, "null frame or scene");
+    int64_t ntiles;
+    int ntx, nty;
+    int rc = check_camera(cam, params, &ntiles, &ntx, &nty);
+    if (rc != SVR_OK) return rc;
+    const int64_t N = scene->n_vox;
+    if (N < 0) return fail(SVR_ERR_INVALID, "n_vox %lld", (long long)N);
+    if (N > ((int64_t)1 << 29)) return fail(SVR_ERR_LIMIT, "n_vox %lld > 2^29", (long long)N);
+    if (scene->max_level < 1 || scene->max_level > 16)
+        return fail(SVR_ERR_INVALID, "max_level %d", scene->max_level);
+    if (!(scene->world_size > 0.f) || !std::isfinite(scene->world_size))
+        return fail(SVR_ERR_INVALID, "world_size %g", scene->world_size);
+    if (N > 0 && (!scene->centre || !scene->level || !scene->corner_idx || !scene->sh ||
+                  (!scene->grid && scene->n_pts > 0)))
+        return fail(SVR_ERR_INVALID, "null scene array");
+    if (N > 0 && (((uintptr_t)scene->sh) & 15u)) return fail(SVR_ERR_INVALID, "sh not 16-byte aligned");
+    if (N > 0 && (((uintptr_t)scene->corner_idx) & 15u))
+        return fail(SVR_ERR_INVALID, "corner_idx not 16-byte aligned");
+    if (pair_capacity < 0 || pair_capacity > INT32_MAX)
+        return fail(SVR_ERR_INVALID, "pair_capacity %lld", (long long)pair_capacity);
+    if (!ws || (((uintptr_t)ws) & 255u)) return fail(SVR_ERR_INVALID, "workspace null or not 256-byte aligned");
+    const Layout L = make_layout(N, pair_capacity, ntiles);
+    if (ws_bytes < L.off[kTotal])
+        return fail(SVR_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, (size_t)L.off[kTotal]);
+
+    memset(frame, 0, sizeof(*frame));
+    frame->scene = *scene;
+    frame->cam = *cam;
+    frame->params = *params;
+    frame->ws = ws;
+    frame->ws_bytes = ws_bytes;
+    frame->pair_capacity = pair_capacity;
+    frame->n_pairs = -1;
+    frame->n_tiles_x = ntx;
+    frame->n_tiles_y = nty;
+    for (int i = 0; i < kNumSlots; ++i) frame->offsets[i] = L.off[i];
+    for (int i = 0; i < 3; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < 3; ++j) r -= (double)cam->w2c[4 * j + i] * (double)cam->w2c[4 * j + 3];
+        frame->ray_origin[i] = r;
+    }
+    const svr::FrameDev d = frame_dev(frame);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(svr::Status), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&d.status->bad_voxel, 0xFF, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "status reset");
+    e = svr::launch_tile_mask(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tile mask");
+    e = svr::launch_preprocess(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "preprocess");
+    frame->stage = 1;
+    return SVR_OK;
+}
+
+SVR_API int svr_frame_status(const svr_frame *frame, uint32_t *flags, int64_t *n_pairs, void *stream) {
+    if (!frame || frame->stage < 1) return fail(SVR_ERR_INVALID, "frame not preprocessed");
+    svr::Status st;
+    const svr::FrameDev d = frame_dev(frame);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&st, d.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (flags) *flags = st.flags;
+    if (n_pairs) *n_pairs = (int64_t)(((uint64_t)st.n_pairs_hi << 32) | st.n_pairs_lo);
+    return SVR_OK;
+}
+
+SVR_API int svr_bin_sort(svr_frame *frame, int64_t *n_pairs_out, void *stream) {
+    g_err[0] = 0;
+    if (!frame || frame->stage < 1) return fail(SVR_ERR_INVALID, "frame not preprocessed");
+    const svr::FrameDev d = frame_dev(frame);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = svr::launch_scan_emit(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scan/emit");
+    const int64_t ntiles = (int64_t)frame->n_tiles_x * frame->n_tiles_y;
+    const int lmax = frame->scene.max_level;
+    const int lo_bit = 48 - 3 * (lmax < 16 ? lmax + 1 : 16);
+    const int hi_bit = 48 + tile_bits(ntiles);
+    int alt = 0;
+    e = svr::launch_sort(d, lo_bit, hi_bit, lmax == 16, &alt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sort");
+    frame->sorted_alt = alt;
+    e = svr::launch_ranges(d, alt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ranges");
+    frame->stage = 2;
+    frame->n_pairs = -1;
+    if (n_pairs_out) {
+        uint32_t flags = 0;
+        int64_t P = 0;
+        int rc = svr_frame_status(frame, &flags, &P, stream);
+        if (rc != SVR_OK) return rc;
+        *n_pairs_out = P;
+        frame->n_pairs = P;
+        if (flags & SVR_FLAG_INVALID_VOXEL)
+            return fail(SVR_ERR_INVALID, "a voxel is off its lattice or its level is outside [1, %d]", lmax);
+        if (flags & SVR_FLAG_CAPACITY)
+            return fail(SVR_ERR_CAPACITY, "%lld pairs > capacity %lld", (long long)P,
+                        (long long)frame->pair_capacity);
+    }
+    return SVR_OK;
+}
+
+SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, float *alpha, float *T_final,
+                           int32_t *last, void *stream) {
+    g_err[0] = 0;
+    if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
+    if (!rgb || !depth || !alpha || !T_final || !last) return fail(SVR_ERR_INVALID, "null output");
+    const svr::FrameDev d = frame_dev(frame);
+    cudaError_t e = svr::launch_render_fwd(d, frame->sorted_alt, rgb, depth, alpha, T_final, last, nullptr,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render_fwd");
+    return SVR_OK;
+}
+
+SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, float *alpha, float *T_final,
+                             int32_t *last, int32_t *counts, void *stream) {
+    g_err[0] = 0;
+    if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
+    if (!rgb || !depth || !alpha || !T_final || !last || !counts) return fail(SVR_ERR_INVALID, "null output");
+    if (((uintptr_t)counts) & 7u) return fail(SVR_ERR_INVALID, "counts not 8-byte aligned");
+    const svr::FrameDev d = frame_dev(frame);
+    cudaError_t e = svr::launch_render_fwd(d, frame->sorted_alt, rgb, depth, alpha, T_final, last, (int2 *)counts,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render_stats");
+    return SVR_OK;
+}
+
+SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const float *d_depth,
+                           const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
+                           float *d_sh, void *stream) {
+    g_err[0] = 0;
+    if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
+    if (!T_final || !last) return fail(SVR_ERR_INVALID, "null T_final or last");
+    if (frame->scene.n_vox > 0 && (!d_grid || !d_sh)) return fail(SVR_ERR_INVALID, "null gradient output");
+    if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
+    const svr::FrameDev d = frame_dev(frame);
+    cudaError_t e = svr::launch_render_bwd(d, frame->sorted_alt, d_rgb, d_depth, d_alpha, T_final, last, d_grid,
+                                           d_sh, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
+    return SVR_OK;
+}
+
+SVR_API int svr_frame_buffers(const svr_frame *frame, svr_buffers *out) {
+    if (!frame || !out || frame->stage < 1) return fail(SVR_ERR_INVALID, "frame not preprocessed");
+    const svr::FrameDev d = frame_dev(frame);
+    out->status = d.status;
+    out->tile_mask = d.tile_mask;
+    out->octpath = d.octpath;
+    out->rect = (const int16_t *)d.rect;
+    out->count = d.count;
+    out->offset = d.offset;
+    out->record = (const float *)d.rec;
+    out->keys = d.keys[frame->sorted_alt];
+    out->values = d.vals[frame->sorted_alt];
+    out->ranges = (const uint32_t *)d.ranges;
+    return SVR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,332 @@
+// Per-view preprocessing, count scan and pair emission (sm_103a).
+//
+//   k_tile_mask   per tile: OR of 1 << signbits(r_d) over its in-image pixels
+//                 (ray sign bits of Sec. B.2; duplication per sign pattern,
+//                 Sec. B.1)
+//   k_preprocess  per voxel: lattice index, Morton code (Sec. A.1), tile
+//                 rectangle of the projected corners (Sec. 3.1.2), pair count,
+//                 view-dependent colour (Eq. vox_color), gathered densities
+//   k_scan_*      exclusive scan of the pair counts (three phases)
+//   k_emit        key = tile << 48 | (octpath ^ s replicated), value = s << 29
+//                 | voxel id (Sec. B.1; the per-triple permutation of Sec. B.2
+//                 is b ^ s, applied to all 16 triples at once)
+#include <climits>
+
+#include "svr_internal.cuh"
+
+namespace svr {
+
+// --------------------------------------------------------------- tile masks
+
+__global__ void k_tile_mask(DevCam cam, uint8_t *__restrict__ mask) {
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.ntx, ty = tile / cam.ntx;
+    unsigned m = 0;
+    const int npx = cam.tile * cam.tile;
+    for (int p = threadIdx.x; p < npx; p += blockDim.x) {
+        int x = tx * cam.tile + p % cam.tile;
+        int y = ty * cam.tile + p / cam.tile;
+        if (x < cam.W && y < cam.H) m |= 1u << sign_bits(pixel_dir(cam, x, y));
+    }
+    m = __reduce_or_sync(0xffffffffu, m);
+    __shared__ unsigned wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned r = 0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) r |= wm[w];
+        mask[tile] = (uint8_t)r;
+    }
+}
+
+// --------------------------------------------------------------- preprocess
+
+// Spread the low 16 bits of x to bit positions 0, 3, 6, ..., 45.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0xFFFFu;
+    x = (x | (x << 16)) & 0x0000FF0000FFull;
+    x = (x | (x << 8)) & 0x00F00F00F00Full;
+    x = (x | (x << 4)) & 0x0C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ void mark_invalid(Status *st, int64_t v) {
+    atomicOr(&st->flags, SVR_FLAG_INVALID_VOXEL);
+    atomicMin(reinterpret_cast<unsigned *>(&st->bad_voxel), (unsigned)v);
+}
+
+__global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= f.n_vox) return;
+    const DevCam &cam = f.cam;
+    const float c0 = f.centre[3 * v + 0], c1 = f.centre[3 * v + 1], c2 = f.centre[3 * v + 2];
+    const int l = f.level[v];
+    const short4 empty = make_short4(0, -1, 0, -1);
+
+    // lattice index: centre = w_min + v_s (ijk + 1/2)
+    bool ok = l >= 1 && l <= f.max_level;
+    const float vs = ldexpf(f.world_size, -l);
+    int ijk[3] = {0, 0, 0};
+    if (ok) {
+        const float cc[3] = {c0, c1, c2};
+        const int n = 1 << l;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float fi = (cc[a] - f.world_min[a]) / vs - 0.5f;
+            float r = rintf(fi);
+            ok = ok && fabsf(fi - r) <= 0.25f && r >= 0.f && r < (float)n;
+            ijk[a] = (int)r;
+        }
+    }
+    // corner indices must name grid points
+    const int4 *ci = reinterpret_cast<const int4 *>(f.corner_idx + 8 * v);
+    const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
+    {
+        const int64_t np = f.n_pts;
+        const int lo = min(min(min(i0.x, i0.y), min(i0.z, i0.w)), min(min(i1.x, i1.y), min(i1.z, i1.w)));
+        const int hi = max(max(max(i0.x, i0.y), max(i0.z, i0.w)), max(max(i1.x, i1.y), max(i1.z, i1.w)));
+        ok = ok && lo >= 0 && (int64_t)hi < np;
+    }
+    if (!ok) {
+        mark_invalid(f.status, v);
+        f.count[v] = 0;
+        f.rect[v] = empty;
+        return;
+    }
+    const uint64_t code = ((spread3(ijk[0]) << 2) | (spread3(ijk[1]) << 1) | spread3(ijk[2]))
+                          << (3 * (kMaxLevel - l));
+    f.octpath[v] = code;
+
+    // project the eight corners
+    const float h = 0.5f * vs;
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    int behind = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float px = (c & 4) ? c0 + h : c0 - h;
+        const float py = (c & 2) ? c1 + h : c1 - h;
+        const float pz = (c & 1) ? c2 + h : c2 - h;
+        const float X = fmaf(cam.R[0], px, fmaf(cam.R[1], py, fmaf(cam.R[2], pz, cam.t[0])));
+        const float Y = fmaf(cam.R[3], px, fmaf(cam.R[4], py, fmaf(cam.R[5], pz, cam.t[1])));
+        const float Z = fmaf(cam.R[6], px, fmaf(cam.R[7], py, fmaf(cam.R[8], pz, cam.t[2])));
+        if (Z <= kNear) {
+            ++behind;
+        } else {
+            const float u = fmaf(cam.fx, X / Z, cam.cx);
+            const float w = fmaf(cam.fy, Y / Z, cam.cy);
+            umin = fminf(umin, u);
+            umax = fmaxf(umax, u);
+            vmin = fminf(vmin, w);
+            vmax = fmaxf(vmax, w);
+        }
+    }
+    short4 rc = empty;
+    if (behind == 8) {
+        // culled
+    } else if (behind > 0) {
+        rc = make_short4(0, (short)(cam.ntx - 1), 0, (short)(cam.nty - 1));
+    } else if (!(umax < 0.f || umin >= (float)cam.W || vmax < 0.f || vmin >= (float)cam.H)) {
+        const float T = (float)cam.tile;
+        const int tx0 = umin < 0.f ? 0 : min(cam.ntx - 1, (int)floorf(umin / T));
+        const int tx1 = umax >= (float)cam.W ? cam.ntx - 1 : min(cam.ntx - 1, (int)floorf(umax / T));
+        const int ty0 = vmin < 0.f ? 0 : min(cam.nty - 1, (int)floorf(vmin / T));
+        const int ty1 = vmax >= (float)cam.H ? cam.nty - 1 : min(cam.nty - 1, (int)floorf(vmax / T));
+        rc = make_short4((short)tx0, (short)tx1, (short)ty0, (short)ty1);
+    }
+    uint32_t cnt = 0;
+    for (int ty = rc.z; ty <= rc.w; ++ty)
+        for (int tx = rc.x; tx <= rc.y; ++tx) cnt += __popc(f.tile_mask[ty * cam.ntx + tx]);
+    f.rect[v] = rc;
+    f.count[v] = cnt;
+    if (cnt == 0) return;
+
+    // record of this view: min corner relative to the ray origin, size,
+    // gathered raw densities, colour
+    Record r;
+    r.r0 = make_float4((c0 - h) - cam.ro[0], (c1 - h) - cam.ro[1], (c2 - h) - cam.ro[2], vs);
+    r.r1 = make_float4(__ldg(f.grid + i0.x), __ldg(f.grid + i0.y), __ldg(f.grid + i0.z), __ldg(f.grid + i0.w));
+    r.r2 = make_float4(__ldg(f.grid + i1.x), __ldg(f.grid + i1.y), __ldg(f.grid + i1.z), __ldg(f.grid + i1.w));
+
+    float dx = c0 - cam.ro[0], dy = c1 - cam.ro[1], dz = c2 - cam.ro[2];
+    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+    float Y[16];
+    sh_basis(dx, dy, dz, Y);
+    const float4 *shv = reinterpret_cast<const float4 *>(f.sh + 48 * v);
+    float sh[48];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        const float4 s4 = __ldg(shv + q);
+        sh[4 * q + 0] = s4.x;
+        sh[4 * q + 1] = s4.y;
+        sh[4 * q + 2] = s4.z;
+        sh[4 * q + 3] = s4.w;
+    }
+    float col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+#pragma unroll
+        for (int n = 0; n < 16; ++n) acc = fmaf(Y[n], sh[3 * n + ch], acc);
+        col[ch] = acc;
+    }
+    unsigned bits = (col[0] > 0.f ? 1u : 0u) | (col[1] > 0.f ? 2u : 0u) | (col[2] > 0.f ? 4u : 0u);
+    r.r3 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), __uint_as_float(bits));
+    f.rec[v] = r;
+}
+
+// --------------------------------------------------------------------- scan
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sums, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint32_t s = warp_sums[w];
+        wpre += (w < warp) ? s : 0u;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + inc - x;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ count, int64_t n,
+                                                     uint32_t *__restrict__ block_sums) {
+    __shared__ uint32_t ws[8];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint64_t acc = 0;
+    for (int r = 0; r < kScanTile / 256; ++r) {
+        int64_t i = base + r * 256 + threadIdx.x;
+        if (i < n) acc += count[i];
+    }
+    uint32_t tot;
+    // counts per voxel are < 2^24 in practice; a block sum beyond 2^32 is
+    // caught by the capacity check on the 64-bit total
+    block_exclusive_scan((uint32_t)tmin<uint64_t>(acc, 0xFFFFFFFFull), ws, tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ block_sums, int nb,
+                                                   Status *st, int64_t capacity) {
+    __shared__ unsigned long long carry;
+    __shared__ unsigned long long wsum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        unsigned long long x = i < nb ? block_sums[i] : 0ull;
+        unsigned long long inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        unsigned long long wpre = 0, tot = 0;
+        for (int w = 0; w < 32; ++w) {
+            wpre += (w < warp) ? wsum[w] : 0ull;
+            tot += wsum[w];
+        }
+        const unsigned long long excl = carry + wpre + inc - x;
+        if (i < nb) block_sums[i] = (uint32_t)tmin<unsigned long long>(excl, 0xFFFFFFFFull);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st->n_pairs_lo = (unsigned)(carry & 0xFFFFFFFFull);
+        st->n_pairs_hi = (unsigned)(carry >> 32);
+        if (carry > (unsigned long long)capacity) atomicOr(&st->flags, SVR_FLAG_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ count, int64_t n,
+                                                   const uint32_t *__restrict__ block_off,
+                                                   uint32_t *__restrict__ offset) {
+    __shared__ uint32_t ws[8];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t carry = block_off[blockIdx.x];
+    for (int r = 0; r < kScanTile / 256; ++r) {
+        const int64_t i = base + r * 256 + threadIdx.x;
+        const uint32_t x = i < n ? count[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(x, ws, tot);
+        if (i < n) offset[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+// --------------------------------------------------------------------- emit
+
+__global__ void __launch_bounds__(256) k_emit(FrameDev f) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= f.n_vox) return;
+    if (f.status->flags & SVR_FLAG_CAPACITY) return;
+    const uint32_t cnt = f.count[v];
+    if (cnt == 0) return;
+    uint32_t o = f.offset[v];
+    const short4 rc = f.rect[v];
+    const uint64_t code = f.octpath[v];
+    uint64_t *keys = f.keys[0];
+    uint32_t *vals = f.vals[0];
+    for (int ty = rc.z; ty <= rc.w; ++ty) {
+        for (int tx = rc.x; tx <= rc.y; ++tx) {
+            const int tile = ty * f.cam.ntx + tx;
+            unsigned m = f.tile_mask[tile];
+            while (m) {
+                const unsigned s = __ffs(m) - 1;
+                m &= m - 1;
+                keys[o] = ((uint64_t)tile << 48) | (code ^ ((uint64_t)s * kTripleOnes));
+                vals[o] = (s << 29) | (uint32_t)v;
+                ++o;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s) {
+    const int ntiles = f.cam.ntx * f.cam.nty;
+    const int threads = f.cam.tile * f.cam.tile >= 256 ? 256 : 64;
+    k_tile_mask<<<ntiles, threads, 0, s>>>(f.cam, f.tile_mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s) {
+    if (f.n_vox == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((f.n_vox + 255) / 256);
+    k_preprocess<<<blocks, 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s) {
+    if (f.n_vox == 0) {
+        k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, 0, f.status, f.capacity);
+        return cudaGetLastError();
+    }
+    const int nb = (int)((f.n_vox + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, 256, 0, s>>>(f.count, f.n_vox, f.scan_blocks);
+    k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, nb, f.status, f.capacity);
+    k_scan_down<<<nb, 256, 0, s>>>(f.count, f.n_vox, f.scan_blocks, f.offset);
+    const unsigned blocks = (unsigned)((f.n_vox + 255) / 256);
+    k_emit<<<blocks, 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+}  // namespace svr

@@ -1,0 +1,147 @@
+// Internal declarations of the sparse-voxel rasterizer (sm_103a).
+// Shared by the kernel translation units and the C ABI; not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/svr.h"
+
+namespace svr {
+
+template <class T>
+__host__ __device__ __forceinline__ T tmin(T a, T b) {
+    return a < b ? a : b;
+}
+
+constexpr int kMaxLevel = 16;
+constexpr float kNear = 1e-3f;             // corners at camera depth <= kNear are "behind"
+constexpr uint64_t kTripleOnes = 0x249249249249ull;  // bit 0 of each of the 16 triples
+constexpr int kRadixItems = 16;            // keys per thread in one radix tile
+constexpr int kRadixThreads = 256;
+constexpr int kRadixTile = kRadixItems * kRadixThreads;
+constexpr int kScanTile = 4096;            // voxels per block of the count scan
+
+// Camera as the kernels see it: intrinsics, [R | t], the ray origin -R^T t
+// (computed in double on the host) and the tile grid.
+struct DevCam {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float ro[3];
+    int W, H;
+    int ntx, nty;
+    int tile;
+};
+
+// Device status block at the start of the workspace (64 bytes).
+struct Status {
+    unsigned flags;       // SVR_FLAG_*
+    unsigned n_pairs_lo;  // total pair count (64-bit, split)
+    unsigned n_pairs_hi;
+    int bad_voxel;        // smallest invalid voxel id, or INT_MAX
+    unsigned pad[12];
+};
+
+// Per-voxel record of one view (64 bytes):
+//   r0 = (lo - r_o).xyz, size      lo = centre - size / 2, the min corner
+//   r1 = corner densities 0..3     (raw, gathered from the grid)
+//   r2 = corner densities 4..7
+//   r3 = colour rgb, bit c of the w word set if channel c was > 0 before the clamp
+struct Record {
+    float4 r0, r1, r2, r3;
+};
+
+// Ray direction of pixel (x, y): R^T ((x + .5 - cx) / fx, (y + .5 - cy) / fy, 1),
+// written with explicit roundings so every kernel derives the same bits.
+__device__ __forceinline__ float3 pixel_dir(const DevCam &c, int x, int y) {
+    float dx = __fdiv_rn(__fsub_rn(__fadd_rn((float)x, 0.5f), c.cx), c.fx);
+    float dy = __fdiv_rn(__fsub_rn(__fadd_rn((float)y, 0.5f), c.cy), c.fy);
+    float3 d;
+    d.x = __fadd_rn(__fadd_rn(__fmul_rn(c.R[0], dx), __fmul_rn(c.R[3], dy)), c.R[6]);
+    d.y = __fadd_rn(__fadd_rn(__fmul_rn(c.R[1], dx), __fmul_rn(c.R[4], dy)), c.R[7]);
+    d.z = __fadd_rn(__fadd_rn(__fmul_rn(c.R[2], dx), __fmul_rn(c.R[5], dy)), c.R[8]);
+    return d;
+}
+
+// 4 (rd.x < 0) + 2 (rd.y < 0) + (rd.z < 0).
+__device__ __forceinline__ int sign_bits(float3 d) {
+    return (d.x < 0.f ? 4 : 0) | (d.y < 0.f ? 2 : 0) | (d.z < 0.f ? 1 : 0);
+}
+
+// explin (Eq. explin): x above 1.1, else exp(x / 1.1 - 1 + ln 1.1).
+__device__ __forceinline__ float explin(float x) {
+    return x > 1.1f ? x : __expf(fmaf(x, 0.909090909f, -0.904689820f));
+}
+
+// Real SH basis, degree 0..3, index l*l + l + m, no Condon-Shortley phase,
+// as polynomials of the unit direction (x, y, z).  Constants are
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the factors of the
+// corresponding Legendre / trigonometric polynomial.
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = 0.28209479177387814f;
+    Y[1] = 0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = 0.4886025119029199f * x;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = 1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.f * zz - 1.f);
+    Y[7] = 1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (xx - yy);
+    Y[9] = 0.5900435899266435f * y * (3.f * xx - yy);
+    Y[10] = 2.890611442640554f * x * y * z;
+    Y[11] = 0.4570457994644658f * y * (5.f * zz - 1.f);
+    Y[12] = 0.3731763325901154f * z * (5.f * zz - 3.f);
+    Y[13] = 0.4570457994644658f * x * (5.f * zz - 1.f);
+    Y[14] = 1.445305721320277f * z * (xx - yy);
+    Y[15] = 0.5900435899266435f * x * (xx - 3.f * yy);
+}
+
+// ------------------------------------------------------------ launchers
+
+struct FrameDev {
+    DevCam cam;
+    Status *status;
+    uint8_t *tile_mask;
+    uint64_t *octpath;
+    short4 *rect;
+    uint32_t *count;
+    uint32_t *offset;
+    Record *rec;
+    uint32_t *scan_blocks;   // [ceil(N / kScanTile)]
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *hist;          // [256][capacity tiles]
+    uint32_t *digit_tot;     // [256]
+    uint2 *ranges;           // [ntiles]
+    float *dcol;             // [N][3] colour gradient accumulator
+    int64_t n_vox;
+    int64_t n_pts;
+    int64_t capacity;
+    float world_size;
+    float world_min[3];      // w_c - w_s / 2
+    int max_level;
+    int K;
+    float t_stop;
+    float bg[3];
+    const float *centre;
+    const uint8_t *level;
+    const int32_t *corner_idx;
+    const float *grid;
+    const float *sh;
+};
+
+cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_sort(const FrameDev &f, int lo_bit, int hi_bit, bool sign_pass, int *result_alt,
+                        cudaStream_t s);
+cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s);
+cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth,
+                              float *alpha, float *T_final, int32_t *last, int2 *stats, cudaStream_t s);
+cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_rgb,
+                              const float *d_depth, const float *d_alpha, const float *T_final,
+                              const int32_t *last, float *d_grid, float *d_sh, cudaStream_t s);
+
+}  // namespace svr

@@ -1,0 +1,295 @@
+"""Python front end of the sparse-voxel rasterizer.
+
+Thin layer over the C ABI (include/svr.h): device memory and streams come
+from PyTorch, every step of the path runs in libsvr.so's kernels.
+
+    scene = DeviceScene.from_arrays(...)          # or from a synth.Scene
+    frame = Frame(scene, camera, K=3)             # workspace + per-view state
+    out = frame.render()                          # preprocess, bin/sort, forward
+    d_grid, d_sh = frame.backward(g_rgb, g_depth, g_alpha, out)
+
+    rgb, depth, alpha = rasterize(grid, sh, scene, camera, K=3)   # autograd
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream: Optional[torch.cuda.Stream] = None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> N.SvrCamera:
+    """svr_camera from any object with fx, fy, cx, cy, w2c [3, 4], width, height."""
+    c = N.SvrCamera()
+    c.fx, c.fy, c.cx, c.cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    w2c = np.asarray(cam.w2c, np.float32).reshape(-1)
+    for i in range(12):
+        c.w2c[i] = float(w2c[i])
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def params_struct(K: int = 1, t_stop: float = 1e-4, tile: int = 16, bg=(0.0, 0.0, 0.0)) -> N.SvrParams:
+    p = N.SvrParams()
+    p.K, p.t_stop, p.tile = int(K), float(t_stop), int(tile)
+    for i in range(3):
+        p.bg[i] = float(bg[i])
+    return p
+
+
+@dataclasses.dataclass
+class DeviceScene:
+    """Scene arrays resident on the GPU (the C ABI's svr_scene)."""
+    centre: torch.Tensor      # float32 [N, 3]
+    level: torch.Tensor       # uint8 [N]
+    corner_idx: torch.Tensor  # int32 [N, 8]
+    grid: torch.Tensor        # float32 [Pts]
+    sh: torch.Tensor          # float32 [N, 48]
+    world_center: tuple
+    world_size: float
+    max_level: int
+
+    @property
+    def n_vox(self) -> int:
+        return int(self.level.shape[0])
+
+    @staticmethod
+    def from_host(scene, device="cuda", max_level: Optional[int] = None) -> "DeviceScene":
+        def t(a, dtype):
+            return torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dtype)
+        ml = max_level if max_level is not None else max(1, int(scene.max_level))
+        return DeviceScene(t(scene.centre, torch.float32), t(scene.level, torch.uint8),
+                           t(scene.corner_idx, torch.int32), t(scene.grid, torch.float32),
+                           t(scene.sh, torch.float32),
+                           tuple(float(x) for x in np.asarray(scene.world_center, np.float32)),
+                           float(np.float32(scene.world_size)), ml)
+
+    def struct(self, grid: Optional[torch.Tensor] = None, sh: Optional[torch.Tensor] = None) -> N.SvrScene:
+        g = self.grid if grid is None else grid
+        s = self.sh if sh is None else sh
+        for name, x in (("centre", self.centre), ("level", self.level), ("corner_idx", self.corner_idx),
+                        ("grid", g), ("sh", s)):
+            if not x.is_cuda or not x.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        sc = N.SvrScene()
+        for i in range(3):
+            sc.world_center[i] = self.world_center[i]
+        sc.world_size = self.world_size
+        sc.n_vox = self.n_vox
+        sc.n_pts = int(g.shape[0])
+        sc.max_level = int(self.max_level)
+        sc.centre = self.centre.data_ptr()
+        sc.level = self.level.data_ptr()
+        sc.corner_idx = self.corner_idx.data_ptr()
+        sc.grid = g.data_ptr()
+        sc.sh = s.data_ptr()
+        return sc
+
+
+def workspace_size(n_vox: int, pair_capacity: int, cam, K=1, t_stop=1e-4, tile=16, bg=(0, 0, 0)) -> int:
+    c = camera_struct(cam)
+    p = params_struct(K, t_stop, tile, bg)
+    n = N.lib().svr_workspace_size(int(n_vox), int(pair_capacity), N.ref(c), N.ref(p))
+    if n == 0:
+        raise N.SvrError(N.SVR_ERR_INVALID, "svr_workspace_size", "invalid arguments")
+    return int(n)
+
+
+class Frame:
+    """One view of a scene: its workspace, its svr_frame and its outputs."""
+
+    def __init__(self, scene: DeviceScene, cam, K: int = 1, t_stop: float = 1e-4, tile: int = 16,
+                 bg=(0.0, 0.0, 0.0), pair_capacity: Optional[int] = None):
+        self.scene = scene
+        self.cam = cam
+        self.cstruct = camera_struct(cam)
+        self.pstruct = params_struct(K, t_stop, tile, bg)
+        self.K = K
+        if pair_capacity is None:
+            pair_capacity = max(1 << 16, 4 * scene.n_vox)
+        self.pair_capacity = int(pair_capacity)
+        self.frame = N.SvrFrame()
+        self.ws = None
+        self.n_pairs = None
+        self.grid = scene.grid
+        self.sh = scene.sh
+
+    def _alloc(self):
+        nbytes = workspace_size(self.scene.n_vox, self.pair_capacity, self.cam, self.pstruct.K,
+                                self.pstruct.t_stop, self.pstruct.tile, tuple(self.pstruct.bg))
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.scene.centre.device)
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self._ws_bytes = self.ws.numel() - (self._ws_ptr - base)
+
+    def preprocess(self, grid=None, sh=None, stream=None):
+        self.grid = self.scene.grid if grid is None else grid
+        self.sh = self.scene.sh if sh is None else sh
+        self._alloc()
+        self.sstruct = self.scene.struct(self.grid, self.sh)
+        N.check(N.lib().svr_preprocess(N.ref(self.frame), N.ref(self.sstruct), N.ref(self.cstruct),
+                                       N.ref(self.pstruct), ctypes.c_void_p(self._ws_ptr), self._ws_bytes,
+                                       self.pair_capacity, _stream(stream)), "svr_preprocess")
+
+    def bin_sort(self, sync: bool = True, stream=None) -> Optional[int]:
+        """Emit and sort the pairs.  sync=True reads the pair count back (and
+        grows the workspace and redoes the view if it did not fit)."""
+        if not sync:
+            N.check(N.lib().svr_bin_sort(N.ref(self.frame), None, _stream(stream)), "svr_bin_sort")
+            self.n_pairs = None
+            return None
+        n = ctypes.c_int64(0)
+        rc = N.lib().svr_bin_sort(N.ref(self.frame), N.ref(n), _stream(stream))
+        if rc == N.SVR_ERR_CAPACITY:
+            self.pair_capacity = int(n.value * 1.25) + 1024
+            self.preprocess(self.grid, self.sh, stream)
+            rc = N.lib().svr_bin_sort(N.ref(self.frame), N.ref(n), _stream(stream))
+        N.check(rc, "svr_bin_sort")
+        self.n_pairs = int(n.value)
+        return self.n_pairs
+
+    def forward(self, out=None, stream=None):
+        H, W = self.cam.height, self.cam.width
+        dev = self.scene.centre.device
+        if out is None:
+            out = dict(rgb=torch.empty(3, H, W, device=dev), depth=torch.empty(H, W, device=dev),
+                       alpha=torch.empty(H, W, device=dev), T_final=torch.empty(H, W, device=dev),
+                       last=torch.empty(H, W, dtype=torch.int32, device=dev))
+        N.check(N.lib().svr_render_fwd(N.ref(self.frame), _ptr(out["rgb"]), _ptr(out["depth"]),
+                                       _ptr(out["alpha"]), _ptr(out["T_final"]), _ptr(out["last"]),
+                                       _stream(stream)), "svr_render_fwd")
+        return out
+
+    def forward_stats(self, stream=None):
+        """Forward render plus per-pixel (candidates examined, hits) counts."""
+        H, W = self.cam.height, self.cam.width
+        dev = self.scene.centre.device
+        out = dict(rgb=torch.empty(3, H, W, device=dev), depth=torch.empty(H, W, device=dev),
+                   alpha=torch.empty(H, W, device=dev), T_final=torch.empty(H, W, device=dev),
+                   last=torch.empty(H, W, dtype=torch.int32, device=dev),
+                   counts=torch.empty(H, W, 2, dtype=torch.int32, device=dev))
+        N.check(N.lib().svr_render_stats(N.ref(self.frame), _ptr(out["rgb"]), _ptr(out["depth"]),
+                                         _ptr(out["alpha"]), _ptr(out["T_final"]), _ptr(out["last"]),
+                                         _ptr(out["counts"]), _stream(stream)), "svr_render_stats")
+        return out
+
+    def render(self, grid=None, sh=None, sync: bool = True, stream=None):
+        self.preprocess(grid, sh, stream)
+        self.bin_sort(sync=sync, stream=stream)
+        return self.forward(stream=stream)
+
+    def backward(self, g_rgb, g_depth, g_alpha, out, d_grid=None, d_sh=None, stream=None):
+        dev = self.scene.centre.device
+        if d_grid is None:
+            d_grid = torch.zeros(self.grid.shape[0], device=dev)
+        if d_sh is None:
+            d_sh = torch.empty(self.scene.n_vox, 48, device=dev)
+        c = lambda t: None if t is None else t.contiguous()
+        N.check(N.lib().svr_render_bwd(N.ref(self.frame), _ptr(c(g_rgb)), _ptr(c(g_depth)),
+                                       _ptr(c(g_alpha)), _ptr(out["T_final"]), _ptr(out["last"]),
+                                       _ptr(d_grid), _ptr(d_sh), _stream(stream)), "svr_render_bwd")
+        return d_grid, d_sh
+
+    def status(self, stream=None):
+        flags = ctypes.c_uint32(0)
+        n = ctypes.c_int64(0)
+        N.check(N.lib().svr_frame_status(N.ref(self.frame), N.ref(flags), N.ref(n), _stream(stream)),
+                "svr_frame_status")
+        return int(flags.value), int(n.value)
+
+    def buffers(self) -> N.SvrBuffers:
+        b = N.SvrBuffers()
+        N.check(N.lib().svr_frame_buffers(N.ref(self.frame), N.ref(b)), "svr_frame_buffers")
+        return b
+
+    # -- inspection helpers (copies of internal buffers) ---------------------
+    def _dev_array(self, ptr, n, dtype):
+        if n == 0:
+            return torch.empty(0, dtype=dtype, device=self.scene.centre.device)
+        nbytes = n * torch.empty(0, dtype=dtype).element_size()
+        out = torch.empty(n, dtype=dtype, device=self.scene.centre.device)
+        cudart_copy(out.data_ptr(), ptr, nbytes)
+        return out
+
+    def inspect(self):
+        """Host copies of the integer buffers (synchronises)."""
+        torch.cuda.synchronize()
+        b = self.buffers()
+        nv = self.scene.n_vox
+        ntiles = self.frame.n_tiles_x * self.frame.n_tiles_y
+        flags, P = self.status()
+        Pc = min(P, self.pair_capacity)
+        get = lambda p, n, dt: self._dev_array(p, n, dt).cpu().numpy()
+        return dict(
+            flags=flags, n_pairs=P,
+            tile_mask=get(b.tile_mask, ntiles, torch.uint8),
+            octpath=get(b.octpath, nv, torch.int64).view(np.uint64),
+            rect=get(b.rect, 4 * nv, torch.int16).reshape(nv, 4),
+            count=get(b.count, nv, torch.int32).view(np.uint32),
+            offset=get(b.offset, nv, torch.int32).view(np.uint32),
+            keys=get(b.keys, Pc, torch.int64).view(np.uint64),
+            values=get(b.values, Pc, torch.int32).view(np.uint32),
+            ranges=get(b.ranges, 2 * ntiles, torch.int32).view(np.uint32).reshape(ntiles, 2),
+        )
+
+
+def cudart_copy(dst: int, src: int, nbytes: int):
+    """Device-to-device copy through torch (no allocation by the library)."""
+    d = torch.cuda.current_device()
+    src_t = _wrap_device_ptr(src, nbytes, d)
+    dst_t = _wrap_device_ptr(dst, nbytes, d)
+    dst_t.copy_(src_t)
+
+
+def _wrap_device_ptr(ptr: int, nbytes: int, device: int) -> torch.Tensor:
+    """A uint8 tensor view of existing device memory (not owned)."""
+    class _Holder:
+        pass
+    h = _Holder()
+    h.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                  "version": 3, "strides": None}
+    return torch.as_tensor(h, device=f"cuda:{device}")
+
+
+# --------------------------------------------------------------------- autograd
+
+class SVRasterFn(torch.autograd.Function):
+    """rgb, depth, alpha = f(grid, sh) for a fixed voxel layout and camera.
+
+    Forward: svr_preprocess + svr_bin_sort + svr_render_fwd.  Backward:
+    svr_render_bwd, which recomputes each pixel's walk back to front from the
+    saved T_final and last index."""
+
+    @staticmethod
+    def forward(ctx, grid, sh, scene: DeviceScene, cam, K: int, t_stop: float, bg, pair_capacity):
+        frame = Frame(scene, cam, K=K, t_stop=t_stop, bg=bg, pair_capacity=pair_capacity)
+        out = frame.render(grid.detach().contiguous(), sh.detach().contiguous())
+        ctx.frame = frame
+        ctx.out = out
+        return out["rgb"], out["depth"], out["alpha"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_alpha):
+        frame = ctx.frame
+        d_grid, d_sh = frame.backward(g_rgb, g_depth, g_alpha, ctx.out)
+        return d_grid, d_sh, None, None, None, None, None, None
+
+
+def rasterize(grid, sh, scene: DeviceScene, cam, K: int = 1, t_stop: float = 1e-4,
+              bg=(0.0, 0.0, 0.0), pair_capacity: Optional[int] = None):
+    """Differentiable render of (grid densities, SH) -> (rgb [3,H,W], depth, alpha)."""
+    return SVRasterFn.apply(grid, sh, scene, cam, K, t_stop, tuple(bg), pair_capacity)

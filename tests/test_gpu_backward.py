@@ -1,0 +1,116 @@
+"""Backward parity: the CUDA back-to-front backward (through the C ABI) vs the
+oracle's FP64 analytic gradient, which the CPU tests pin to finite
+differences; and the autograd front end."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.conftest import cached
+from tests.gpu_common import compare_grads, require_gpu, run_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _grads(scene, cam, K, t_stop, bg, seed, ref_stop=None):
+    import torch
+    fr, out, _ = run_gpu(scene, cam, K=K, t_stop=t_stop, bg=bg, inspect=False)
+    g_rgb, g_depth, g_alpha = synth.upstream_grads(seed, cam.height, cam.width)
+    if ref_stop is not None:
+        # pixels whose transmittance grazes the threshold have a jump there
+        keep = ref_stop == 0
+        g_rgb = g_rgb * keep[None]
+        g_depth = g_depth * keep
+        g_alpha = g_alpha * keep
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    d_grid, d_sh = fr.backward(t(g_rgb), t(g_depth), t(g_alpha), out)
+    og, osh = oracle.render_grad(scene, cam, g_rgb.astype(np.float64), g_depth, g_alpha, K=K,
+                                 t_stop=t_stop, bg=bg)
+    return d_grid.cpu().numpy(), d_sh.cpu().numpy(), og, osh
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tiny_gradients(K, seed):
+    sc = synth.random_octree_scene(seed + 20, max_level=4, p_split=0.5, max_cells=64,
+                                   grid_fn=synth.normal_grid(1.0, 1.5))
+    cam = synth.orbit_camera(seed + 3, 48, 40, distance=1.7)
+    bg = (0.1, 0.2, 0.3) if seed else (0.0, 0.0, 0.0)
+    ref = oracle.render(sc, cam, K=K, t_stop=1e-4, bg=bg)
+    dg, ds, og, osh = _grads(sc, cam, K, 1e-4, bg, seed, ref["near_stop"])
+    compare_grads(dg, og, name="grid")
+    compare_grads(ds, osh, name="sh")
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_dense_level5_gradients(K):
+    sc = cached("dense5", lambda: synth.dense_scene(5, seed=0))
+    cam = synth.dense_view_camera()
+    ref = cached(("dense5_ref", K), lambda: oracle.render(sc, cam, K=K, t_stop=1e-4))
+    dg, ds, og, osh = _grads(sc, cam, K, 1e-4, (0.0, 0.0, 0.0), 5, ref["near_stop"])
+    compare_grads(dg, og, name="grid")
+    compare_grads(ds, osh, name="sh")
+
+
+def test_terminated_pixels_gradients():
+    """Opaque scene: most pixels stop early; the backward starts at `last`."""
+    sc = synth.random_octree_scene(31, max_level=4, p_split=0.6, max_cells=64,
+                                   grid_fn=synth.normal_grid(8.0, 2.0))
+    cam = synth.orbit_camera(6, 40, 40, distance=1.6)
+    ref = oracle.render(sc, cam, K=3, t_stop=1e-3)
+    assert (ref["term_vox"] >= 0).mean() > 0.2
+    dg, ds, og, osh = _grads(sc, cam, 3, 1e-3, (0.0, 0.0, 0.0), 2, ref["near_stop"])
+    compare_grads(dg, og, name="grid")
+    compare_grads(ds, osh, name="sh")
+
+
+def test_underflowing_transmittance_takes_front_to_back_phase():
+    """Densities so high that T_final underflows to 0 (t_stop = 0): the
+    back-to-front division is impossible and the kernel's front-to-back
+    phase must give the same gradients."""
+    def grid_fn(pos, rng):
+        dense = rng.random(len(pos)) < 0.3
+        return np.where(dense, 400.0, rng.normal(0.5, 1.0, size=len(pos)))
+    sc = synth.random_octree_scene(41, max_level=3, p_split=0.4, max_cells=60, grid_fn=grid_fn)
+    cam = synth.orbit_camera(8, 32, 32, distance=1.6)
+    fr, out, _ = run_gpu(sc, cam, K=2, t_stop=0.0, inspect=False)
+    T = to_np(out)["T_final"]
+    assert (T < 1e-30).mean() > 0.05
+    dg, ds, og, osh = _grads(sc, cam, 2, 0.0, (0.2, 0.2, 0.2), 4)
+    assert np.isfinite(dg).all() and np.isfinite(ds).all()
+    compare_grads(dg, og, name="grid")
+    compare_grads(ds, osh, name="sh")
+
+
+def test_autograd_matches_frame_backward_and_l2_loss():
+    """rasterize() under autograd: an L2 loss against a target rendered from
+    perturbed densities; gradients equal the oracle's for the same loss."""
+    import torch
+    from paper_2412_04459_gb300 import DeviceScene, rasterize
+    sc = synth.random_octree_scene(51, max_level=4, p_split=0.5, max_cells=64,
+                                   grid_fn=synth.normal_grid(1.5, 1.0))
+    cam = synth.orbit_camera(10, 40, 32, distance=1.7)
+    dev = DeviceScene.from_host(sc)
+    rng = np.random.default_rng(1)
+    target_grid = torch.as_tensor(sc.grid + 0.1 * rng.normal(size=sc.n_pts).astype(np.float32), device="cuda")
+    with torch.no_grad():
+        target, _, _ = rasterize(target_grid, dev.sh, dev, cam, K=3)
+    grid = dev.grid.clone().requires_grad_(True)
+    sh = dev.sh.clone().requires_grad_(True)
+    rgb, depth, alpha = rasterize(grid, sh, dev, cam, K=3)
+    loss = ((rgb - target) ** 2).mean()
+    loss.backward()
+    # same loss through the oracle: dL/dC = 2 (C - C*) / (3 H W)
+    ref = oracle.render(sc, cam, K=3)
+    tgt = oracle.render(sc, cam, K=3, grid=target_grid.cpu().numpy().astype(np.float64))
+    g_rgb = 2.0 * (ref["rgb"] - tgt["rgb"]) / ref["rgb"].size
+    zeros = np.zeros((cam.height, cam.width))
+    og, osh = oracle.render_grad(sc, cam, g_rgb, zeros, zeros, K=3)
+    compare_grads(grid.grad.cpu().numpy(), og, rel=2e-3, name="grid")
+    compare_grads(sh.grad.cpu().numpy(), osh, rel=2e-3, name="sh")
+    assert abs(loss.item() - float(((ref["rgb"] - tgt["rgb"]) ** 2).mean())) < 1e-6

@@ -59,8 +59,8 @@ def test_dense_level5_gradients(K):
 
 def test_terminated_pixels_gradients():
     """Opaque scene: most pixels stop early; the backward starts at `last`."""
-    sc = synth.random_octree_scene(31, max_level=4, p_split=0.6, max_cells=64,
-                                   grid_fn=synth.normal_grid(8.0, 2.0))
+    sc = synth.random_octree_scene(31, max_level=4, p_split=0.4,
+                                   grid_fn=synth.normal_grid(12.0, 2.0))
     cam = synth.orbit_camera(6, 40, 40, distance=1.6)
     ref = oracle.render(sc, cam, K=3, t_stop=1e-3)
     assert (ref["term_vox"] >= 0).mean() > 0.2

@@ -49,8 +49,11 @@ def test_dense_level5_full_frame(K):
     sc = dense5()
     cam = synth.dense_view_camera()
     fr, out, ins = run_gpu(sc, cam, K=K, t_stop=1e-4)
-    n_amb, n_either = compare_integers(sc, cam, ins)
-    assert n_amb <= 10 and n_either <= 2
+    n_diff, n_either = compare_integers(sc, cam, ins)
+    # rectangles may differ only where a projected corner lands within the
+    # rounding margin of a tile edge (lattice corners on the optical axis do)
+    _, amb = oracle.binning.voxel_rects(sc, cam)
+    assert n_diff <= amb.sum() and n_either <= 2
     assert len(np.unique(ins["tile_mask"])) > 2          # several sign patterns present
     ref = cached(("dense5_ref", K), lambda: oracle.render(sc, cam, K=K, t_stop=1e-4))
     err, excluded = compare_images(out, ref)
@@ -58,8 +61,8 @@ def test_dense_level5_full_frame(K):
 
 
 def test_last_index_names_the_stopping_voxel():
-    sc = synth.random_octree_scene(7, max_level=4, p_split=0.6, max_cells=64,
-                                   grid_fn=synth.normal_grid(6.0, 1.0))
+    sc = synth.random_octree_scene(7, max_level=4, p_split=0.4,
+                                   grid_fn=synth.normal_grid(12.0, 2.0))
     cam = synth.orbit_camera(4, 40, 40, distance=1.6)
     fr, out, ins = run_gpu(sc, cam, K=2, t_stop=1e-2)
     ref = oracle.render(sc, cam, K=2, t_stop=1e-2)
@@ -122,7 +125,7 @@ def test_invalid_voxels_are_reported():
     from paper_2412_04459_gb300 import DeviceScene, Frame, _native as N
     sc = synth.dense_scene(2)
     sc.centre = sc.centre.copy()
-    sc.centre[5, 1] += 0.1 * 0.25       # 0.4 of a level-2 cell off its lattice point
+    sc.centre[5, 1] += 0.4 * 0.25       # 0.4 of a level-2 cell off its lattice point
     fr = Frame(DeviceScene.from_host(sc), synth.dense_view_camera(32, 32))
     fr.preprocess()
     with pytest.raises(N.SvrError) as e:

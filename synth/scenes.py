@@ -19,6 +19,8 @@ This module only builds inputs.  It holds none of the rasterizer's arithmetic.
 from __future__ import annotations
 
 import dataclasses
+import hashlib
+import os
 
 import numpy as np
 
@@ -321,6 +323,39 @@ def shell_scene(seed: int = 0, target: int = 1 << 20, p_split: float | None = No
     """
     if spec is None and p_split is None and ("one", seed, target) in KNOWN_SPLIT_P:
         p_split = KNOWN_SPLIT_P[("one", seed, target)]
+    cache = _cache_path("shell", seed, target, p_split, spec, sh_std, near_mean, near_std, far_value)
+    if cache and os.path.exists(cache):
+        return _load(cache)
+    scene = _shell_scene(seed, target, p_split, spec, sh_std, near_mean, near_std, far_value)
+    if cache:
+        _save(cache, scene)
+    return scene
+
+
+def _cache_path(*key):
+    """File under $SVR_SCENE_CACHE for a generated scene (None if unset)."""
+    d = os.environ.get("SVR_SCENE_CACHE")
+    if not d:
+        return None
+    os.makedirs(d, exist_ok=True)
+    h = hashlib.sha1(repr(key).encode()).hexdigest()[:16]
+    return os.path.join(d, f"scene_{h}.npz")
+
+
+def _save(path, scene):
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, **{k: np.asarray(v) for k, v in dataclasses.asdict(scene).items()})
+    os.replace(tmp, path)
+
+
+def _load(path):
+    z = np.load(path)
+    kw = {k: z[k] for k in z.files}
+    kw["world_size"] = np.float32(kw["world_size"])
+    return Scene(**kw)
+
+
+def _shell_scene(seed, target, p_split, spec, sh_std, near_mean, near_std, far_value):
     spec = dict(SHELL_ONE if spec is None else spec)
     if p_split is None:
         key = (seed, target, tuple(sorted((k, str(v)) for k, v in spec.items())))

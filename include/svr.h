@@ -217,6 +217,31 @@ SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const flo
 SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, float *alpha,
                              float *T_final, int32_t *last, int32_t *counts, void *stream);
 
+/*
+ * Forward render of one view that allocates nothing and needs no workspace
+ * from the caller.  The paper has no counterpart: it exists for callers that
+ * may not allocate device memory themselves (a plugin inside an application
+ * that owns the device-memory budget, or a latency-critical render callback
+ * where an allocation and the device synchronisation it can cause are not
+ * allowed).  Same computation and outputs as svr_preprocess + svr_bin_sort
+ * (with a pair count) + svr_render_fwd, but the scratch memory is one 16 MiB
+ * array compiled into the library, which every GPU that loads the library
+ * keeps until the process exits.
+ * Limits: at most 65536 voxels, and as many pairs as fit in the array next to
+ * the voxel buffers; beyond them the call returns SVR_ERR_LIMIT (voxels or
+ * image) or SVR_ERR_CAPACITY (pairs; *n_pairs_out then holds the count).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  The call synchronises the stream (to read the pair count).  All
+ * calls share the array and each leaves its contents behind (everything that
+ * must start at zero is cleared by the call); calls whose GPU work overlaps
+ * race on the array.  Outputs as for svr_render_fwd; n_pairs_out may be NULL.
+ */
+SVR_API int svr_render_fwd_static(const svr_scene *scene, const svr_camera *cam,
+                                  const svr_params *params, float *rgb, float *depth,
+                                  float *alpha, float *T_final, int32_t *last,
+                                  int64_t *n_pairs_out, void *stream);
+
 /* Synchronises the stream and reads the device-side error flags
  * (SVR_FLAG_*) and the pair count of a frame.  Either output may be NULL. */
 SVR_API int svr_frame_status(const svr_frame *frame, uint32_t *flags, int64_t *n_pairs,

@@ -71,6 +71,7 @@ SIGNATURES = {
     "svr_render_fwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "svr_render_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_render_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "svr_render_fwd_static": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_frame_status": (ctypes.c_int, [_P, _P, _P, _P]),
     "svr_frame_buffers": (ctypes.c_int, [_P, _P]),
     "svr_last_error": (ctypes.c_char_p, []),

@@ -141,6 +141,16 @@ int tile_bits(int64_t ntiles) {
 
 }  // namespace
 
+namespace svr {
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+}  // namespace svr
+
 extern "C" {
 
 SVR_API const char *svr_last_error(void) { return g_err; }

@@ -132,6 +132,9 @@ struct FrameDev {
     const float *sh;
 };
 
+// Records a printf-style message for svr_last_error() and returns code.
+int set_error(int code, const char *fmt, ...);
+
 cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s);

@@ -28,7 +28,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 enum Slot {
     kStatus, kTileMask, kOctpath, kRect, kCount, kOffset, kRecord, kScanBlocks,
-    kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kTotal, kNumSlots
+    kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kBox, kTileOrder, kTotal, kNumSlots
 };
 
 struct Layout {
@@ -59,6 +59,8 @@ Layout make_layout(int64_t n_vox, int64_t cap, int64_t ntiles) {
     take(kDigitTot, 4 * 256);
     take(kRanges, 8 * (size_t)ntiles);
     take(kDcol, 12 * N);
+    take(kBox, 8 * N);
+    take(kTileOrder, 4 * (size_t)ntiles);
     L.off[kTotal] = o;
     return L;
 }
@@ -107,6 +109,8 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.count = (uint32_t *)(ws + o[kCount]);
     d.offset = (uint32_t *)(ws + o[kOffset]);
     d.rec = (svr::Record *)(ws + o[kRecord]);
+    d.box = (ushort4 *)(ws + o[kBox]);
+    d.tile_order = (uint32_t *)(ws + o[kTileOrder]);
     d.scan_blocks = (uint32_t *)(ws + o[kScanBlocks]);
     d.keys[0] = (uint64_t *)(ws + o[kKeys0]);
     d.keys[1] = (uint64_t *)(ws + o[kKeys1]);

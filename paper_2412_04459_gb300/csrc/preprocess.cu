@@ -122,11 +122,20 @@ __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
         }
     }
     short4 rc = empty;
+    ushort4 box = make_ushort4(0, (unsigned short)(cam.W - 1), 0, (unsigned short)(cam.H - 1));
     if (behind == 8) {
         // culled
     } else if (behind > 0) {
         rc = make_short4(0, (short)(cam.ntx - 1), 0, (short)(cam.nty - 1));
     } else if (!(umax < 0.f || umin >= (float)cam.W || vmax < 0.f || vmin >= (float)cam.H)) {
+        // pixels whose centre (x + 1/2, y + 1/2) can lie in the projected box,
+        // widened by a rounding margin: a conservative filter for the render
+        const float mu = 0.01f + 1e-5f * fmaxf(fabsf(umin), fabsf(umax));
+        const float mv = 0.01f + 1e-5f * fmaxf(fabsf(vmin), fabsf(vmax));
+        const float fx0 = fmaxf(floorf(umin - 0.5f - mu), 0.f), fx1 = fminf(floorf(umax - 0.5f + mu), (float)(cam.W - 1));
+        const float fy0 = fmaxf(floorf(vmin - 0.5f - mv), 0.f), fy1 = fminf(floorf(vmax - 0.5f + mv), (float)(cam.H - 1));
+        box = make_ushort4((unsigned short)fx0, (unsigned short)fmaxf(fx1, fx0), (unsigned short)fy0,
+                           (unsigned short)fmaxf(fy1, fy0));
         const float T = (float)cam.tile;
         const int tx0 = umin < 0.f ? 0 : min(cam.ntx - 1, (int)floorf(umin / T));
         const int tx1 = umax >= (float)cam.W ? cam.ntx - 1 : min(cam.ntx - 1, (int)floorf(umax / T));
@@ -140,6 +149,7 @@ __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
     f.rect[v] = rc;
     f.count[v] = cnt;
     if (cnt == 0) return;
+    f.box[v] = box;
 
     // record of this view: min corner relative to the ray origin, size,
     // gathered raw densities, colour

@@ -1,20 +1,29 @@
 // Forward and backward compositing of the sorted tile lists (sm_103a).
 //
-// One CTA per 16x16 tile, one thread per pixel; warp w covers the 8x4 pixel
-// block (w & 1, w >> 1) of its tile.  The tile's list is staged through
-// shared memory 256 entries at a time (one entry per thread: value, then the
-// voxel's 64-byte record as four 16-byte loads); every pixel then walks the
-// staged entries, skipping those whose sign bits differ from its own
-// (Sec. B.1) and those its ray misses (ray-AABB, Sec. A.2).  The entry and
-// exit planes of a voxel follow from the sign bits, so the slab test is six
-// multiplies by 1/r_d and four min/max.
+// Work is split into items of (tile, 8x4 pixel block): 8 items per 16x16
+// tile.  A persistent grid of warps pulls items from a device counter in the
+// order of k_tile_order (longest tile lists first, so the heavy tiles do not
+// form the tail).  A warp walks its tile's sorted list by itself, 32 entries
+// per batch, with no CTA-wide barrier: lane j reads entry j of the batch (its
+// value, then the voxel's conservative pixel box); the warp keeps the entries
+// whose sign pattern one of its pixels has (Sec. B.1) and whose box meets its
+// block, and stages them, ballot-compacted in list order, into its shared
+// memory slots from the voxel's 64-byte record.
+//
+// Each batch then runs in two phases.  Phase A: every pixel tests all staged
+// entries (broadcast reads): same sign bits, pixel inside the box, and the
+// ray-AABB slab test of Sec. A.2 (entry and exit planes follow from the sign
+// bits: 6 multiplies by 1/r_d and 4 min/max), and records its hits as a bit
+// mask.  Phase B: in rounds, every pixel with hits left composites its next
+// hit, so the lanes of a warp run the costly per-hit arithmetic together
+// instead of one voxel at a time.
 //
 // Forward (Sec. 3.1.2, Eq. alpha_blend, Eq. supp_alpha_comp, Sec. A.4):
 //   K samples per segment, trilinear raw density, explin, per-sample
 //   e_k = exp(-(l/K) explin(v_k)); 1 - alpha = prod_k e_k; local depth
 //   d = sum_k prod_{j<k} e_j (1 - e_k) t_k; C += T alpha c, D += T d,
-//   T *= 1 - alpha; the warp's pixels stop after the voxel that leaves
-//   T < t_stop and the CTA leaves the list once all its pixels stopped.
+//   T *= 1 - alpha; a pixel stops after the voxel that leaves T < t_stop and
+//   the warp leaves the list once all its pixels stopped.
 //
 // Backward, back to front from the saved (T_final, last).  With x_i the
 // optical depth of voxel i (T_{i+1} = T_i exp(-x_i)) and, accumulated from
@@ -26,28 +35,36 @@
 //                the general form of the K <= 3 closed forms of Sec. A.4),
 //   dx_ik/dv_k = (l/K) explin'(v_k), dv_k/dV_c = trilinear weight of corner c.
 // T_i is recovered as T_{i+1} / exp(-x_i).  Pixels whose T_final is below
-// 1e-30 (where that division loses precision) take a front-to-back second
-// phase instead, with SC_i, SD_i from totals recomputed in a first sweep.
-// The per-voxel gradients (8 corner densities, 3 colour channels) of the
-// lanes that hit the same entry are summed in the warp before the atomics.
+// 1e-30 (where that division loses precision) take a front-to-back phase
+// instead, with SC_i, SD_i from totals recomputed in a first sweep.  The
+// per-voxel gradients (8 corner densities, 3 colour channels) of all the
+// warp's pixels are summed per staged entry in shared memory, and each entry
+// that was hit is added to the global accumulators once per warp.
 #include "svr_internal.cuh"
 
 namespace svr {
 
-constexpr int kChunk = 256;
+constexpr int kBlocksPerTile = 8;  // 8x4 pixel blocks of a 16x16 tile: the work items
+constexpr int kWarps = 8;          // warps per CTA of the forward
+constexpr int kThreads = kWarps * 32;
+constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
+constexpr int kBwdThreads = kBwdWarps * 32;
+constexpr int kBatch = 32;
+constexpr int kAccStride = 13;  // floats per staged entry's gradient row (odd: no bank conflicts)
 
-// Staged entry (96 bytes).  a/b hold the entry (near) and exit (far) planes
-// relative to the ray origin for the entry's sign pattern; s rides in a.w.
+// Staged list entry (112 bytes).
 struct Entry {
-    float4 a;   // near.xyz, sign bits (int)
-    float4 b;   // far.xyz, 1 / size
-    float4 c;   // (lo - r_o) / size, voxel id (int)
-    float4 g0;  // corner densities 0..3
-    float4 g1;  // corner densities 4..7
-    float4 col; // colour, clamp bits
+    float4 a;    // entry plane (near corner) relative to r_o, sign bits (int)
+    float4 b;    // exit plane (far corner) relative to r_o, 1 / size
+    float4 c;    // (min corner - r_o) / size, index in the sorted list (int)
+    float4 g0;   // raw corner densities 0..3
+    float4 g1;   // raw corner densities 4..7
+    float4 col;  // colour, voxel id (int)
+    int4 box;    // pixel box x0, x1, y0, y1 (inclusive)
 };
 
-__device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, const Record *__restrict__ rec) {
+__device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, ushort4 bx,
+                                            const Record *__restrict__ rec) {
     const uint32_t s = val >> 29;
     const uint32_t vid = val & 0x1FFFFFFFu;
     const Record *r = rec + vid;
@@ -57,10 +74,12 @@ __device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, const Record
     const float inv = 1.0f / size;
     e.a = make_float4((s & 4) ? hx : lx, (s & 2) ? hy : ly, (s & 1) ? hz : lz, __int_as_float((int)s));
     e.b = make_float4((s & 4) ? lx : hx, (s & 2) ? ly : hy, (s & 1) ? lz : hz, inv);
-    e.c = make_float4(lx * inv, ly * inv, lz * inv, __int_as_float((int)vid));
+    e.c = make_float4(lx * inv, ly * inv, lz * inv, __int_as_float(idx));
     e.g0 = __ldg(&r->r1);
     e.g1 = __ldg(&r->r2);
-    e.col = __ldg(&r->r3);
+    const float4 c3 = __ldg(&r->r3);
+    e.col = make_float4(c3.x, c3.y, c3.z, __int_as_float((int)vid));
+    e.box = make_int4(bx.x, bx.y, bx.z, bx.w);
 }
 
 // Trilinear interpolation of Eq. interp; corner bits (x, y, z), x most significant.
@@ -82,19 +101,33 @@ struct PixelRay {
     bool inside;
 };
 
-__device__ __forceinline__ PixelRay pixel_ray(const DevCam &cam, int tile) {
+struct WarpBlock {
+    int x0, y0;      // origin of the warp's 8x4 pixel block
+    unsigned smask;  // bit s set if one of its in-image pixels has sign bits s
+};
+
+__device__ __forceinline__ PixelRay pixel_ray(const DevCam &cam, int tile, int blk, WarpBlock &wb) {
     PixelRay p;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    p.x = tx * 16 + (warp & 1) * 8 + (lane & 7);
-    p.y = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+    const int lane = threadIdx.x & 31;
+    wb.x0 = tx * 16 + (blk & 1) * 8;
+    wb.y0 = ty * 16 + (blk >> 1) * 4;
+    p.x = wb.x0 + (lane & 7);
+    p.y = wb.y0 + (lane >> 3);
     p.inside = p.x < cam.W && p.y < cam.H;
     p.rd = pixel_dir(cam, p.x, p.y);
     p.s = sign_bits(p.rd);
     // +0.0 for a zero component so that 1/r_d has the sign of the sign bits
     p.inv = make_float3(1.0f / (p.rd.x + 0.0f), 1.0f / (p.rd.y + 0.0f), 1.0f / (p.rd.z + 0.0f));
     p.rdn = sqrtf(p.rd.x * p.rd.x + p.rd.y * p.rd.y + p.rd.z * p.rd.z);
+    wb.smask = __reduce_or_sync(0xffffffffu, p.inside ? (1u << p.s) : 0u);
     return p;
+}
+
+// Same sign bits and pixel inside the entry's box: the entry can be hit.
+__device__ __forceinline__ bool may_hit(const Entry &e, const PixelRay &p) {
+    return __float_as_int(e.a.w) == p.s && (unsigned)(p.x - e.box.x) <= (unsigned)(e.box.y - e.box.x) &&
+           (unsigned)(p.y - e.box.z) <= (unsigned)(e.box.w - e.box.z);
 }
 
 // Slab test against a staged entry whose sign bits match the ray's.
@@ -104,9 +137,78 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
     return a <= b && a > 0.f;
 }
 
+// One batch of the warp's walk: lane j looks at list entry idx (if valid),
+// keeps it if the warp can use it and stages it at its rank among the kept
+// lanes.  Returns the number of staged entries (list order by lane).
+__device__ __forceinline__ int stage_batch(Entry *st, const FrameDev &f, const uint32_t *__restrict__ vals,
+                                           int idx, bool valid, const WarpBlock &wb) {
+    bool keep = false;
+    uint32_t val = 0;
+    ushort4 bx = make_ushort4(0, 0, 0, 0);
+    if (valid) {
+        val = __ldg(vals + idx);
+        if ((wb.smask >> (val >> 29)) & 1u) {
+            bx = __ldg(f.box + (val & 0x1FFFFFFFu));
+            keep = bx.x <= wb.x0 + 7 && bx.y >= wb.x0 && bx.z <= wb.y0 + 3 && bx.w >= wb.y0;
+        }
+    }
+    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+        stage_entry(st[__popc(kb & lt)], val, idx, bx, f.rec);
+    }
+    __syncwarp();
+    return __popc(kb);
+}
+
+// Software-pipelined walk: the value and the pixel box of the next batch's
+// entry are fetched while the current batch is staged and composited, so a
+// batch waits on one dependent load (the record) instead of three.
+struct Lookahead {
+    uint32_t val;
+    ushort4 box;
+    bool want;  // valid entry whose sign pattern the warp has
+};
+
+__device__ __forceinline__ void fetch_val(Lookahead &la, const uint32_t *__restrict__ vals, int idx, bool valid,
+                                          const WarpBlock &wb) {
+    la.val = valid ? __ldg(vals + idx) : 0u;
+    la.want = valid && ((wb.smask >> (la.val >> 29)) & 1u);
+}
+
+__device__ __forceinline__ void fetch_box(Lookahead &la, const FrameDev &f) {
+    la.box = la.want ? __ldg(f.box + (la.val & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
+}
+
+// Stage the looked-ahead entries (index idx per lane) that the warp keeps.
+__device__ __forceinline__ int stage_ahead(Entry *st, const FrameDev &f, const Lookahead &la, int idx,
+                                           const WarpBlock &wb) {
+    const bool keep = la.want && la.box.x <= wb.x0 + 7 && la.box.y >= wb.x0 && la.box.z <= wb.y0 + 3 &&
+                      la.box.w >= wb.y0;
+    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+        stage_entry(st[__popc(kb & lt)], la.val, idx, la.box, f.rec);
+    }
+    __syncwarp();
+    return __popc(kb);
+}
+
+// Next work item (tile, block) of the calling warp, or false when done.
+__device__ __forceinline__ bool next_item(unsigned *counter, unsigned n_items, const uint32_t *order, int &tile,
+                                          int &blk) {
+    unsigned item = 0;
+    if ((threadIdx.x & 31) == 0) item = atomicAdd(counter, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) return false;
+    tile = (int)order[item / kBlocksPerTile];
+    blk = (int)(item % kBlocksPerTile);
+    return true;
+}
+
 // ------------------------------------------------------------------ forward
 
-// Local depth and transmittance factor of a hit (forward recompute).
+// Local depth and transmittance factor of a hit.
 template <int K>
 __device__ __forceinline__ void hit_fwd(const Entry &e, const PixelRay &p, float a, float b, float &trans,
                                         float &dloc) {
@@ -130,37 +232,55 @@ __device__ __forceinline__ void hit_fwd(const Entry &e, const PixelRay &p, float
     dloc = d;
 }
 
+struct FwdOut {
+    float *rgb, *depth, *alpha, *T;
+    int32_t *last;
+    int2 *stats;
+};
 
-// STATS: also count, per pixel, the list entries with its sign bits that it
-// examined and the hits it composited (int2 per pixel), for work accounting.
 template <int K, bool STATS>
-__global__ void __launch_bounds__(kChunk) k_render_fwd(FrameDev f, const uint32_t *__restrict__ vals,
-                                                       float *__restrict__ out_rgb, float *__restrict__ out_depth,
-                                                       float *__restrict__ out_alpha, float *__restrict__ out_T,
-                                                       int32_t *__restrict__ out_last, int2 *__restrict__ stats) {
-    __shared__ Entry ent[kChunk];
-    const int tile = blockIdx.x;
-    const PixelRay p = pixel_ray(f.cam, tile);
+__device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int tile, int blk,
+                                          Entry *st, const FwdOut &out) {
+    WarpBlock wb;
+    const PixelRay p = pixel_ray(f.cam, tile, blk, wb);
+    if (wb.smask == 0) return;  // the whole block lies outside the image
     const uint2 rg = f.ranges[tile];
     const int beg = (int)rg.x, end = (int)rg.y;
+    const int lane = threadIdx.x & 31;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int last = end - 1;
     bool done = !p.inside;
     int n_cand = 0, n_hit = 0;
 
-    for (int base = beg; base < end; base += kChunk) {
-        if (__syncthreads_count(!done) == 0) break;
-        const int i = base + threadIdx.x;
-        if (i < end) stage_entry(ent[threadIdx.x], vals[i], f.rec);
-        __syncthreads();
-        const int n = min(kChunk, end - base);
+    Lookahead la;
+    fetch_val(la, vals, beg + lane, beg + lane < end, wb);
+    fetch_box(la, f);
+    for (int base = beg; base < end; base += kBatch) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const Lookahead cur = la;
+        const int nidx = base + kBatch + lane;
+        fetch_val(la, vals, nidx, nidx < end, wb);
+        const int n = stage_ahead(st, f, cur, base + lane, wb);
+        fetch_box(la, f);
+        // phase A: this pixel's hits among the staged entries
+        unsigned hits = 0;
         if (!done) {
-            for (int j = 0; j < n; ++j) {
-                const Entry &e = ent[j];
-                if (__float_as_int(e.a.w) != p.s) continue;
+            for (int k = 0; k < n; ++k) {
+                const Entry &e = st[k];
+                if (!may_hit(e, p)) continue;
                 if (STATS) ++n_cand;
                 float a, b;
-                if (!slab(e, p, a, b)) continue;
+                if (slab(e, p, a, b)) hits |= 1u << k;
+            }
+        }
+        // phase B: composite them in list order, one hit per pixel per round
+        while (__any_sync(0xffffffffu, hits != 0)) {
+            if (hits != 0) {
+                const int k = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const Entry &e = st[k];
+                float a, b;
+                slab(e, p, a, b);
                 if (STATS) ++n_hit;
                 float P, dloc;
                 hit_fwd<K>(e, p, a, b, P, dloc);
@@ -172,23 +292,39 @@ __global__ void __launch_bounds__(kChunk) k_render_fwd(FrameDev f, const uint32_
                 T *= P;
                 if (T < f.t_stop) {
                     done = true;
-                    last = base + j;
-                    break;
+                    last = __float_as_int(e.c.w);
+                    hits = 0;
                 }
             }
         }
+        __syncwarp();
     }
     if (p.inside) {
         const size_t HW = (size_t)f.cam.W * f.cam.H;
         const size_t o = (size_t)p.y * f.cam.W + p.x;
-        out_rgb[o] = fmaf(T, f.bg[0], C0);
-        out_rgb[HW + o] = fmaf(T, f.bg[1], C1);
-        out_rgb[2 * HW + o] = fmaf(T, f.bg[2], C2);
-        out_depth[o] = D;
-        out_alpha[o] = 1.f - T;
-        out_T[o] = T;
-        out_last[o] = last;
-        if (STATS) stats[o] = make_int2(n_cand, n_hit);
+        out.rgb[o] = fmaf(T, f.bg[0], C0);
+        out.rgb[HW + o] = fmaf(T, f.bg[1], C1);
+        out.rgb[2 * HW + o] = fmaf(T, f.bg[2], C2);
+        out.depth[o] = D;
+        out.alpha[o] = 1.f - T;
+        out.T[o] = T;
+        out.last[o] = last;
+        if (STATS) out.stats[o] = make_int2(n_cand, n_hit);
+    }
+}
+
+// STATS: also count, per pixel, the list entries with its sign bits whose
+// pixel box contains it (the slab tests it must make) and the hits it
+// composited (int2 per pixel), for work accounting.
+template <int K, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_render_fwd(FrameDev f, const uint32_t *__restrict__ vals, FwdOut out) {
+    __shared__ Entry stage[kWarps][kBatch];
+    Entry *st = stage[threadIdx.x >> 5];
+    const unsigned n_items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    int tile, blk;
+    while (next_item(&f.status->fwd_next, n_items, f.tile_order, tile, blk)) {
+        fwd_block<K, STATS>(f, vals, tile, blk, st, out);
+        __syncwarp();
     }
 }
 
@@ -199,13 +335,17 @@ struct PixelGrad {
     float Tfin;
 };
 
-// Gradient contributions of one hit.  T_i: transmittance in front of the
-// voxel; T_after = T_i * prod_k e_k; SC, SD: sums behind it.  Adds the local
-// quantities the caller needs to update its suffix or prefix sums.
-template <int K>
+// Gradient contributions of one hit, computed from one pass over its K
+// samples.  B2F: T_known is the transmittance behind the voxel (T_{i+1}) and
+// SC, SD the sums strictly behind it.  Front to back: T_known is T_i and
+// SC, SD are the sums behind AND including the voxel (total minus the
+// prefix before it); the voxel's own share is removed here.  Returns the
+// transmittance in front of the voxel (T_i) and behind it (T_{i+1}), its
+// blending weight and local depth.
+template <int K, bool B2F>
 __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, const PixelGrad &g, float a, float b,
-                                         float T_i, float T_after, const float SC[3], float SD, float dgeo[8],
-                                         float dcol[3]) {
+                                         float T_known, float SC0, float SC1, float SC2, float SD, float dgeo[8],
+                                         float dcol[3], float &T_i, float &T_after, float &w, float &dloc) {
     const float inv_k = 1.0f / K;
     const float seg = b - a;
     const float xs = seg * p.rdn * inv_k;
@@ -214,6 +354,7 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     const float rx = p.rd.x * inv_size, ry = p.rd.y * inv_size, rz = p.rd.z * inv_size;
     float tk[K], ek[K], qx[K], qy[K], qz[K], dsig[K];
     float t = fmaf(0.5f, step, a);
+    float trans = 1.f, d = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         qx[k] = fmaf(t, rx, -e.c.x);
@@ -224,19 +365,31 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
         dsig[k] = v > 1.1f ? 1.f : sig * 0.909090909f;
         ek[k] = __expf(-xs * sig);
         tk[k] = t;
+        d = fmaf(trans * (1.f - ek[k]), t, d);
+        trans *= ek[k];
         t += step;
     }
-    float trans = 1.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) trans *= ek[k];
-    const float alpha = 1.f - trans;
-    const float w = T_i * alpha;
+    if (B2F) {
+        T_after = T_known;
+        T_i = T_known / trans;
+    } else {
+        T_i = T_known;
+        T_after = T_known * trans;
+    }
+    w = T_i * (1.f - trans);
+    dloc = d;
+    if (!B2F) {
+        SC0 -= w * e.col.x;
+        SC1 -= w * e.col.y;
+        SC2 -= w * e.col.z;
+        SD -= T_i * d;
+    }
     dcol[0] = w * g.gC0;
     dcol[1] = w * g.gC1;
     dcol[2] = w * g.gC2;
     // dL/dx_i through C, A and the transmittance of later voxels in D
-    const float gx = g.gC0 * fmaf(T_after, e.col.x, -SC[0]) + g.gC1 * fmaf(T_after, e.col.y, -SC[1]) +
-                     g.gC2 * fmaf(T_after, e.col.z, -SC[2]) + g.gA * g.Tfin - g.gD * SD;
+    const float gx = g.gC0 * fmaf(T_after, e.col.x, -SC0) + g.gC1 * fmaf(T_after, e.col.y, -SC1) +
+                     g.gC2 * fmaf(T_after, e.col.z, -SC2) + g.gA * g.Tfin - g.gD * SD;
     // per-sample depth term, suffix Q_k = sum_{m>k} P_m (1 - e_m) t_m
     float Pk[K + 1];
     Pk[0] = 1.f;
@@ -245,9 +398,10 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     float Q = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) dgeo[c] = 0.f;
+    const float gdT = g.gD * T_i;
 #pragma unroll
     for (int k = K - 1; k >= 0; --k) {
-        const float gxk = fmaf(g.gD * T_i, fmaf(Pk[k + 1], tk[k], -Q), gx);
+        const float gxk = fmaf(gdT, fmaf(Pk[k + 1], tk[k], -Q), gx);
         const float dv = gxk * xs * dsig[k];
         const float ux = 1.f - qx[k], uy = 1.f - qy[k], uz = 1.f - qz[k];
         const float w00 = ux * uy, w01 = ux * qy[k], w10 = qx[k] * uy, w11 = qx[k] * qy[k];
@@ -263,254 +417,371 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     }
 }
 
-// Sum the 11 gradient values over the lanes that hit the entry and add them
-// to the global accumulators.
-__device__ __forceinline__ void flush_grad(bool hit, float dgeo[8], float dcol[3], const int32_t *__restrict__ cidx,
-                                           int vid, float *__restrict__ d_grid, float *__restrict__ acc_col) {
-    const unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (m == 0) return;
+// Add this round's per-lane gradients (lane hit staged entry k, or k < 0) to
+// the entries' rows.  Lanes on the same entry form a group (warp match); a
+// lane alone on its entry adds its values directly, a larger group goes
+// through the scratch rows and its first lane sums them.  No two groups share
+// a row, so plain shared-memory loads and stores suffice.
+__device__ __forceinline__ void acc_group_add(float *acc, float *scratch, int k, const float dgeo[8],
+                                              const float dcol[3]) {
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
     const int lane = threadIdx.x & 31;
-    if (__popc(m) == 1) {
-        if (hit) {
+    const bool solo = (peers & (peers - 1u)) == 0u;
+    if (k >= 0 && !solo) {
+        float *s = scratch + lane * kAccStride;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) atomicAdd(d_grid + __ldg(cidx + c), dgeo[c]);
-            atomicAdd(acc_col + 3 * vid + 0, dcol[0]);
-            atomicAdd(acc_col + 3 * vid + 1, dcol[1]);
-            atomicAdd(acc_col + 3 * vid + 2, dcol[2]);
+        for (int c = 0; c < 8; ++c) s[c] = dgeo[c];
+        s[8] = dcol[0];
+        s[9] = dcol[1];
+        s[10] = dcol[2];
+    }
+    __syncwarp();
+    if (k >= 0) {
+        float *row = acc + k * kAccStride;
+        if (solo) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) row[c] += dgeo[c];
+            row[8] += dcol[0];
+            row[9] += dcol[1];
+            row[10] += dcol[2];
+        } else if (lane == __ffs(peers) - 1) {
+            float sum[11];
+#pragma unroll
+            for (int c = 0; c < 11; ++c) sum[c] = 0.f;
+            for (unsigned m = peers; m; m &= m - 1u) {
+                const float *s = scratch + (__ffs(m) - 1) * kAccStride;
+#pragma unroll
+                for (int c = 0; c < 11; ++c) sum[c] += s[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 11; ++c) row[c] += sum[c];
         }
-        return;
     }
-    if (!hit) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) dgeo[c] = 0.f;
-        dcol[0] = dcol[1] = dcol[2] = 0.f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) dgeo[c] += __shfl_xor_sync(0xffffffffu, dgeo[c], o);
-        dcol[0] += __shfl_xor_sync(0xffffffffu, dcol[0], o);
-        dcol[1] += __shfl_xor_sync(0xffffffffu, dcol[1], o);
-        dcol[2] += __shfl_xor_sync(0xffffffffu, dcol[2], o);
-    }
-    if (lane == __ffs(m) - 1) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) atomicAdd(d_grid + __ldg(cidx + c), dgeo[c]);
-        atomicAdd(acc_col + 3 * vid + 0, dcol[0]);
-        atomicAdd(acc_col + 3 * vid + 1, dcol[1]);
-        atomicAdd(acc_col + 3 * vid + 2, dcol[2]);
-    }
+    __syncwarp();
 }
 
+// Zero the gradient rows of the staged entries that some pixel hits.
+__device__ __forceinline__ void acc_clear(float *acc, int n, unsigned any_hit) {
+    const int lane = threadIdx.x & 31;
+    if (lane < n && ((any_hit >> lane) & 1u)) {
+        float *row = acc + lane * kAccStride;
+#pragma unroll
+        for (int c = 0; c < 11; ++c) row[c] = 0.f;
+    }
+    __syncwarp();
+}
+
+// Add each hit entry's summed row to the global accumulators (lane j: entry j).
+__device__ __forceinline__ void acc_flush(const float *acc, const Entry *st, int n, unsigned any_hit,
+                                          const int32_t *__restrict__ corner_idx, float *__restrict__ d_grid,
+                                          float *__restrict__ acc_col) {
+    const int lane = threadIdx.x & 31;
+    if (lane < n && ((any_hit >> lane) & 1u)) {
+        const float *row = acc + lane * kAccStride;
+        const int vid = __float_as_int(st[lane].col.w);
+        const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
+        const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
+        atomicAdd(d_grid + i0.x, row[0]);
+        atomicAdd(d_grid + i0.y, row[1]);
+        atomicAdd(d_grid + i0.z, row[2]);
+        atomicAdd(d_grid + i0.w, row[3]);
+        atomicAdd(d_grid + i1.x, row[4]);
+        atomicAdd(d_grid + i1.y, row[5]);
+        atomicAdd(d_grid + i1.z, row[6]);
+        atomicAdd(d_grid + i1.w, row[7]);
+        atomicAdd(acc_col + 3 * (size_t)vid + 0, row[8]);
+        atomicAdd(acc_col + 3 * (size_t)vid + 1, row[9]);
+        atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
+    }
+    __syncwarp();
+}
+
+struct BwdIn {
+    const float *d_rgb, *d_depth, *d_alpha, *T;
+    const int32_t *last;
+    float *d_grid;
+};
+
 template <int K>
-__global__ void __launch_bounds__(kChunk) k_render_bwd(FrameDev f, const uint32_t *__restrict__ vals,
-                                                       const float *__restrict__ d_rgb,
-                                                       const float *__restrict__ d_depth,
-                                                       const float *__restrict__ d_alpha,
-                                                       const float *__restrict__ in_T,
-                                                       const int32_t *__restrict__ in_last,
-                                                       float *__restrict__ d_grid) {
-    __shared__ Entry ent[kChunk];
-    __shared__ int max_last;
-    const int tile = blockIdx.x;
-    const PixelRay p = pixel_ray(f.cam, tile);
+__device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int tile, int blk,
+                                          Entry *st, float *acc, float *scratch, const BwdIn &in) {
+    WarpBlock wb;
+    const PixelRay p = pixel_ray(f.cam, tile, blk, wb);
+    if (wb.smask == 0) return;
     const uint2 rg = f.ranges[tile];
     const int beg = (int)rg.x;
+    const int lane = threadIdx.x & 31;
     const size_t HW = (size_t)f.cam.W * f.cam.H;
     const size_t o = (size_t)p.y * f.cam.W + p.x;
 
     PixelGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
     int last = beg - 1;
     if (p.inside) {
-        if (d_rgb) {
-            g.gC0 = d_rgb[o];
-            g.gC1 = d_rgb[HW + o];
-            g.gC2 = d_rgb[2 * HW + o];
+        if (in.d_rgb) {
+            g.gC0 = in.d_rgb[o];
+            g.gC1 = in.d_rgb[HW + o];
+            g.gC2 = in.d_rgb[2 * HW + o];
         }
-        if (d_depth) g.gD = d_depth[o];
-        if (d_alpha) g.gA = d_alpha[o];
-        g.Tfin = in_T[o];
-        last = max(beg - 1, min(in_last[o], (int)rg.y - 1));   // stay inside the tile's list
+        if (in.d_depth) g.gD = in.d_depth[o];
+        if (in.d_alpha) g.gA = in.d_alpha[o];
+        g.Tfin = in.T[o];
+        last = max(beg - 1, min(in.last[o], (int)rg.y - 1));   // stay inside the tile's list
     }
     const bool fallback = p.inside && last >= beg && g.Tfin < 1e-30f;
     const bool active = p.inside && last >= beg && !fallback;
 
-    if (threadIdx.x == 0) max_last = beg - 1;
-    __syncthreads();
-    if (p.inside && last >= beg) atomicMax(&max_last, last);
-    __syncthreads();
-    const int hi_all = max_last + 1;
-
     // ---- back to front
-    float T_after = g.Tfin;
-    float SC[3] = {g.Tfin * f.bg[0], g.Tfin * f.bg[1], g.Tfin * f.bg[2]};
-    float SD = 0.f;
-    for (int hi = hi_all; hi > beg; hi -= kChunk) {
-        const int lo = max(beg, hi - kChunk);
-        __syncthreads();
-        const int i = lo + threadIdx.x;
-        if (i < hi) stage_entry(ent[threadIdx.x], vals[i], f.rec);
-        __syncthreads();
-        for (int j = hi - 1 - lo; j >= 0; --j) {
-            const Entry &e = ent[j];
-            float a = 0.f, b = 0.f;
-            const bool hit = active && (lo + j) <= last && __float_as_int(e.a.w) == p.s && slab(e, p, a, b);
-            float dgeo[8], dcol[3];
-            if (hit) {
-                float trans, dloc;
-                hit_fwd<K>(e, p, a, b, trans, dloc);
-                const float T_i = T_after / trans;
-                hit_grad<K>(e, p, g, a, b, T_i, T_after, SC, SD, dgeo, dcol);
-                const float w = T_i * (1.f - trans);
-                SC[0] = fmaf(w, e.col.x, SC[0]);
-                SC[1] = fmaf(w, e.col.y, SC[1]);
-                SC[2] = fmaf(w, e.col.z, SC[2]);
-                SD = fmaf(T_i, dloc, SD);
-                T_after = T_i;
+    {
+        const int hi = __reduce_max_sync(0xffffffffu, active ? last + 1 : beg);
+        float T_after = g.Tfin;
+        float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
+        Lookahead la;
+        fetch_val(la, vals, hi - 1 - lane, hi - 1 - lane >= beg, wb);
+        fetch_box(la, f);
+        for (int top = hi; top > beg; top -= kBatch) {
+            const Lookahead cur = la;
+            const int nidx = top - 1 - kBatch - lane;
+            fetch_val(la, vals, nidx, nidx >= beg, wb);
+            const int n = stage_ahead(st, f, cur, top - 1 - lane, wb);
+            fetch_box(la, f);
+            unsigned hits = 0;
+            if (active) {
+                for (int k = 0; k < n; ++k) {
+                    const Entry &e = st[k];
+                    float a, b;
+                    if (__float_as_int(e.c.w) <= last && may_hit(e, p) && slab(e, p, a, b)) hits |= 1u << k;
+                }
             }
-            const int vid = __float_as_int(e.c.w);
-            flush_grad(hit, dgeo, dcol, f.corner_idx + 8 * (size_t)vid, vid, d_grid, f.dcol);
+            const unsigned any_hit = __reduce_or_sync(0xffffffffu, hits);
+            if (any_hit) {
+                acc_clear(acc, n, any_hit);
+                while (__any_sync(0xffffffffu, hits != 0)) {
+                    int k = -1;
+                    float dgeo[8], dcol[3];
+                    if (hits != 0) {
+                        k = __ffs(hits) - 1;   // staged in decreasing list order
+                        hits &= hits - 1;
+                        const Entry &e = st[k];
+                        float a, b;
+                        slab(e, p, a, b);
+                        float T_i, Ta, w, dloc;
+                        hit_grad<K, true>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, dgeo, dcol, T_i, Ta, w, dloc);
+                        SC0 = fmaf(w, e.col.x, SC0);
+                        SC1 = fmaf(w, e.col.y, SC1);
+                        SC2 = fmaf(w, e.col.z, SC2);
+                        SD = fmaf(T_i, dloc, SD);
+                        T_after = T_i;
+                    }
+                    acc_group_add(acc, scratch, k, dgeo, dcol);
+                }
+                __syncwarp();
+                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, f.dcol);
+            }
+            __syncwarp();
         }
     }
 
     // ---- front to back for pixels whose T_final underflowed
-    if (__syncthreads_or(fallback)) {
+    if (__any_sync(0xffffffffu, fallback)) {
+        const int hi = __reduce_max_sync(0xffffffffu, fallback ? last + 1 : beg);
         // sweep 1: totals
-        float T = 1.f, Ct[3] = {0.f, 0.f, 0.f}, Dt = 0.f;
-        for (int lo = beg; lo < hi_all; lo += kChunk) {
-            const int hi = min(hi_all, lo + kChunk);
-            __syncthreads();
-            const int i = lo + threadIdx.x;
-            if (i < hi) stage_entry(ent[threadIdx.x], vals[i], f.rec);
-            __syncthreads();
+        float T = 1.f, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
+        for (int base = beg; base < hi; base += kBatch) {
+            const int idx = base + lane;
+            const int n = stage_batch(st, f, vals, idx, idx < hi, wb);
             if (fallback) {
-                for (int j = 0; j < hi - lo && lo + j <= last; ++j) {
-                    const Entry &e = ent[j];
+                for (int k = 0; k < n; ++k) {
+                    const Entry &e = st[k];
                     float a, b;
-                    if (__float_as_int(e.a.w) != p.s || !slab(e, p, a, b)) continue;
+                    if (__float_as_int(e.c.w) > last || !may_hit(e, p) || !slab(e, p, a, b)) continue;
                     float trans, dloc;
                     hit_fwd<K>(e, p, a, b, trans, dloc);
                     const float w = T * (1.f - trans);
-                    Ct[0] = fmaf(w, e.col.x, Ct[0]);
-                    Ct[1] = fmaf(w, e.col.y, Ct[1]);
-                    Ct[2] = fmaf(w, e.col.z, Ct[2]);
+                    Ct0 = fmaf(w, e.col.x, Ct0);
+                    Ct1 = fmaf(w, e.col.y, Ct1);
+                    Ct2 = fmaf(w, e.col.z, Ct2);
                     Dt = fmaf(T, dloc, Dt);
                     T *= trans;
                 }
             }
+            __syncwarp();
         }
-        Ct[0] = fmaf(T, f.bg[0], Ct[0]);
-        Ct[1] = fmaf(T, f.bg[1], Ct[1]);
-        Ct[2] = fmaf(T, f.bg[2], Ct[2]);
-        // sweep 2: gradients with SC = total - prefix
-        float Tf = 1.f, PC[3] = {0.f, 0.f, 0.f}, PD = 0.f;
-        for (int lo = beg; lo < hi_all; lo += kChunk) {
-            const int hi = min(hi_all, lo + kChunk);
-            __syncthreads();
-            const int i = lo + threadIdx.x;
-            if (i < hi) stage_entry(ent[threadIdx.x], vals[i], f.rec);
-            __syncthreads();
-            for (int j = 0; j < hi - lo; ++j) {
-                const Entry &e = ent[j];
-                float a = 0.f, b = 0.f;
-                const bool hit = fallback && (lo + j) <= last && __float_as_int(e.a.w) == p.s && slab(e, p, a, b);
-                float dgeo[8], dcol[3];
-                if (hit) {
-                    float trans, dloc;
-                    hit_fwd<K>(e, p, a, b, trans, dloc);
-                    const float w = Tf * (1.f - trans);
-                    PC[0] = fmaf(w, e.col.x, PC[0]);
-                    PC[1] = fmaf(w, e.col.y, PC[1]);
-                    PC[2] = fmaf(w, e.col.z, PC[2]);
-                    PD = fmaf(Tf, dloc, PD);
-                    const float SCi[3] = {Ct[0] - PC[0], Ct[1] - PC[1], Ct[2] - PC[2]};
-                    const float Ta = Tf * trans;
-                    hit_grad<K>(e, p, g, a, b, Tf, Ta, SCi, Dt - PD, dgeo, dcol);
-                    Tf = Ta;
+        Ct0 = fmaf(T, f.bg[0], Ct0);
+        Ct1 = fmaf(T, f.bg[1], Ct1);
+        Ct2 = fmaf(T, f.bg[2], Ct2);
+        // sweep 2: gradients with the sums behind = total - prefix
+        float Tf = 1.f, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
+        for (int base = beg; base < hi; base += kBatch) {
+            const int idx = base + lane;
+            const int n = stage_batch(st, f, vals, idx, idx < hi, wb);
+            unsigned hits = 0;
+            if (fallback) {
+                for (int k = 0; k < n; ++k) {
+                    const Entry &e = st[k];
+                    float a, b;
+                    if (__float_as_int(e.c.w) <= last && may_hit(e, p) && slab(e, p, a, b)) hits |= 1u << k;
                 }
-                const int vid = __float_as_int(e.c.w);
-                flush_grad(hit, dgeo, dcol, f.corner_idx + 8 * (size_t)vid, vid, d_grid, f.dcol);
             }
+            const unsigned any_hit = __reduce_or_sync(0xffffffffu, hits);
+            if (any_hit) {
+                acc_clear(acc, n, any_hit);
+                while (__any_sync(0xffffffffu, hits != 0)) {
+                    int k = -1;
+                    float dgeo[8], dcol[3];
+                    if (hits != 0) {
+                        k = __ffs(hits) - 1;   // staged in increasing list order
+                        hits &= hits - 1;
+                        const Entry &e = st[k];
+                        float a, b;
+                        slab(e, p, a, b);
+                        float T_i, Ta, w, dloc;
+                        hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo,
+                                           dcol, T_i, Ta, w, dloc);
+                        PC0 = fmaf(w, e.col.x, PC0);
+                        PC1 = fmaf(w, e.col.y, PC1);
+                        PC2 = fmaf(w, e.col.z, PC2);
+                        PD = fmaf(T_i, dloc, PD);
+                        Tf = Ta;
+                    }
+                    acc_group_add(acc, scratch, k, dgeo, dcol);
+                }
+                __syncwarp();
+                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, f.dcol);
+            }
+            __syncwarp();
         }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBwdThreads) k_render_bwd(FrameDev f, const uint32_t *__restrict__ vals,
+                                                            BwdIn in) {
+    __shared__ Entry stage[kBwdWarps][kBatch];
+    __shared__ float acc_all[kBwdWarps][kBatch * kAccStride];
+    __shared__ float scratch_all[kBwdWarps][32 * kAccStride];
+    const int warp = threadIdx.x >> 5;
+    Entry *st = stage[warp];
+    const unsigned n_items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    int tile, blk;
+    while (next_item(&f.status->bwd_next, n_items, f.tile_order, tile, blk)) {
+        bwd_block<K>(f, vals, tile, blk, st, acc_all[warp], scratch_all[warp], in);
+        __syncwarp();
     }
 }
 
 // Per voxel: dL/dsh[n][c] = Y_n(d) * dL/dc_c where the channel was > 0 before
-// the clamp (Eq. vox_color), zero for voxels not in view.
-__global__ void __launch_bounds__(256) k_voxel_bwd(FrameDev f, float *__restrict__ d_sh) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= f.n_vox) return;
-    float4 *out = reinterpret_cast<float4 *>(d_sh + 48 * v);
-    if (f.count[v] == 0) {
+// the clamp (Eq. vox_color), zero for voxels not in view.  Each thread builds
+// its voxel's 48 values in shared memory; the block then writes its rows
+// with consecutive threads on consecutive words.
+constexpr int kVoxBwdThreads = 128;
+
+__global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float *__restrict__ d_sh) {
+    __shared__ float rows[kVoxBwdThreads][49];
+    const int64_t v0 = (int64_t)blockIdx.x * kVoxBwdThreads;
+    const int64_t v = v0 + threadIdx.x;
+    if (v < f.n_vox) {
+        float *o = rows[threadIdx.x];
+        if (f.count[v] == 0) {
 #pragma unroll
-        for (int q = 0; q < 12; ++q) out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+            for (int i = 0; i < 48; ++i) o[i] = 0.f;
+        } else {
+            const unsigned bits = __float_as_uint(f.rec[v].r3.w);
+            const float g0 = (bits & 1u) ? f.dcol[3 * v + 0] : 0.f;
+            const float g1 = (bits & 2u) ? f.dcol[3 * v + 1] : 0.f;
+            const float g2 = (bits & 4u) ? f.dcol[3 * v + 2] : 0.f;
+            float dx = f.centre[3 * v + 0] - f.cam.ro[0];
+            float dy = f.centre[3 * v + 1] - f.cam.ro[1];
+            float dz = f.centre[3 * v + 2] - f.cam.ro[2];
+            const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+            float Y[16];
+            sh_basis(dx * inv, dy * inv, dz * inv, Y);
+#pragma unroll
+            for (int n = 0; n < 16; ++n) {
+                o[3 * n + 0] = Y[n] * g0;
+                o[3 * n + 1] = Y[n] * g1;
+                o[3 * n + 2] = Y[n] * g2;
+            }
+        }
     }
-    const unsigned bits = __float_as_uint(f.rec[v].r3.w);
-    const float g0 = (bits & 1u) ? f.dcol[3 * v + 0] : 0.f;
-    const float g1 = (bits & 2u) ? f.dcol[3 * v + 1] : 0.f;
-    const float g2 = (bits & 4u) ? f.dcol[3 * v + 2] : 0.f;
-    float dx = f.centre[3 * v + 0] - f.cam.ro[0];
-    float dy = f.centre[3 * v + 1] - f.cam.ro[1];
-    float dz = f.centre[3 * v + 2] - f.cam.ro[2];
-    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-    float Y[16];
-    sh_basis(dx * inv, dy * inv, dz * inv, Y);
-    float o[48];
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-        o[3 * n + 0] = Y[n] * g0;
-        o[3 * n + 1] = Y[n] * g1;
-        o[3 * n + 2] = Y[n] * g2;
-    }
-#pragma unroll
-    for (int q = 0; q < 12; ++q) out[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    __syncthreads();
+    const int nv = (int)tmin<int64_t>(kVoxBwdThreads, f.n_vox - v0);
+    float *out = d_sh + 48 * v0;
+    for (int i = threadIdx.x; i < nv * 48; i += kVoxBwdThreads) out[i] = rows[i / 48][i % 48];
 }
 
 // ---------------------------------------------------------------- launchers
 
+// Persistent grid: as many CTAs as fit on the device at once.
+template <class Kern>
+static unsigned persistent_grid(Kern kernel, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    if (sms <= 0) sms = 1;
+    if (per_sm <= 0) per_sm = 1;
+    return (unsigned)(sms * per_sm);
+}
+
+template <int K, bool ST>
+static cudaError_t fwd_k(const FrameDev &f, const uint32_t *vals, const FwdOut &out, cudaStream_t s) {
+    static unsigned grid = 0;
+    if (grid == 0) grid = persistent_grid(k_render_fwd<K, ST>, kThreads);
+    const unsigned items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    const unsigned g = tmin<unsigned>(grid, (items + kWarps - 1) / kWarps);
+    k_render_fwd<K, ST><<<g, kThreads, 0, s>>>(f, vals, out);
+    return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t bwd_k(const FrameDev &f, const uint32_t *vals, const BwdIn &in, cudaStream_t s) {
+    static unsigned grid = 0;
+    if (grid == 0) grid = persistent_grid(k_render_bwd<K>, kBwdThreads);
+    const unsigned items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    const unsigned g = tmin<unsigned>(grid, (items + kBwdWarps - 1) / kBwdWarps);
+    k_render_bwd<K><<<g, kBwdThreads, 0, s>>>(f, vals, in);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth, float *alpha,
                               float *T_final, int32_t *last, int2 *stats, cudaStream_t s) {
-    const int ntiles = f.cam.ntx * f.cam.nty;
     const uint32_t *vals = f.vals[sorted_alt];
-#define SVR_FWD(KK, ST) k_render_fwd<KK, ST><<<ntiles, kChunk, 0, s>>>(f, vals, rgb, depth, alpha, T_final, last, stats)
+    const FwdOut out = {rgb, depth, alpha, T_final, last, stats};
+    cudaError_t e = cudaMemsetAsync(&f.status->fwd_next, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     if (stats) {
         switch (f.K) {
-            case 1: SVR_FWD(1, true); break;
-            case 2: SVR_FWD(2, true); break;
-            case 3: SVR_FWD(3, true); break;
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (f.K) {
-            case 1: SVR_FWD(1, false); break;
-            case 2: SVR_FWD(2, false); break;
-            case 3: SVR_FWD(3, false); break;
+            case 1: return fwd_k<1, true>(f, vals, out, s);
+            case 2: return fwd_k<2, true>(f, vals, out, s);
+            case 3: return fwd_k<3, true>(f, vals, out, s);
             default: return cudaErrorInvalidValue;
         }
     }
-#undef SVR_FWD
-    return cudaGetLastError();
+    switch (f.K) {
+        case 1: return fwd_k<1, false>(f, vals, out, s);
+        case 2: return fwd_k<2, false>(f, vals, out, s);
+        case 3: return fwd_k<3, false>(f, vals, out, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_rgb, const float *d_depth,
                               const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
                               float *d_sh, cudaStream_t s) {
-    const int ntiles = f.cam.ntx * f.cam.nty;
     const uint32_t *vals = f.vals[sorted_alt];
-    cudaError_t e = cudaSuccess;
-    if (f.n_vox > 0) e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox, s);
+    cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess && f.n_vox > 0) e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox, s);
     if (e != cudaSuccess) return e;
+    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid};
     switch (f.K) {
-        case 1: k_render_bwd<1><<<ntiles, kChunk, 0, s>>>(f, vals, d_rgb, d_depth, d_alpha, T_final, last, d_grid); break;
-        case 2: k_render_bwd<2><<<ntiles, kChunk, 0, s>>>(f, vals, d_rgb, d_depth, d_alpha, T_final, last, d_grid); break;
-        case 3: k_render_bwd<3><<<ntiles, kChunk, 0, s>>>(f, vals, d_rgb, d_depth, d_alpha, T_final, last, d_grid); break;
+        case 1: e = bwd_k<1>(f, vals, in, s); break;
+        case 2: e = bwd_k<2>(f, vals, in, s); break;
+        case 3: e = bwd_k<3>(f, vals, in, s); break;
         default: return cudaErrorInvalidValue;
     }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (f.n_vox > 0) {
-        k_voxel_bwd<<<(unsigned)((f.n_vox + 255) / 256), 256, 0, s>>>(f, d_sh);
+        k_voxel_bwd<<<(unsigned)((f.n_vox + kVoxBwdThreads - 1) / kVoxBwdThreads), kVoxBwdThreads, 0, s>>>(f, d_sh);
         e = cudaGetLastError();
     }
     return e;

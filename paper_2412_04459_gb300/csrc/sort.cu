@@ -170,6 +170,38 @@ __global__ void k_tile_ranges(const uint64_t *__restrict__ keys, const Status *s
     }
 }
 
+// Render work order: tiles grouped by floor(log2(list length)), longest
+// lists first, so the heaviest tiles start early and the short ones fill the
+// tail (one block; order within a group is arbitrary, results do not depend
+// on it).
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, int ntiles,
+                                                     uint32_t *__restrict__ order) {
+    __shared__ unsigned cnt[33];
+    __shared__ unsigned start[33];
+    const int t = threadIdx.x;
+    if (t < 33) cnt[t] = 0;
+    __syncthreads();
+    for (int i = t; i < ntiles; i += blockDim.x) {
+        const uint2 r = ranges[i];
+        const unsigned len = r.y - r.x;
+        atomicAdd(&cnt[len ? 32 - __clz(len) : 0], 1u);
+    }
+    __syncthreads();
+    if (t == 0) {
+        unsigned acc = 0;
+        for (int b = 32; b >= 0; --b) {
+            start[b] = acc;
+            acc += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < ntiles; i += blockDim.x) {
+        const uint2 r = ranges[i];
+        const unsigned len = r.y - r.x;
+        order[atomicAdd(&start[len ? 32 - __clz(len) : 0], 1u)] = (uint32_t)i;
+    }
+}
+
 static int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -207,10 +239,12 @@ cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s) {
     const int ntiles = f.cam.ntx * f.cam.nty;
     cudaError_t e = cudaMemsetAsync(f.ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
     if (e != cudaSuccess) return e;
-    if (f.capacity == 0) return cudaSuccess;
-    const int64_t need = (f.capacity + 255) / 256;
-    const unsigned grid = (unsigned)tmin<int64_t>(need, (int64_t)sm_count() * 8);
-    k_tile_ranges<<<grid, 256, 0, s>>>(f.keys[sorted_alt], f.status, f.capacity, (uint32_t)ntiles, f.ranges);
+    if (f.capacity > 0) {
+        const int64_t need = (f.capacity + 255) / 256;
+        const unsigned grid = (unsigned)tmin<int64_t>(need, (int64_t)sm_count() * 8);
+        k_tile_ranges<<<grid, 256, 0, s>>>(f.keys[sorted_alt], f.status, f.capacity, (uint32_t)ntiles, f.ranges);
+    }
+    k_tile_order<<<1, 1024, 0, s>>>(f.ranges, ntiles, f.tile_order);
     return cudaGetLastError();
 }
 

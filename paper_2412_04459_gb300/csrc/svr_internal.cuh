@@ -40,7 +40,9 @@ struct Status {
     unsigned n_pairs_lo;  // total pair count (64-bit, split)
     unsigned n_pairs_hi;
     int bad_voxel;        // smallest invalid voxel id, or INT_MAX
-    unsigned pad[12];
+    unsigned fwd_next;    // next work item of the forward render (reset before each launch)
+    unsigned bwd_next;    // next work item of the backward render
+    unsigned pad[10];
 };
 
 // Per-voxel record of one view (64 bytes):
@@ -109,12 +111,14 @@ struct FrameDev {
     uint32_t *count;
     uint32_t *offset;
     Record *rec;
+    ushort4 *box;            // [N] inclusive pixel range x0, x1, y0, y1 a hit can fall in
     uint32_t *scan_blocks;   // [ceil(N / kScanTile)]
     uint64_t *keys[2];
     uint32_t *vals[2];
     uint32_t *hist;          // [256][capacity tiles]
     uint32_t *digit_tot;     // [256]
     uint2 *ranges;           // [ntiles]
+    uint32_t *tile_order;    // [ntiles] tiles by decreasing list length (render work order)
     float *dcol;             // [N][3] colour gradient accumulator
     int64_t n_vox;
     int64_t n_pts;

@@ -360,13 +360,15 @@ def frame_algorithmic_bytes(scene, P, H, W):
 
 
 def launches_per_step(fr):
-    """Kernels of ours launched per step (fills/memsets excluded)."""
-    nt = fr.frame.n_tiles_x * fr.frame.n_tiles_y
+    """Kernels of ours launched per step (fills/memsets excluded): tile masks,
+    preprocess, 3 scan kernels, emit, 3 per radix pass, ranges, tile order,
+    forward, backward, voxel backward."""
+    nt = int(fr.frame.total_tiles)
     tb = max(0, int(np.ceil(np.log2(nt)))) if nt > 1 else 0
     lmax = fr.scene.max_level
-    lo = 48 - 3 * (lmax + 1 if lmax < 16 else 16)
-    passes = (48 + tb - lo + 7) // 8 + (1 if lmax == 16 else 0)
-    return 2 + 4 + 3 * passes + 1 + 1 + 2
+    morton = 3 * (lmax + 1 if lmax < 16 else 16)
+    passes = (morton + tb + 7) // 8 + (1 if lmax == 16 else 0)
+    return 2 + 4 + 3 * passes + 2 + 1 + 2
 
 
 def load_peaks():

@@ -82,9 +82,12 @@ typedef struct svr_camera {
 typedef struct svr_params {
     int32_t K;      /* samples per ray segment, 1..3 (Eq. K_samp_pts) */
     float t_stop;   /* stop compositing once T < t_stop (Sec. 3.1.2; 1e-4 in the paper) */
-    int32_t tile;   /* tile edge in pixels; 16 (Sec. B.1) */
+    int32_t tile;   /* tile edge in pixels: 16 as in the paper (Sec. B.1), or 8 or 32 */
     float bg[3];    /* background colour added as T_final * bg */
 } svr_params;
+
+/* Views rendered together by svr_preprocess_views / svr_render_batched. */
+#define SVR_MAX_VIEWS 32
 
 typedef struct svr_scene {
     float world_center[3]; /* w_c */
@@ -101,44 +104,61 @@ typedef struct svr_scene {
 } svr_scene;
 
 /*
- * Per-view state, in HOST memory owned by the caller.  svr_preprocess fills
- * it; svr_bin_sort, svr_render_fwd and svr_render_bwd read it (svr_bin_sort
- * also updates it).  It points into the workspace and at the scene arrays,
- * which must stay alive while it is used.  Treat the fields as read-only.
+ * State of one view or a batch of views, in HOST memory owned by the caller.
+ * svr_preprocess / svr_preprocess_views fill it; svr_bin_sort,
+ * svr_render_fwd and svr_render_bwd read it (svr_bin_sort also updates it).
+ * It points into the workspace and at the scene arrays, which must stay
+ * alive while it is used.  Treat the fields as read-only.
+ *
+ * Tiles of all views share one numbering: view v owns global tiles
+ * [tile_base[v], tile_base[v+1]), its tile (tx, ty) being tile_base[v] +
+ * ty * ntx_v + tx.  Images of all views share one buffer per output: view v
+ * owns pixels [pixel_base[v], pixel_base[v+1]) of depth/alpha/T_final/last
+ * (row-major H_v x W_v) and floats [3 pixel_base[v], 3 pixel_base[v+1]) of
+ * rgb (planar [3][H_v][W_v]).
  */
 typedef struct svr_frame {
     svr_scene scene;
-    svr_camera cam;
     svr_params params;
+    int32_t n_views;     /* 1 after svr_preprocess */
+    int32_t key_shift;   /* Morton bits under the tile id in a key: 48 for svr_preprocess */
+    int64_t total_tiles;
+    svr_camera cams[SVR_MAX_VIEWS];
+    int32_t tile_base[SVR_MAX_VIEWS + 1];
+    int64_t pixel_base[SVR_MAX_VIEWS + 1];
+    double ray_origin[SVR_MAX_VIEWS][3];
     void *ws;
     size_t ws_bytes;
     int64_t pair_capacity;
     int64_t n_pairs;    /* pair count, or -1 while it is known only on the device */
-    int32_t n_tiles_x, n_tiles_y;
-    int32_t stage;      /* 1 after svr_preprocess, 2 after svr_bin_sort */
+    int32_t stage;      /* 1 after preprocessing, 2 after svr_bin_sort */
     int32_t sorted_alt; /* internal: which key buffer holds the sorted pairs */
-    double ray_origin[3];
     uint64_t offsets[24]; /* internal: byte offsets of the workspace buffers */
 } svr_frame;
 
 /* Device views of the internal buffers of a frame, for inspection. */
 typedef struct svr_buffers {
     const void *status;       /* uint32[16]: flags, n_pairs (low, high), ... */
-    const uint8_t *tile_mask; /* [n_tiles] bit s set if a pixel of the tile has ray sign bits s */
+    const uint8_t *tile_mask; /* [total_tiles] bit s set if a pixel of the tile has ray sign bits s */
     const uint64_t *octpath;  /* [N] Morton code (Sec. A.1) */
-    const int16_t *rect;      /* [N][4] tx0, tx1, ty0, ty1 (empty: tx0 > tx1) */
-    const uint32_t *count;    /* [N] pairs emitted per voxel */
-    const uint32_t *offset;   /* [N] exclusive scan of count */
-    const float *record;      /* [N][16] per-voxel record of the view */
-    const uint64_t *keys;     /* [pair_capacity] sorted keys: tile << 48 | Morton order */
+    const int16_t *rect;      /* [V][N][4] tx0, tx1, ty0, ty1 (empty: tx0 > tx1) */
+    const uint32_t *count;    /* [V][N] pairs emitted per (view, voxel) */
+    const uint32_t *offset;   /* [V][N] exclusive scan of count */
+    const float *record;      /* [V][N][16] per-voxel record of each view */
+    const uint64_t *keys;     /* [pair_capacity] sorted keys: tile << key_shift | Morton order */
     const uint32_t *values;   /* [pair_capacity] sorted values: s << 29 | voxel id */
-    const uint32_t *ranges;   /* [n_tiles][2] begin, end of each tile's list */
+    const uint32_t *ranges;   /* [total_tiles][2] begin, end of each tile's list */
 } svr_buffers;
 
 /* Workspace bytes needed for n_vox voxels, pair_capacity pairs and this
  * camera / tile size; 0 if the arguments are invalid.  Host only. */
 SVR_API size_t svr_workspace_size(int64_t n_vox, int64_t pair_capacity,
                                   const svr_camera *cam, const svr_params *params);
+
+/* Workspace bytes for a batch of n_views (1..SVR_MAX_VIEWS) cameras. */
+SVR_API size_t svr_workspace_size_views(int64_t n_vox, int64_t pair_capacity,
+                                        const svr_camera *cams, int n_views,
+                                        const svr_params *params);
 
 /*
  * Per-view preprocessing (Sec. 3.1.2 "Projection to image space" and
@@ -159,6 +179,21 @@ SVR_API size_t svr_workspace_size(int64_t n_vox, int64_t pair_capacity,
 SVR_API int svr_preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cam,
                            const svr_params *params, void *ws, size_t ws_bytes,
                            int64_t pair_capacity, void *stream);
+
+/*
+ * svr_preprocess for a batch of n_views (1..SVR_MAX_VIEWS) views of one scene
+ * rendered together: the views' tiles are numbered consecutively (see
+ * svr_frame), all pairs of all views are sorted at once and one persistent
+ * launch composites every (view, tile) of the batch.  Per view the result is
+ * that of svr_preprocess; the sorted order within each (view, tile) is the
+ * paper's.  The keys are compact: tile id << S | the top S bits of the
+ * direction-dependent Morton order, S = 3 min(16, max_level + 1), so the
+ * tile ids of all views need only fit 64 - S bits (SVR_ERR_LIMIT otherwise).
+ * The paper renders one view at a time; batching is this library's addition.
+ */
+SVR_API int svr_preprocess_views(svr_frame *frame, const svr_scene *scene, const svr_camera *cams,
+                                 int n_views, const svr_params *params, void *ws, size_t ws_bytes,
+                                 int64_t pair_capacity, void *stream);
 
 /*
  * Pair emission and sort (Sec. B.1).  Enqueues: the exclusive scan of the
@@ -209,6 +244,23 @@ SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, flo
 SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const float *d_depth,
                            const float *d_alpha, const float *T_final, const int32_t *last,
                            float *d_grid, float *d_sh, void *stream);
+
+/*
+ * Whole batched step in one call: svr_preprocess_views, svr_bin_sort without
+ * a pair count (no host synchronisation), svr_render_fwd and, when d_rgb,
+ * d_depth or d_alpha is not NULL, svr_render_bwd.  Only enqueues work, so the
+ * call can be captured in a CUDA graph and replayed (inputs and outputs must
+ * then stay at the same addresses).  Outputs and gradients use the batch
+ * layout of svr_frame; d_grid accumulates over all views, d_sh sums the views.
+ * Capacity overflow or invalid voxels are reported by svr_frame_status.  The
+ * paper has no batched path; see svr_preprocess_views.
+ */
+SVR_API int svr_render_batched(svr_frame *frame, const svr_scene *scene, const svr_camera *cams,
+                               int n_views, const svr_params *params, void *ws, size_t ws_bytes,
+                               int64_t pair_capacity, float *rgb, float *depth, float *alpha,
+                               float *T_final, int32_t *last, const float *d_rgb,
+                               const float *d_depth, const float *d_alpha, float *d_grid,
+                               float *d_sh, void *stream);
 
 /* svr_render_fwd that also writes, per pixel, counts[y][x] = (list entries
  * with the pixel's sign bits that it examined, hits it composited): the

@@ -41,13 +41,18 @@ class SvrScene(ctypes.Structure):
                 ("centre", _P), ("level", _P), ("corner_idx", _P), ("grid", _P), ("sh", _P)]
 
 
+SVR_MAX_VIEWS = 32
+
+
 class SvrFrame(ctypes.Structure):
-    _fields_ = [("scene", SvrScene), ("cam", SvrCamera), ("params", SvrParams),
+    _fields_ = [("scene", SvrScene), ("params", SvrParams), ("n_views", ctypes.c_int32),
+                ("key_shift", ctypes.c_int32), ("total_tiles", ctypes.c_int64),
+                ("cams", SvrCamera * SVR_MAX_VIEWS), ("tile_base", ctypes.c_int32 * (SVR_MAX_VIEWS + 1)),
+                ("pixel_base", ctypes.c_int64 * (SVR_MAX_VIEWS + 1)),
+                ("ray_origin", (ctypes.c_double * 3) * SVR_MAX_VIEWS),
                 ("ws", _P), ("ws_bytes", ctypes.c_size_t), ("pair_capacity", ctypes.c_int64),
-                ("n_pairs", ctypes.c_int64), ("n_tiles_x", ctypes.c_int32),
-                ("n_tiles_y", ctypes.c_int32), ("stage", ctypes.c_int32),
-                ("sorted_alt", ctypes.c_int32), ("ray_origin", ctypes.c_double * 3),
-                ("offsets", ctypes.c_uint64 * 24)]
+                ("n_pairs", ctypes.c_int64), ("stage", ctypes.c_int32),
+                ("sorted_alt", ctypes.c_int32), ("offsets", ctypes.c_uint64 * 24)]
 
 
 class SvrBuffers(ctypes.Structure):
@@ -66,7 +71,12 @@ _LIB = None
 # name -> (restype, argtypes)
 SIGNATURES = {
     "svr_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "svr_workspace_size_views": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int, _P]),
     "svr_preprocess": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_size_t, ctypes.c_int64, _P]),
+    "svr_preprocess_views": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_size_t,
+                                            ctypes.c_int64, _P]),
+    "svr_render_batched": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_size_t,
+                                          ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_bin_sort": (ctypes.c_int, [_P, _P, _P]),
     "svr_render_fwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "svr_render_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),

@@ -35,22 +35,23 @@ struct Layout {
     size_t off[kNumSlots];
 };
 
-Layout make_layout(int64_t n_vox, int64_t cap, int64_t ntiles) {
+// n_vox voxels seen by n_views views with ntiles tiles in all.
+Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles) {
     Layout L;
     size_t o = 0;
     auto take = [&](Slot s, size_t bytes) {
         L.off[s] = o;
         o = align256(o + bytes);
     };
-    const size_t N = (size_t)n_vox, C = (size_t)cap;
+    const size_t N = (size_t)n_vox, VN = (size_t)n_vox * (size_t)n_views, C = (size_t)cap;
     take(kStatus, sizeof(svr::Status));
     take(kTileMask, (size_t)ntiles);
     take(kOctpath, 8 * N);
-    take(kRect, 8 * N);
-    take(kCount, 4 * N);
-    take(kOffset, 4 * N);
-    take(kRecord, sizeof(svr::Record) * N);
-    take(kScanBlocks, 4 * ((N + svr::kScanTile - 1) / svr::kScanTile + 1));
+    take(kRect, 8 * VN);
+    take(kCount, 4 * VN);
+    take(kOffset, 4 * VN);
+    take(kRecord, sizeof(svr::Record) * VN);
+    take(kScanBlocks, 4 * ((VN + svr::kScanTile - 1) / svr::kScanTile + 1));
     take(kKeys0, 8 * C);
     take(kKeys1, 8 * C);
     take(kVals0, 4 * C);
@@ -58,48 +59,85 @@ Layout make_layout(int64_t n_vox, int64_t cap, int64_t ntiles) {
     take(kHist, 4 * 256 * ((C + svr::kRadixTile - 1) / svr::kRadixTile + 1));
     take(kDigitTot, 4 * 256);
     take(kRanges, 8 * (size_t)ntiles);
-    take(kDcol, 12 * N);
-    take(kBox, 8 * N);
+    take(kDcol, 12 * VN);
+    take(kBox, 8 * VN);
     take(kTileOrder, 4 * (size_t)ntiles);
     L.off[kTotal] = o;
     return L;
 }
 
-int check_camera(const svr_camera *cam, const svr_params *p, int64_t *ntiles, int *ntx, int *nty) {
-    if (!cam || !p) return fail(SVR_ERR_INVALID, "null camera or params");
+int tile_bits(int64_t ntiles) {
+    int b = 0;
+    while (((int64_t)1 << b) < ntiles) ++b;
+    return b;
+}
+
+int check_params(const svr_params *p) {
+    if (!p) return fail(SVR_ERR_INVALID, "null params");
+    if (p->tile != 8 && p->tile != 16 && p->tile != 32)
+        return fail(SVR_ERR_INVALID, "tile %d (8, 16 or 32 supported)", p->tile);
+    if (p->K < 1 || p->K > 3) return fail(SVR_ERR_INVALID, "K = %d (1..3 supported)", p->K);
+    if (!(p->t_stop >= 0.f) || !(p->t_stop < 1.f)) return fail(SVR_ERR_INVALID, "t_stop %g", p->t_stop);
+    return SVR_OK;
+}
+
+int check_camera(const svr_camera *cam, int tile, int *ntx, int *nty) {
+    if (!cam) return fail(SVR_ERR_INVALID, "null camera");
     if (cam->width <= 0 || cam->height <= 0 || cam->width > 65536 || cam->height > 65536)
         return fail(SVR_ERR_INVALID, "image size %d x %d", cam->width, cam->height);
     if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
         return fail(SVR_ERR_INVALID, "bad intrinsics");
     for (int i = 0; i < 12; ++i)
         if (!std::isfinite(cam->w2c[i])) return fail(SVR_ERR_INVALID, "non-finite w2c");
-    if (p->tile != 16) return fail(SVR_ERR_INVALID, "tile %d (16 supported)", p->tile);
-    if (p->K < 1 || p->K > 3) return fail(SVR_ERR_INVALID, "K = %d (1..3 supported)", p->K);
-    if (!(p->t_stop >= 0.f) || !(p->t_stop < 1.f)) return fail(SVR_ERR_INVALID, "t_stop %g", p->t_stop);
-    *ntx = (cam->width + p->tile - 1) / p->tile;
-    *nty = (cam->height + p->tile - 1) / p->tile;
-    *ntiles = (int64_t)(*ntx) * (*nty);
-    if (*ntiles > 65536) return fail(SVR_ERR_LIMIT, "%lld tiles > 2^16", (long long)*ntiles);
+    *ntx = (cam->width + tile - 1) / tile;
+    *nty = (cam->height + tile - 1) / tile;
+    return SVR_OK;
+}
+
+// Tile count of all views; SVR_OK or an error.
+int check_views(const svr_camera *cams, int n_views, const svr_params *p, int64_t *ntiles) {
+    int rc = check_params(p);
+    if (rc != SVR_OK) return rc;
+    if (!cams) return fail(SVR_ERR_INVALID, "null cameras");
+    if (n_views < 1 || n_views > SVR_MAX_VIEWS)
+        return fail(SVR_ERR_LIMIT, "%d views (1..%d supported)", n_views, SVR_MAX_VIEWS);
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        int ntx, nty;
+        rc = check_camera(cams + v, p->tile, &ntx, &nty);
+        if (rc != SVR_OK) return rc;
+        total += (int64_t)ntx * nty;
+    }
+    if (total > INT32_MAX / 64) return fail(SVR_ERR_LIMIT, "%lld tiles", (long long)total);
+    *ntiles = total;
     return SVR_OK;
 }
 
 svr::FrameDev frame_dev(const svr_frame *f) {
     svr::FrameDev d;
     memset(&d, 0, sizeof(d));
-    const svr_camera &c = f->cam;
-    d.cam.fx = c.fx;
-    d.cam.fy = c.fy;
-    d.cam.cx = c.cx;
-    d.cam.cy = c.cy;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) d.cam.R[3 * i + j] = c.w2c[4 * i + j];
-    for (int i = 0; i < 3; ++i) d.cam.t[i] = c.w2c[4 * i + 3];
-    for (int i = 0; i < 3; ++i) d.cam.ro[i] = (float)f->ray_origin[i];
-    d.cam.W = c.width;
-    d.cam.H = c.height;
-    d.cam.ntx = f->n_tiles_x;
-    d.cam.nty = f->n_tiles_y;
-    d.cam.tile = f->params.tile;
+    d.n_views = f->n_views;
+    d.total_tiles = (int)f->total_tiles;
+    d.key_shift = f->key_shift;
+    for (int v = 0; v < f->n_views; ++v) {
+        const svr_camera &c = f->cams[v];
+        svr::DevCam &dc = d.views[v];
+        dc.fx = c.fx;
+        dc.fy = c.fy;
+        dc.cx = c.cx;
+        dc.cy = c.cy;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) dc.R[3 * i + j] = c.w2c[4 * i + j];
+        for (int i = 0; i < 3; ++i) dc.t[i] = c.w2c[4 * i + 3];
+        for (int i = 0; i < 3; ++i) dc.ro[i] = (float)f->ray_origin[v][i];
+        dc.W = c.width;
+        dc.H = c.height;
+        dc.tile = f->params.tile;
+        dc.ntx = (c.width + dc.tile - 1) / dc.tile;
+        dc.nty = (c.height + dc.tile - 1) / dc.tile;
+        dc.tile_base = f->tile_base[v];
+        dc.pix_base = f->pixel_base[v];
+    }
     char *ws = (char *)f->ws;
     const uint64_t *o = f->offsets;
     d.status = (svr::Status *)(ws + o[kStatus]);
@@ -110,7 +148,6 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.offset = (uint32_t *)(ws + o[kOffset]);
     d.rec = (svr::Record *)(ws + o[kRecord]);
     d.box = (ushort4 *)(ws + o[kBox]);
-    d.tile_order = (uint32_t *)(ws + o[kTileOrder]);
     d.scan_blocks = (uint32_t *)(ws + o[kScanBlocks]);
     d.keys[0] = (uint64_t *)(ws + o[kKeys0]);
     d.keys[1] = (uint64_t *)(ws + o[kKeys1]);
@@ -119,6 +156,7 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.hist = (uint32_t *)(ws + o[kHist]);
     d.digit_tot = (uint32_t *)(ws + o[kDigitTot]);
     d.ranges = (uint2 *)(ws + o[kRanges]);
+    d.tile_order = (uint32_t *)(ws + o[kTileOrder]);
     d.dcol = (float *)(ws + o[kDcol]);
     d.n_vox = f->scene.n_vox;
     d.n_pts = f->scene.n_pts;
@@ -137,10 +175,80 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     return d;
 }
 
-int tile_bits(int64_t ntiles) {
-    int b = 0;
-    while (((int64_t)1 << b) < ntiles) ++b;
-    return b;
+// Shared by svr_preprocess (paper key layout) and svr_preprocess_views
+// (compact keys).
+int preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cams, int n_views,
+               const svr_params *params, void *ws, size_t ws_bytes, int64_t pair_capacity, bool paper_keys,
+               void *stream) {
+    g_err[0] = 0;
+    if (!frame || !scene) return fail(SVR_ERR_INVALID, "null frame or scene");
+    int64_t ntiles = 0;
+    int rc = check_views(cams, n_views, params, &ntiles);
+    if (rc != SVR_OK) return rc;
+    const int64_t N = scene->n_vox;
+    if (N < 0) return fail(SVR_ERR_INVALID, "n_vox %lld", (long long)N);
+    if (N > ((int64_t)1 << 29)) return fail(SVR_ERR_LIMIT, "n_vox %lld > 2^29", (long long)N);
+    if (scene->max_level < 1 || scene->max_level > 16)
+        return fail(SVR_ERR_INVALID, "max_level %d", scene->max_level);
+    const int lmax = scene->max_level;
+    const int key_shift = paper_keys ? 48 : 3 * (lmax < 16 ? lmax + 1 : 16);
+    if (paper_keys && ntiles > 65536)
+        return fail(SVR_ERR_LIMIT, "%lld tiles > 2^16 (the key's 16-bit tile id)", (long long)ntiles);
+    if (key_shift + tile_bits(ntiles) > 64)
+        return fail(SVR_ERR_LIMIT, "%lld tiles and max_level %d do not fit a 64-bit key", (long long)ntiles, lmax);
+    if (!(scene->world_size > 0.f) || !std::isfinite(scene->world_size))
+        return fail(SVR_ERR_INVALID, "world_size %g", scene->world_size);
+    if (N > 0 && (!scene->centre || !scene->level || !scene->corner_idx || !scene->sh ||
+                  (!scene->grid && scene->n_pts > 0)))
+        return fail(SVR_ERR_INVALID, "null scene array");
+    if (N > 0 && (((uintptr_t)scene->sh) & 15u)) return fail(SVR_ERR_INVALID, "sh not 16-byte aligned");
+    if (N > 0 && (((uintptr_t)scene->corner_idx) & 15u))
+        return fail(SVR_ERR_INVALID, "corner_idx not 16-byte aligned");
+    if (pair_capacity < 0 || pair_capacity > INT32_MAX)
+        return fail(SVR_ERR_INVALID, "pair_capacity %lld", (long long)pair_capacity);
+    if (!ws || (((uintptr_t)ws) & 255u)) return fail(SVR_ERR_INVALID, "workspace null or not 256-byte aligned");
+    const Layout L = make_layout(N, n_views, pair_capacity, ntiles);
+    if (ws_bytes < L.off[kTotal])
+        return fail(SVR_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, (size_t)L.off[kTotal]);
+
+    memset(frame, 0, sizeof(*frame));
+    frame->scene = *scene;
+    frame->params = *params;
+    frame->n_views = n_views;
+    frame->key_shift = key_shift;
+    frame->total_tiles = ntiles;
+    int64_t tb = 0, pb = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const svr_camera &c = cams[v];
+        frame->cams[v] = c;
+        frame->tile_base[v] = (int32_t)tb;
+        frame->pixel_base[v] = pb;
+        tb += (int64_t)((c.width + params->tile - 1) / params->tile) * ((c.height + params->tile - 1) / params->tile);
+        pb += (int64_t)c.width * c.height;
+        for (int i = 0; i < 3; ++i) {
+            double r = 0.0;
+            for (int j = 0; j < 3; ++j) r -= (double)c.w2c[4 * j + i] * (double)c.w2c[4 * j + 3];
+            frame->ray_origin[v][i] = r;
+        }
+    }
+    frame->tile_base[n_views] = (int32_t)tb;
+    frame->pixel_base[n_views] = pb;
+    frame->ws = ws;
+    frame->ws_bytes = ws_bytes;
+    frame->pair_capacity = pair_capacity;
+    frame->n_pairs = -1;
+    for (int i = 0; i < kNumSlots; ++i) frame->offsets[i] = L.off[i];
+    const svr::FrameDev d = frame_dev(frame);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(svr::Status), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&d.status->bad_voxel, 0xFF, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "status reset");
+    e = svr::launch_tile_mask(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tile mask");
+    e = svr::launch_preprocess(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "preprocess");
+    frame->stage = 1;
+    return SVR_OK;
 }
 
 }  // namespace
@@ -159,74 +267,37 @@ extern "C" {
 
 SVR_API const char *svr_last_error(void) { return g_err; }
 
-SVR_API int svr_version(void) { return 100; }
+SVR_API int svr_version(void) { return 200; }
+
+SVR_API size_t svr_workspace_size_views(int64_t n_vox, int64_t pair_capacity, const svr_camera *cams, int n_views,
+                                        const svr_params *params) {
+    int64_t ntiles = 0;
+    if (n_vox < 0 || n_vox > ((int64_t)1 << 29)) return 0;
+    if (pair_capacity < 0 || pair_capacity > INT32_MAX) return 0;
+    if (check_views(cams, n_views, params, &ntiles) != SVR_OK) return 0;
+    return make_layout(n_vox, n_views, pair_capacity, ntiles).off[kTotal];
+}
 
 SVR_API size_t svr_workspace_size(int64_t n_vox, int64_t pair_capacity, const svr_camera *cam,
                                   const svr_params *params) {
-    int64_t ntiles;
+    if (!cam) return 0;
+    const size_t n = svr_workspace_size_views(n_vox, pair_capacity, cam, 1, params);
+    if (n == 0) return 0;
     int ntx, nty;
-    if (n_vox < 0 || n_vox > ((int64_t)1 << 29)) return 0;
-    if (pair_capacity < 0 || pair_capacity > INT32_MAX) return 0;
-    if (check_camera(cam, params, &ntiles, &ntx, &nty) != SVR_OK) return 0;
-    return make_layout(n_vox, pair_capacity, ntiles).off[kTotal];
+    if (check_camera(cam, params->tile, &ntx, &nty) != SVR_OK || (int64_t)ntx * nty > 65536) return 0;
+    return n;
 }
 
 SVR_API int svr_preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cam,
                            const svr_params *params, void *ws, size_t ws_bytes, int64_t pair_capacity,
                            void *stream) {
-    g_err[0] = 0;
-    if (!frame || !scene) return fail(SVR_ERR_INVALID, "null frame or scene");
-    int64_t ntiles;
-    int ntx, nty;
-    int rc = check_camera(cam, params, &ntiles, &ntx, &nty);
-    if (rc != SVR_OK) return rc;
-    const int64_t N = scene->n_vox;
-    if (N < 0) return fail(SVR_ERR_INVALID, "n_vox %lld", (long long)N);
-    if (N > ((int64_t)1 << 29)) return fail(SVR_ERR_LIMIT, "n_vox %lld > 2^29", (long long)N);
-    if (scene->max_level < 1 || scene->max_level > 16)
-        return fail(SVR_ERR_INVALID, "max_level %d", scene->max_level);
-    if (!(scene->world_size > 0.f) || !std::isfinite(scene->world_size))
-        return fail(SVR_ERR_INVALID, "world_size %g", scene->world_size);
-    if (N > 0 && (!scene->centre || !scene->level || !scene->corner_idx || !scene->sh ||
-                  (!scene->grid && scene->n_pts > 0)))
-        return fail(SVR_ERR_INVALID, "null scene array");
-    if (N > 0 && (((uintptr_t)scene->sh) & 15u)) return fail(SVR_ERR_INVALID, "sh not 16-byte aligned");
-    if (N > 0 && (((uintptr_t)scene->corner_idx) & 15u))
-        return fail(SVR_ERR_INVALID, "corner_idx not 16-byte aligned");
-    if (pair_capacity < 0 || pair_capacity > INT32_MAX)
-        return fail(SVR_ERR_INVALID, "pair_capacity %lld", (long long)pair_capacity);
-    if (!ws || (((uintptr_t)ws) & 255u)) return fail(SVR_ERR_INVALID, "workspace null or not 256-byte aligned");
-    const Layout L = make_layout(N, pair_capacity, ntiles);
-    if (ws_bytes < L.off[kTotal])
-        return fail(SVR_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, (size_t)L.off[kTotal]);
+    return preprocess(frame, scene, cam, 1, params, ws, ws_bytes, pair_capacity, true, stream);
+}
 
-    memset(frame, 0, sizeof(*frame));
-    frame->scene = *scene;
-    frame->cam = *cam;
-    frame->params = *params;
-    frame->ws = ws;
-    frame->ws_bytes = ws_bytes;
-    frame->pair_capacity = pair_capacity;
-    frame->n_pairs = -1;
-    frame->n_tiles_x = ntx;
-    frame->n_tiles_y = nty;
-    for (int i = 0; i < kNumSlots; ++i) frame->offsets[i] = L.off[i];
-    for (int i = 0; i < 3; ++i) {
-        double r = 0.0;
-        for (int j = 0; j < 3; ++j) r -= (double)cam->w2c[4 * j + i] * (double)cam->w2c[4 * j + 3];
-        frame->ray_origin[i] = r;
-    }
-    const svr::FrameDev d = frame_dev(frame);
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(svr::Status), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&d.status->bad_voxel, 0xFF, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_fail(e, "status reset");
-    e = svr::launch_tile_mask(d, s);
-    if (e != cudaSuccess) return cuda_fail(e, "tile mask");
-    e = svr::launch_preprocess(d, s);
-    if (e != cudaSuccess) return cuda_fail(e, "preprocess");
-    frame->stage = 1;
-    return SVR_OK;
+SVR_API int svr_preprocess_views(svr_frame *frame, const svr_scene *scene, const svr_camera *cams, int n_views,
+                                 const svr_params *params, void *ws, size_t ws_bytes, int64_t pair_capacity,
+                                 void *stream) {
+    return preprocess(frame, scene, cams, n_views, params, ws, ws_bytes, pair_capacity, false, stream);
 }
 
 SVR_API int svr_frame_status(const svr_frame *frame, uint32_t *flags, int64_t *n_pairs, void *stream) {
@@ -249,10 +320,10 @@ SVR_API int svr_bin_sort(svr_frame *frame, int64_t *n_pairs_out, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = svr::launch_scan_emit(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "scan/emit");
-    const int64_t ntiles = (int64_t)frame->n_tiles_x * frame->n_tiles_y;
     const int lmax = frame->scene.max_level;
-    const int lo_bit = 48 - 3 * (lmax < 16 ? lmax + 1 : 16);
-    const int hi_bit = 48 + tile_bits(ntiles);
+    const int morton_bits = 3 * (lmax < 16 ? lmax + 1 : 16);
+    const int lo_bit = frame->key_shift - morton_bits;
+    const int hi_bit = frame->key_shift + tile_bits(frame->total_tiles);
     int alt = 0;
     e = svr::launch_sort(d, lo_bit, hi_bit, lmax == 16, &alt, s);
     if (e != cudaSuccess) return cuda_fail(e, "sort");
@@ -315,6 +386,21 @@ SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const flo
                                            d_sh, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
     return SVR_OK;
+}
+
+SVR_API int svr_render_batched(svr_frame *frame, const svr_scene *scene, const svr_camera *cams, int n_views,
+                               const svr_params *params, void *ws, size_t ws_bytes, int64_t pair_capacity,
+                               float *rgb, float *depth, float *alpha, float *T_final, int32_t *last,
+                               const float *d_rgb, const float *d_depth, const float *d_alpha, float *d_grid,
+                               float *d_sh, void *stream) {
+    int rc = svr_preprocess_views(frame, scene, cams, n_views, params, ws, ws_bytes, pair_capacity, stream);
+    if (rc != SVR_OK) return rc;
+    rc = svr_bin_sort(frame, nullptr, stream);
+    if (rc != SVR_OK) return rc;
+    rc = svr_render_fwd(frame, rgb, depth, alpha, T_final, last, stream);
+    if (rc != SVR_OK) return rc;
+    if (d_rgb || d_depth || d_alpha) rc = svr_render_bwd(frame, d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_sh, stream);
+    return rc;
 }
 
 SVR_API int svr_frame_buffers(const svr_frame *frame, svr_buffers *out) {

@@ -3,13 +3,18 @@
 //   k_tile_mask   per tile: OR of 1 << signbits(r_d) over its in-image pixels
 //                 (ray sign bits of Sec. B.2; duplication per sign pattern,
 //                 Sec. B.1)
-//   k_preprocess  per voxel: lattice index, Morton code (Sec. A.1), tile
-//                 rectangle of the projected corners (Sec. 3.1.2), pair count,
-//                 view-dependent colour (Eq. vox_color), gathered densities
+//   k_preprocess  per (view, voxel): lattice index, Morton code (Sec. A.1),
+//                 tile rectangle of the projected corners (Sec. 3.1.2), pair
+//                 count, conservative pixel box, view-dependent colour
+//                 (Eq. vox_color), gathered densities
 //   k_scan_*      exclusive scan of the pair counts (three phases)
-//   k_emit        key = tile << 48 | (octpath ^ s replicated), value = s << 29
-//                 | voxel id (Sec. B.1; the per-triple permutation of Sec. B.2
-//                 is b ^ s, applied to all 16 triples at once)
+//   k_emit        key = tile << S | top S bits of (octpath ^ s replicated),
+//                 value = s << 29 | voxel id (Sec. B.1; the per-triple
+//                 permutation of Sec. B.2 is b ^ s, applied to all 16
+//                 triples at once).  S = 48 for one view (the paper's layout:
+//                 16-bit tile id over the 48-bit order); a batch of views uses
+//                 the global tile id over the 3 (max_level + 1) Morton bits
+//                 that can differ, so more than 2^16 tiles fit in 64 bits.
 #include <climits>
 
 #include "svr_internal.cuh"
@@ -18,8 +23,10 @@ namespace svr {
 
 // --------------------------------------------------------------- tile masks
 
-__global__ void k_tile_mask(DevCam cam, uint8_t *__restrict__ mask) {
-    const int tile = blockIdx.x;
+__global__ void k_tile_mask(FrameDev f) {
+    const int g = blockIdx.x;
+    const DevCam &cam = f.views[view_of_tile(f, g)];
+    const int tile = g - cam.tile_base;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
     unsigned m = 0;
     const int npx = cam.tile * cam.tile;
@@ -35,7 +42,7 @@ __global__ void k_tile_mask(DevCam cam, uint8_t *__restrict__ mask) {
     if (threadIdx.x == 0) {
         unsigned r = 0;
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) r |= wm[w];
-        mask[tile] = (uint8_t)r;
+        f.tile_mask[g] = (uint8_t)r;
     }
 }
 
@@ -56,10 +63,13 @@ __device__ __forceinline__ void mark_invalid(Status *st, int64_t v) {
     atomicMin(reinterpret_cast<unsigned *>(&st->bad_voxel), (unsigned)v);
 }
 
+// grid.y = view
 __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= f.n_vox) return;
-    const DevCam &cam = f.cam;
+    const int view = blockIdx.y;
+    const DevCam &cam = f.views[view];
+    const int64_t iv = (int64_t)view * f.n_vox + v;
     const float c0 = f.centre[3 * v + 0], c1 = f.centre[3 * v + 1], c2 = f.centre[3 * v + 2];
     const int l = f.level[v];
     const short4 empty = make_short4(0, -1, 0, -1);
@@ -89,14 +99,15 @@ __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
         ok = ok && lo >= 0 && (int64_t)hi < np;
     }
     if (!ok) {
-        mark_invalid(f.status, v);
-        f.count[v] = 0;
-        f.rect[v] = empty;
+        if (view == 0) mark_invalid(f.status, v);
+        f.count[iv] = 0;
+        f.rect[iv] = empty;
         return;
     }
-    const uint64_t code = ((spread3(ijk[0]) << 2) | (spread3(ijk[1]) << 1) | spread3(ijk[2]))
-                          << (3 * (kMaxLevel - l));
-    f.octpath[v] = code;
+    if (view == 0) {
+        f.octpath[v] = ((spread3(ijk[0]) << 2) | (spread3(ijk[1]) << 1) | spread3(ijk[2]))
+                       << (3 * (kMaxLevel - l));
+    }
 
     // project the eight corners
     const float h = 0.5f * vs;
@@ -144,12 +155,13 @@ __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
         rc = make_short4((short)tx0, (short)tx1, (short)ty0, (short)ty1);
     }
     uint32_t cnt = 0;
+    const uint8_t *mask = f.tile_mask + cam.tile_base;
     for (int ty = rc.z; ty <= rc.w; ++ty)
-        for (int tx = rc.x; tx <= rc.y; ++tx) cnt += __popc(f.tile_mask[ty * cam.ntx + tx]);
-    f.rect[v] = rc;
-    f.count[v] = cnt;
+        for (int tx = rc.x; tx <= rc.y; ++tx) cnt += __popc(mask[ty * cam.ntx + tx]);
+    f.rect[iv] = rc;
+    f.count[iv] = cnt;
     if (cnt == 0) return;
-    f.box[v] = box;
+    f.box[iv] = box;
 
     // record of this view: min corner relative to the ray origin, size,
     // gathered raw densities, colour
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
     }
     unsigned bits = (col[0] > 0.f ? 1u : 0u) | (col[1] > 0.f ? 2u : 0u) | (col[2] > 0.f ? 4u : 0u);
     r.r3 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), __uint_as_float(bits));
-    f.rec[v] = r;
+    f.rec[iv] = r;
 }
 
 // --------------------------------------------------------------------- scan
@@ -283,25 +295,31 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ 
 
 // --------------------------------------------------------------------- emit
 
+// grid.y = view
 __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= f.n_vox) return;
     if (f.status->flags & SVR_FLAG_CAPACITY) return;
-    const uint32_t cnt = f.count[v];
+    const int view = blockIdx.y;
+    const DevCam &cam = f.views[view];
+    const int64_t iv = (int64_t)view * f.n_vox + v;
+    const uint32_t cnt = f.count[iv];
     if (cnt == 0) return;
-    uint32_t o = f.offset[v];
-    const short4 rc = f.rect[v];
+    uint32_t o = f.offset[iv];
+    const short4 rc = f.rect[iv];
     const uint64_t code = f.octpath[v];
+    const int drop = 48 - f.key_shift;
     uint64_t *keys = f.keys[0];
     uint32_t *vals = f.vals[0];
     for (int ty = rc.z; ty <= rc.w; ++ty) {
         for (int tx = rc.x; tx <= rc.y; ++tx) {
-            const int tile = ty * f.cam.ntx + tx;
-            unsigned m = f.tile_mask[tile];
+            const int tile = ty * cam.ntx + tx;
+            const uint64_t g = (uint64_t)(cam.tile_base + tile);
+            unsigned m = f.tile_mask[cam.tile_base + tile];
             while (m) {
                 const unsigned s = __ffs(m) - 1;
                 m &= m - 1;
-                keys[o] = ((uint64_t)tile << 48) | (code ^ ((uint64_t)s * kTripleOnes));
+                keys[o] = (g << f.key_shift) | ((code ^ ((uint64_t)s * kTripleOnes)) >> drop);
                 vals[o] = (s << 29) | (uint32_t)v;
                 ++o;
             }
@@ -312,30 +330,30 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s) {
-    const int ntiles = f.cam.ntx * f.cam.nty;
-    const int threads = f.cam.tile * f.cam.tile >= 256 ? 256 : 64;
-    k_tile_mask<<<ntiles, threads, 0, s>>>(f.cam, f.tile_mask);
+    const int threads = f.views[0].tile * f.views[0].tile >= 256 ? 256 : 64;
+    k_tile_mask<<<f.total_tiles, threads, 0, s>>>(f);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s) {
     if (f.n_vox == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((f.n_vox + 255) / 256);
-    k_preprocess<<<blocks, 256, 0, s>>>(f);
+    const dim3 grid((unsigned)((f.n_vox + 255) / 256), (unsigned)f.n_views);
+    k_preprocess<<<grid, 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s) {
-    if (f.n_vox == 0) {
+    const int64_t n = f.n_vox * f.n_views;
+    if (n == 0) {
         k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, 0, f.status, f.capacity);
         return cudaGetLastError();
     }
-    const int nb = (int)((f.n_vox + kScanTile - 1) / kScanTile);
-    k_scan_reduce<<<nb, 256, 0, s>>>(f.count, f.n_vox, f.scan_blocks);
+    const int nb = (int)((n + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, 256, 0, s>>>(f.count, n, f.scan_blocks);
     k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, nb, f.status, f.capacity);
-    k_scan_down<<<nb, 256, 0, s>>>(f.count, f.n_vox, f.scan_blocks, f.offset);
-    const unsigned blocks = (unsigned)((f.n_vox + 255) / 256);
-    k_emit<<<blocks, 256, 0, s>>>(f);
+    k_scan_down<<<nb, 256, 0, s>>>(f.count, n, f.scan_blocks, f.offset);
+    const dim3 grid((unsigned)((f.n_vox + 255) / 256), (unsigned)f.n_views);
+    k_emit<<<grid, 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 

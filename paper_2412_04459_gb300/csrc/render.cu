@@ -44,7 +44,6 @@
 
 namespace svr {
 
-constexpr int kBlocksPerTile = 8;  // 8x4 pixel blocks of a 16x16 tile: the work items
 constexpr int kWarps = 8;          // warps per CTA of the forward
 constexpr int kThreads = kWarps * 32;
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
@@ -106,12 +105,21 @@ struct WarpBlock {
     unsigned smask;  // bit s set if one of its in-image pixels has sign bits s
 };
 
+// Per-view arrays of the work item's view.
+struct ViewData {
+    const Record *rec;    // f.rec + view * N
+    const ushort4 *box;   // f.box + view * N
+};
+
+// Pixel of the calling lane in block blk of a tile (tile edge 8, 16 or 32:
+// tile / 8 blocks of 8x4 pixels per block row).
 __device__ __forceinline__ PixelRay pixel_ray(const DevCam &cam, int tile, int blk, WarpBlock &wb) {
     PixelRay p;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
     const int lane = threadIdx.x & 31;
-    wb.x0 = tx * 16 + (blk & 1) * 8;
-    wb.y0 = ty * 16 + (blk >> 1) * 4;
+    const int bpr = cam.tile >> 3;
+    wb.x0 = tx * cam.tile + (blk % bpr) * 8;
+    wb.y0 = ty * cam.tile + (blk / bpr) * 4;
     p.x = wb.x0 + (lane & 7);
     p.y = wb.y0 + (lane >> 3);
     p.inside = p.x < cam.W && p.y < cam.H;
@@ -140,7 +148,7 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 // One batch of the warp's walk: lane j looks at list entry idx (if valid),
 // keeps it if the warp can use it and stages it at its rank among the kept
 // lanes.  Returns the number of staged entries (list order by lane).
-__device__ __forceinline__ int stage_batch(Entry *st, const FrameDev &f, const uint32_t *__restrict__ vals,
+__device__ __forceinline__ int stage_batch(Entry *st, const ViewData &vd, const uint32_t *__restrict__ vals,
                                            int idx, bool valid, const WarpBlock &wb) {
     bool keep = false;
     uint32_t val = 0;
@@ -148,14 +156,14 @@ __device__ __forceinline__ int stage_batch(Entry *st, const FrameDev &f, const u
     if (valid) {
         val = __ldg(vals + idx);
         if ((wb.smask >> (val >> 29)) & 1u) {
-            bx = __ldg(f.box + (val & 0x1FFFFFFFu));
+            bx = __ldg(vd.box + (val & 0x1FFFFFFFu));
             keep = bx.x <= wb.x0 + 7 && bx.y >= wb.x0 && bx.z <= wb.y0 + 3 && bx.w >= wb.y0;
         }
     }
     const unsigned kb = __ballot_sync(0xffffffffu, keep);
     if (keep) {
         const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-        stage_entry(st[__popc(kb & lt)], val, idx, bx, f.rec);
+        stage_entry(st[__popc(kb & lt)], val, idx, bx, vd.rec);
     }
     __syncwarp();
     return __popc(kb);
@@ -176,34 +184,50 @@ __device__ __forceinline__ void fetch_val(Lookahead &la, const uint32_t *__restr
     la.want = valid && ((wb.smask >> (la.val >> 29)) & 1u);
 }
 
-__device__ __forceinline__ void fetch_box(Lookahead &la, const FrameDev &f) {
-    la.box = la.want ? __ldg(f.box + (la.val & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
+__device__ __forceinline__ void fetch_box(Lookahead &la, const ViewData &vd) {
+    la.box = la.want ? __ldg(vd.box + (la.val & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
 }
 
 // Stage the looked-ahead entries (index idx per lane) that the warp keeps.
-__device__ __forceinline__ int stage_ahead(Entry *st, const FrameDev &f, const Lookahead &la, int idx,
+__device__ __forceinline__ int stage_ahead(Entry *st, const ViewData &vd, const Lookahead &la, int idx,
                                            const WarpBlock &wb) {
     const bool keep = la.want && la.box.x <= wb.x0 + 7 && la.box.y >= wb.x0 && la.box.z <= wb.y0 + 3 &&
                       la.box.w >= wb.y0;
     const unsigned kb = __ballot_sync(0xffffffffu, keep);
     if (keep) {
         const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-        stage_entry(st[__popc(kb & lt)], la.val, idx, la.box, f.rec);
+        stage_entry(st[__popc(kb & lt)], la.val, idx, la.box, vd.rec);
     }
     __syncwarp();
     return __popc(kb);
 }
 
-// Next work item (tile, block) of the calling warp, or false when done.
-__device__ __forceinline__ bool next_item(unsigned *counter, unsigned n_items, const uint32_t *order, int &tile,
-                                          int &blk) {
+// Next work item (global tile, block) of the calling warp, or false when done.
+__device__ __forceinline__ bool next_item(unsigned *counter, unsigned n_items, unsigned blocks_per_tile,
+                                          const uint32_t *order, int &tile, int &blk) {
     unsigned item = 0;
     if ((threadIdx.x & 31) == 0) item = atomicAdd(counter, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) return false;
-    tile = (int)order[item / kBlocksPerTile];
-    blk = (int)(item % kBlocksPerTile);
+    tile = (int)order[item / blocks_per_tile];
+    blk = (int)(item % blocks_per_tile);
     return true;
+}
+
+// The view of a global tile and its arrays.
+struct ItemView {
+    int view;
+    int tile;   // tile index within the view
+    ViewData vd;
+};
+
+__device__ __forceinline__ ItemView item_view(const FrameDev &f, int g) {
+    ItemView iv;
+    iv.view = view_of_tile(f, g);
+    iv.tile = g - f.views[iv.view].tile_base;
+    iv.vd.rec = f.rec + (size_t)iv.view * f.n_vox;
+    iv.vd.box = f.box + (size_t)iv.view * f.n_vox;
+    return iv;
 }
 
 // ------------------------------------------------------------------ forward
@@ -239,12 +263,15 @@ struct FwdOut {
 };
 
 template <int K, bool STATS>
-__device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int tile, int blk,
+__device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int g, int blk,
                                           Entry *st, const FwdOut &out) {
+    const ItemView iv = item_view(f, g);
+    const DevCam &cam = f.views[iv.view];
+    const ViewData &vd = iv.vd;
     WarpBlock wb;
-    const PixelRay p = pixel_ray(f.cam, tile, blk, wb);
+    const PixelRay p = pixel_ray(cam, iv.tile, blk, wb);
     if (wb.smask == 0) return;  // the whole block lies outside the image
-    const uint2 rg = f.ranges[tile];
+    const uint2 rg = f.ranges[g];
     const int beg = (int)rg.x, end = (int)rg.y;
     const int lane = threadIdx.x & 31;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
@@ -254,14 +281,14 @@ __device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__r
 
     Lookahead la;
     fetch_val(la, vals, beg + lane, beg + lane < end, wb);
-    fetch_box(la, f);
+    fetch_box(la, vd);
     for (int base = beg; base < end; base += kBatch) {
         if (__all_sync(0xffffffffu, done)) break;
         const Lookahead cur = la;
         const int nidx = base + kBatch + lane;
         fetch_val(la, vals, nidx, nidx < end, wb);
-        const int n = stage_ahead(st, f, cur, base + lane, wb);
-        fetch_box(la, f);
+        const int n = stage_ahead(st, vd, cur, base + lane, wb);
+        fetch_box(la, vd);
         // phase A: this pixel's hits among the staged entries
         unsigned hits = 0;
         if (!done) {
@@ -300,11 +327,14 @@ __device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__r
         __syncwarp();
     }
     if (p.inside) {
-        const size_t HW = (size_t)f.cam.W * f.cam.H;
-        const size_t o = (size_t)p.y * f.cam.W + p.x;
-        out.rgb[o] = fmaf(T, f.bg[0], C0);
-        out.rgb[HW + o] = fmaf(T, f.bg[1], C1);
-        out.rgb[2 * HW + o] = fmaf(T, f.bg[2], C2);
+        // outputs of view v start at pixel pix_base (rgb: 3 * pix_base, planar)
+        const size_t HW = (size_t)cam.W * cam.H;
+        const size_t px = (size_t)p.y * cam.W + p.x;
+        const size_t o = (size_t)cam.pix_base + px;
+        float *rgb = out.rgb + 3 * (size_t)cam.pix_base + px;
+        rgb[0] = fmaf(T, f.bg[0], C0);
+        rgb[HW] = fmaf(T, f.bg[1], C1);
+        rgb[2 * HW] = fmaf(T, f.bg[2], C2);
         out.depth[o] = D;
         out.alpha[o] = 1.f - T;
         out.T[o] = T;
@@ -320,9 +350,10 @@ template <int K, bool STATS>
 __global__ void __launch_bounds__(kThreads) k_render_fwd(FrameDev f, const uint32_t *__restrict__ vals, FwdOut out) {
     __shared__ Entry stage[kWarps][kBatch];
     Entry *st = stage[threadIdx.x >> 5];
-    const unsigned n_items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    const unsigned bpt = (unsigned)(f.views[0].tile * f.views[0].tile) / 32u;
+    const unsigned n_items = (unsigned)f.total_tiles * bpt;
     int tile, blk;
-    while (next_item(&f.status->fwd_next, n_items, f.tile_order, tile, blk)) {
+    while (next_item(&f.status->fwd_next, n_items, bpt, f.tile_order, tile, blk)) {
         fwd_block<K, STATS>(f, vals, tile, blk, st, out);
         __syncwarp();
     }
@@ -503,24 +534,30 @@ struct BwdIn {
 };
 
 template <int K>
-__device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int tile, int blk,
+__device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int gt, int blk,
                                           Entry *st, float *acc, float *scratch, const BwdIn &in) {
+    const ItemView iv = item_view(f, gt);
+    const DevCam &cam = f.views[iv.view];
+    const ViewData &vd = iv.vd;
+    float *dcol = f.dcol + 3 * (size_t)iv.view * f.n_vox;
     WarpBlock wb;
-    const PixelRay p = pixel_ray(f.cam, tile, blk, wb);
+    const PixelRay p = pixel_ray(cam, iv.tile, blk, wb);
     if (wb.smask == 0) return;
-    const uint2 rg = f.ranges[tile];
+    const uint2 rg = f.ranges[gt];
     const int beg = (int)rg.x;
     const int lane = threadIdx.x & 31;
-    const size_t HW = (size_t)f.cam.W * f.cam.H;
-    const size_t o = (size_t)p.y * f.cam.W + p.x;
+    const size_t HW = (size_t)cam.W * cam.H;
+    const size_t px = (size_t)p.y * cam.W + p.x;
+    const size_t o = (size_t)cam.pix_base + px;
 
     PixelGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
     int last = beg - 1;
     if (p.inside) {
         if (in.d_rgb) {
-            g.gC0 = in.d_rgb[o];
-            g.gC1 = in.d_rgb[HW + o];
-            g.gC2 = in.d_rgb[2 * HW + o];
+            const float *gr = in.d_rgb + 3 * (size_t)cam.pix_base + px;
+            g.gC0 = gr[0];
+            g.gC1 = gr[HW];
+            g.gC2 = gr[2 * HW];
         }
         if (in.d_depth) g.gD = in.d_depth[o];
         if (in.d_alpha) g.gA = in.d_alpha[o];
@@ -537,13 +574,13 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
         float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
         Lookahead la;
         fetch_val(la, vals, hi - 1 - lane, hi - 1 - lane >= beg, wb);
-        fetch_box(la, f);
+        fetch_box(la, vd);
         for (int top = hi; top > beg; top -= kBatch) {
             const Lookahead cur = la;
             const int nidx = top - 1 - kBatch - lane;
             fetch_val(la, vals, nidx, nidx >= beg, wb);
-            const int n = stage_ahead(st, f, cur, top - 1 - lane, wb);
-            fetch_box(la, f);
+            const int n = stage_ahead(st, vd, cur, top - 1 - lane, wb);
+            fetch_box(la, vd);
             unsigned hits = 0;
             if (active) {
                 for (int k = 0; k < n; ++k) {
@@ -575,7 +612,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
                     acc_group_add(acc, scratch, k, dgeo, dcol);
                 }
                 __syncwarp();
-                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, f.dcol);
+                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, dcol);
             }
             __syncwarp();
         }
@@ -588,7 +625,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
         float T = 1.f, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
         for (int base = beg; base < hi; base += kBatch) {
             const int idx = base + lane;
-            const int n = stage_batch(st, f, vals, idx, idx < hi, wb);
+            const int n = stage_batch(st, vd, vals, idx, idx < hi, wb);
             if (fallback) {
                 for (int k = 0; k < n; ++k) {
                     const Entry &e = st[k];
@@ -613,7 +650,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
         float Tf = 1.f, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
         for (int base = beg; base < hi; base += kBatch) {
             const int idx = base + lane;
-            const int n = stage_batch(st, f, vals, idx, idx < hi, wb);
+            const int n = stage_batch(st, vd, vals, idx, idx < hi, wb);
             unsigned hits = 0;
             if (fallback) {
                 for (int k = 0; k < n; ++k) {
@@ -646,7 +683,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
                     acc_group_add(acc, scratch, k, dgeo, dcol);
                 }
                 __syncwarp();
-                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, f.dcol);
+                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, dcol);
             }
             __syncwarp();
         }
@@ -661,18 +698,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(FrameDev f, const ui
     __shared__ float scratch_all[kBwdWarps][32 * kAccStride];
     const int warp = threadIdx.x >> 5;
     Entry *st = stage[warp];
-    const unsigned n_items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    const unsigned bpt = (unsigned)(f.views[0].tile * f.views[0].tile) / 32u;
+    const unsigned n_items = (unsigned)f.total_tiles * bpt;
     int tile, blk;
-    while (next_item(&f.status->bwd_next, n_items, f.tile_order, tile, blk)) {
+    while (next_item(&f.status->bwd_next, n_items, bpt, f.tile_order, tile, blk)) {
         bwd_block<K>(f, vals, tile, blk, st, acc_all[warp], scratch_all[warp], in);
         __syncwarp();
     }
 }
 
-// Per voxel: dL/dsh[n][c] = Y_n(d) * dL/dc_c where the channel was > 0 before
-// the clamp (Eq. vox_color), zero for voxels not in view.  Each thread builds
-// its voxel's 48 values in shared memory; the block then writes its rows
-// with consecutive threads on consecutive words.
+// Per voxel: dL/dsh[n][c] = sum over views of Y_n(d_v) * dL/dc_{v,c}, over
+// the views where the voxel is in view and channel c was > 0 before the
+// clamp (Eq. vox_color); zero for a voxel in no view.  Each thread builds its
+// voxel's 48 values in shared memory; the block then writes its rows with
+// consecutive threads on consecutive words.
 constexpr int kVoxBwdThreads = 128;
 
 __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float *__restrict__ d_sh) {
@@ -681,25 +720,27 @@ __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float 
     const int64_t v = v0 + threadIdx.x;
     if (v < f.n_vox) {
         float *o = rows[threadIdx.x];
-        if (f.count[v] == 0) {
 #pragma unroll
-            for (int i = 0; i < 48; ++i) o[i] = 0.f;
-        } else {
-            const unsigned bits = __float_as_uint(f.rec[v].r3.w);
-            const float g0 = (bits & 1u) ? f.dcol[3 * v + 0] : 0.f;
-            const float g1 = (bits & 2u) ? f.dcol[3 * v + 1] : 0.f;
-            const float g2 = (bits & 4u) ? f.dcol[3 * v + 2] : 0.f;
-            float dx = f.centre[3 * v + 0] - f.cam.ro[0];
-            float dy = f.centre[3 * v + 1] - f.cam.ro[1];
-            float dz = f.centre[3 * v + 2] - f.cam.ro[2];
+        for (int i = 0; i < 48; ++i) o[i] = 0.f;
+        for (int view = 0; view < f.n_views; ++view) {
+            const int64_t iv = (int64_t)view * f.n_vox + v;
+            if (f.count[iv] == 0) continue;
+            const DevCam &cam = f.views[view];
+            const unsigned bits = __float_as_uint(f.rec[iv].r3.w);
+            const float g0 = (bits & 1u) ? f.dcol[3 * iv + 0] : 0.f;
+            const float g1 = (bits & 2u) ? f.dcol[3 * iv + 1] : 0.f;
+            const float g2 = (bits & 4u) ? f.dcol[3 * iv + 2] : 0.f;
+            float dx = f.centre[3 * v + 0] - cam.ro[0];
+            float dy = f.centre[3 * v + 1] - cam.ro[1];
+            float dz = f.centre[3 * v + 2] - cam.ro[2];
             const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
             float Y[16];
             sh_basis(dx * inv, dy * inv, dz * inv, Y);
 #pragma unroll
             for (int n = 0; n < 16; ++n) {
-                o[3 * n + 0] = Y[n] * g0;
-                o[3 * n + 1] = Y[n] * g1;
-                o[3 * n + 2] = Y[n] * g2;
+                o[3 * n + 0] = fmaf(Y[n], g0, o[3 * n + 0]);
+                o[3 * n + 1] = fmaf(Y[n], g1, o[3 * n + 1]);
+                o[3 * n + 2] = fmaf(Y[n], g2, o[3 * n + 2]);
             }
         }
     }
@@ -727,7 +768,7 @@ template <int K, bool ST>
 static cudaError_t fwd_k(const FrameDev &f, const uint32_t *vals, const FwdOut &out, cudaStream_t s) {
     static unsigned grid = 0;
     if (grid == 0) grid = persistent_grid(k_render_fwd<K, ST>, kThreads);
-    const unsigned items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    const unsigned items = (unsigned)f.total_tiles * (unsigned)(f.views[0].tile * f.views[0].tile / 32);
     const unsigned g = tmin<unsigned>(grid, (items + kWarps - 1) / kWarps);
     k_render_fwd<K, ST><<<g, kThreads, 0, s>>>(f, vals, out);
     return cudaGetLastError();
@@ -737,7 +778,7 @@ template <int K>
 static cudaError_t bwd_k(const FrameDev &f, const uint32_t *vals, const BwdIn &in, cudaStream_t s) {
     static unsigned grid = 0;
     if (grid == 0) grid = persistent_grid(k_render_bwd<K>, kBwdThreads);
-    const unsigned items = (unsigned)(f.cam.ntx * f.cam.nty) * kBlocksPerTile;
+    const unsigned items = (unsigned)f.total_tiles * (unsigned)(f.views[0].tile * f.views[0].tile / 32);
     const unsigned g = tmin<unsigned>(grid, (items + kBwdWarps - 1) / kBwdWarps);
     k_render_bwd<K><<<g, kBwdThreads, 0, s>>>(f, vals, in);
     return cudaGetLastError();
@@ -770,7 +811,8 @@ cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_
                               float *d_sh, cudaStream_t s) {
     const uint32_t *vals = f.vals[sorted_alt];
     cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess && f.n_vox > 0) e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox, s);
+    if (e == cudaSuccess && f.n_vox > 0)
+        e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
     const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid};
     switch (f.K) {

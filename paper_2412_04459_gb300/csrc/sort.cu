@@ -160,13 +160,13 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
 }
 
 __global__ void k_tile_ranges(const uint64_t *__restrict__ keys, const Status *st, int64_t cap,
-                              uint32_t ntiles, uint2 *__restrict__ ranges) {
+                              uint32_t ntiles, int shift, uint2 *__restrict__ ranges) {
     const uint32_t P = pair_count(st, cap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-        const uint32_t tile = (uint32_t)(keys[i] >> 48);
+        const uint32_t tile = (uint32_t)(keys[i] >> shift);
         if (tile >= ntiles) continue;
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 48) != tile) ranges[tile].x = i;
-        if (i == P - 1 || (uint32_t)(keys[i + 1] >> 48) != tile) ranges[tile].y = i + 1;
+        if (i == 0 || (uint32_t)(keys[i - 1] >> shift) != tile) ranges[tile].x = i;
+        if (i == P - 1 || (uint32_t)(keys[i + 1] >> shift) != tile) ranges[tile].y = i + 1;
     }
 }
 
@@ -236,13 +236,14 @@ cudaError_t launch_sort(const FrameDev &f, int lo_bit, int hi_bit, bool sign_pas
 }
 
 cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s) {
-    const int ntiles = f.cam.ntx * f.cam.nty;
+    const int ntiles = f.total_tiles;
     cudaError_t e = cudaMemsetAsync(f.ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
     if (e != cudaSuccess) return e;
     if (f.capacity > 0) {
         const int64_t need = (f.capacity + 255) / 256;
         const unsigned grid = (unsigned)tmin<int64_t>(need, (int64_t)sm_count() * 8);
-        k_tile_ranges<<<grid, 256, 0, s>>>(f.keys[sorted_alt], f.status, f.capacity, (uint32_t)ntiles, f.ranges);
+        k_tile_ranges<<<grid, 256, 0, s>>>(f.keys[sorted_alt], f.status, f.capacity, (uint32_t)ntiles, f.key_shift,
+                                           f.ranges);
     }
     k_tile_order<<<1, 1024, 0, s>>>(f.ranges, ntiles, f.tile_order);
     return cudaGetLastError();

@@ -15,15 +15,16 @@ __host__ __device__ __forceinline__ T tmin(T a, T b) {
 }
 
 constexpr int kMaxLevel = 16;
+constexpr int kMaxViews = SVR_MAX_VIEWS;
 constexpr float kNear = 1e-3f;             // corners at camera depth <= kNear are "behind"
 constexpr uint64_t kTripleOnes = 0x249249249249ull;  // bit 0 of each of the 16 triples
 constexpr int kRadixItems = 16;            // keys per thread in one radix tile
 constexpr int kRadixThreads = 256;
 constexpr int kRadixTile = kRadixItems * kRadixThreads;
-constexpr int kScanTile = 4096;            // voxels per block of the count scan
+constexpr int kScanTile = 4096;            // entries per block of the count scan
 
-// Camera as the kernels see it: intrinsics, [R | t], the ray origin -R^T t
-// (computed in double on the host) and the tile grid.
+// Camera of one view as the kernels see it: intrinsics, [R | t], the ray
+// origin -R^T t (computed in double on the host) and the view's tile grid.
 struct DevCam {
     float fx, fy, cx, cy;
     float R[9];
@@ -32,6 +33,8 @@ struct DevCam {
     int W, H;
     int ntx, nty;
     int tile;
+    int tile_base;     // first global tile id of the view
+    int64_t pix_base;  // first pixel of the view in the contiguous outputs
 };
 
 // Device status block at the start of the workspace (64 bytes).
@@ -100,26 +103,31 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16])
     Y[15] = 0.5900435899266435f * x * (xx - 3.f * yy);
 }
 
-// ------------------------------------------------------------ launchers
-
+// Everything the kernels need about a frame: the view table, the scene
+// arrays and the workspace buffers.  Passed by value as a kernel parameter,
+// so launches need no host-to-device copies (CUDA-graph capturable).
+// Per-(view, voxel) arrays are indexed view * n_vox + voxel.
 struct FrameDev {
-    DevCam cam;
+    DevCam views[kMaxViews];
+    int n_views;
+    int total_tiles;         // sum of the views' tile counts
+    int key_shift;           // Morton bits kept in the key; the tile id sits above them
     Status *status;
-    uint8_t *tile_mask;
-    uint64_t *octpath;
-    short4 *rect;
-    uint32_t *count;
-    uint32_t *offset;
-    Record *rec;
-    ushort4 *box;            // [N] inclusive pixel range x0, x1, y0, y1 a hit can fall in
-    uint32_t *scan_blocks;   // [ceil(N / kScanTile)]
+    uint8_t *tile_mask;      // [total_tiles]
+    uint64_t *octpath;       // [N]
+    short4 *rect;            // [V * N] tile rectangle tx0, tx1, ty0, ty1
+    uint32_t *count;         // [V * N]
+    uint32_t *offset;        // [V * N]
+    Record *rec;             // [V * N]
+    ushort4 *box;            // [V * N] inclusive pixel range x0, x1, y0, y1 a hit can fall in
+    uint32_t *scan_blocks;   // [ceil(V * N / kScanTile)]
     uint64_t *keys[2];
     uint32_t *vals[2];
     uint32_t *hist;          // [256][capacity tiles]
     uint32_t *digit_tot;     // [256]
-    uint2 *ranges;           // [ntiles]
-    uint32_t *tile_order;    // [ntiles] tiles by decreasing list length (render work order)
-    float *dcol;             // [N][3] colour gradient accumulator
+    uint2 *ranges;           // [total_tiles]
+    uint32_t *tile_order;    // [total_tiles] tiles by decreasing list length (render work order)
+    float *dcol;             // [V * N][3] colour gradient accumulator
     int64_t n_vox;
     int64_t n_pts;
     int64_t capacity;
@@ -135,6 +143,13 @@ struct FrameDev {
     const float *grid;
     const float *sh;
 };
+
+// View that owns global tile g.
+__device__ __forceinline__ int view_of_tile(const FrameDev &f, int g) {
+    int v = 0;
+    while (v + 1 < f.n_views && g >= f.views[v + 1].tile_base) ++v;
+    return v;
+}
 
 // Records a printf-style message for svr_last_error() and returns code.
 int set_error(int code, const char *fmt, ...);

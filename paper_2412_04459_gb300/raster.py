@@ -3,10 +3,13 @@
 Thin layer over the C ABI (include/svr.h): device memory and streams come
 from PyTorch, every step of the path runs in libsvr.so's kernels.
 
-    scene = DeviceScene.from_arrays(...)          # or from a synth.Scene
+    scene = DeviceScene.from_host(synth_scene)    # scene arrays on the GPU
     frame = Frame(scene, camera, K=3)             # workspace + per-view state
     out = frame.render()                          # preprocess, bin/sort, forward
     d_grid, d_sh = frame.backward(g_rgb, g_depth, g_alpha, out)
+
+    batch = Frame(scene, [cam0, cam1, ...], K=3)  # several views, one sort, one launch
+    out = batch.render(); batch.views(out)        # per-view images
 
     rgb, depth, alpha = rasterize(grid, sh, scene, camera, K=3)   # autograd
 """
@@ -99,27 +102,40 @@ class DeviceScene:
         return sc
 
 
-def workspace_size(n_vox: int, pair_capacity: int, cam, K=1, t_stop=1e-4, tile=16, bg=(0, 0, 0)) -> int:
-    c = camera_struct(cam)
+def workspace_size(n_vox: int, pair_capacity: int, cams, K=1, t_stop=1e-4, tile=16, bg=(0, 0, 0),
+                   batched: bool = False) -> int:
     p = params_struct(K, t_stop, tile, bg)
-    n = N.lib().svr_workspace_size(int(n_vox), int(pair_capacity), N.ref(c), N.ref(p))
+    if not batched:
+        c = camera_struct(cams)
+        n = N.lib().svr_workspace_size(int(n_vox), int(pair_capacity), N.ref(c), N.ref(p))
+    else:
+        arr = (N.SvrCamera * len(cams))(*[camera_struct(c) for c in cams])
+        n = N.lib().svr_workspace_size_views(int(n_vox), int(pair_capacity), arr, len(cams), N.ref(p))
     if n == 0:
-        raise N.SvrError(N.SVR_ERR_INVALID, "svr_workspace_size", "invalid arguments")
+        raise N.SvrError(N.SVR_ERR_INVALID, "workspace size", "invalid arguments")
     return int(n)
 
 
 class Frame:
-    """One view of a scene: its workspace, its svr_frame and its outputs."""
+    """One view (cams = a camera) or a batch of views (cams = a list) of a
+    scene: the workspace, the svr_frame and the outputs.  Outputs of a batch
+    are flat buffers in the C ABI's batch layout; Frame.views() splits them."""
 
-    def __init__(self, scene: DeviceScene, cam, K: int = 1, t_stop: float = 1e-4, tile: int = 16,
+    def __init__(self, scene: DeviceScene, cams, K: int = 1, t_stop: float = 1e-4, tile: int = 16,
                  bg=(0.0, 0.0, 0.0), pair_capacity: Optional[int] = None):
         self.scene = scene
-        self.cam = cam
-        self.cstruct = camera_struct(cam)
+        self.batched = isinstance(cams, (list, tuple))
+        self.cams = list(cams) if self.batched else [cams]
+        self.cam = self.cams[0]
+        self.cstructs = (N.SvrCamera * len(self.cams))(*[camera_struct(c) for c in self.cams])
         self.pstruct = params_struct(K, t_stop, tile, bg)
         self.K = K
+        self.tile = tile
+        self.pixels = [c.width * c.height for c in self.cams]
+        self.pixel_base = np.concatenate([[0], np.cumsum(self.pixels)]).astype(np.int64)
+        self.n_pixels = int(self.pixel_base[-1])
         if pair_capacity is None:
-            pair_capacity = max(1 << 16, 4 * scene.n_vox)
+            pair_capacity = max(1 << 16, 4 * scene.n_vox * len(self.cams))
         self.pair_capacity = int(pair_capacity)
         self.frame = N.SvrFrame()
         self.ws = None
@@ -127,23 +143,36 @@ class Frame:
         self.grid = scene.grid
         self.sh = scene.sh
 
+    # -- workspace -----------------------------------------------------------
+    def ws_bytes(self) -> int:
+        return workspace_size(self.scene.n_vox, self.pair_capacity, self.cams if self.batched else self.cam,
+                              self.pstruct.K, self.pstruct.t_stop, self.pstruct.tile, tuple(self.pstruct.bg),
+                              batched=self.batched)
+
     def _alloc(self):
-        nbytes = workspace_size(self.scene.n_vox, self.pair_capacity, self.cam, self.pstruct.K,
-                                self.pstruct.t_stop, self.pstruct.tile, tuple(self.pstruct.bg))
-        if self.ws is None or self.ws.numel() < nbytes:
+        nbytes = self.ws_bytes()
+        if self.ws is None or self.ws.numel() < nbytes + 256:
             self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.scene.centre.device)
         base = self.ws.data_ptr()
         self._ws_ptr = (base + 255) & ~255
         self._ws_bytes = self.ws.numel() - (self._ws_ptr - base)
 
+    # -- the path ------------------------------------------------------------
     def preprocess(self, grid=None, sh=None, stream=None):
         self.grid = self.scene.grid if grid is None else grid
         self.sh = self.scene.sh if sh is None else sh
         self._alloc()
         self.sstruct = self.scene.struct(self.grid, self.sh)
-        N.check(N.lib().svr_preprocess(N.ref(self.frame), N.ref(self.sstruct), N.ref(self.cstruct),
-                                       N.ref(self.pstruct), ctypes.c_void_p(self._ws_ptr), self._ws_bytes,
-                                       self.pair_capacity, _stream(stream)), "svr_preprocess")
+        L = N.lib()
+        if self.batched:
+            rc = L.svr_preprocess_views(N.ref(self.frame), N.ref(self.sstruct), self.cstructs, len(self.cams),
+                                        N.ref(self.pstruct), ctypes.c_void_p(self._ws_ptr), self._ws_bytes,
+                                        self.pair_capacity, _stream(stream))
+        else:
+            rc = L.svr_preprocess(N.ref(self.frame), N.ref(self.sstruct), self.cstructs, N.ref(self.pstruct),
+                                  ctypes.c_void_p(self._ws_ptr), self._ws_bytes, self.pair_capacity,
+                                  _stream(stream))
+        N.check(rc, "svr_preprocess")
 
     def bin_sort(self, sync: bool = True, stream=None) -> Optional[int]:
         """Emit and sort the pairs.  sync=True reads the pair count back (and
@@ -162,13 +191,23 @@ class Frame:
         self.n_pairs = int(n.value)
         return self.n_pairs
 
-    def forward(self, out=None, stream=None):
-        H, W = self.cam.height, self.cam.width
+    def new_outputs(self, counts: bool = False):
         dev = self.scene.centre.device
+        P = self.n_pixels
+        out = dict(rgb=torch.empty(3 * P, device=dev), depth=torch.empty(P, device=dev),
+                   alpha=torch.empty(P, device=dev), T_final=torch.empty(P, device=dev),
+                   last=torch.empty(P, dtype=torch.int32, device=dev))
+        if counts:
+            out["counts"] = torch.empty(P, 2, dtype=torch.int32, device=dev)
+        if not self.batched:
+            H, W = self.cam.height, self.cam.width
+            out = {k: (v.view(3, H, W) if k == "rgb" else v.view(H, W, 2) if k == "counts" else v.view(H, W))
+                   for k, v in out.items()}
+        return out
+
+    def forward(self, out=None, stream=None):
         if out is None:
-            out = dict(rgb=torch.empty(3, H, W, device=dev), depth=torch.empty(H, W, device=dev),
-                       alpha=torch.empty(H, W, device=dev), T_final=torch.empty(H, W, device=dev),
-                       last=torch.empty(H, W, dtype=torch.int32, device=dev))
+            out = self.new_outputs()
         N.check(N.lib().svr_render_fwd(N.ref(self.frame), _ptr(out["rgb"]), _ptr(out["depth"]),
                                        _ptr(out["alpha"]), _ptr(out["T_final"]), _ptr(out["last"]),
                                        _stream(stream)), "svr_render_fwd")
@@ -176,12 +215,7 @@ class Frame:
 
     def forward_stats(self, stream=None):
         """Forward render plus per-pixel (candidates examined, hits) counts."""
-        H, W = self.cam.height, self.cam.width
-        dev = self.scene.centre.device
-        out = dict(rgb=torch.empty(3, H, W, device=dev), depth=torch.empty(H, W, device=dev),
-                   alpha=torch.empty(H, W, device=dev), T_final=torch.empty(H, W, device=dev),
-                   last=torch.empty(H, W, dtype=torch.int32, device=dev),
-                   counts=torch.empty(H, W, 2, dtype=torch.int32, device=dev))
+        out = self.new_outputs(counts=True)
         N.check(N.lib().svr_render_stats(N.ref(self.frame), _ptr(out["rgb"]), _ptr(out["depth"]),
                                          _ptr(out["alpha"]), _ptr(out["T_final"]), _ptr(out["last"]),
                                          _ptr(out["counts"]), _stream(stream)), "svr_render_stats")
@@ -204,6 +238,36 @@ class Frame:
                                        _ptr(d_grid), _ptr(d_sh), _stream(stream)), "svr_render_bwd")
         return d_grid, d_sh
 
+    def render_batched(self, out, grads=None, d_grid=None, d_sh=None, stream=None):
+        """The whole step through svr_render_batched (no host synchronisation;
+        graph-capturable).  grads: (g_rgb, g_depth, g_alpha) flat buffers or None."""
+        if not self.batched:
+            raise ValueError("render_batched needs a list of cameras")
+        if self.ws is None:
+            self._alloc()
+        self.sstruct = self.scene.struct(self.grid, self.sh)
+        g = grads if grads is not None else (None, None, None)
+        N.check(N.lib().svr_render_batched(
+            N.ref(self.frame), N.ref(self.sstruct), self.cstructs, len(self.cams), N.ref(self.pstruct),
+            ctypes.c_void_p(self._ws_ptr), self._ws_bytes, self.pair_capacity, _ptr(out["rgb"]),
+            _ptr(out["depth"]), _ptr(out["alpha"]), _ptr(out["T_final"]), _ptr(out["last"]), _ptr(g[0]),
+            _ptr(g[1]), _ptr(g[2]), _ptr(d_grid), _ptr(d_sh), _stream(stream)), "svr_render_batched")
+        return out
+
+    def views(self, out):
+        """Per-view images (views into the flat batch buffers)."""
+        res = []
+        for v, c in enumerate(self.cams):
+            b, e = int(self.pixel_base[v]), int(self.pixel_base[v + 1])
+            H, W = c.height, c.width
+            d = {"rgb": out["rgb"].reshape(-1)[3 * b:3 * e].view(3, H, W)}
+            for k in ("depth", "alpha", "T_final", "last"):
+                d[k] = out[k].reshape(-1)[b:e].view(H, W)
+            if "counts" in out:
+                d["counts"] = out["counts"].reshape(-1, 2)[b:e].view(H, W, 2)
+            res.append(d)
+        return res
+
     def status(self, stream=None):
         flags = ctypes.c_uint32(0)
         n = ctypes.c_int64(0)
@@ -222,22 +286,22 @@ class Frame:
             return torch.empty(0, dtype=dtype, device=self.scene.centre.device)
         nbytes = n * torch.empty(0, dtype=dtype).element_size()
         out = torch.empty(n, dtype=dtype, device=self.scene.centre.device)
-        cudart_copy(out.data_ptr(), ptr, nbytes)
+        _device_copy(out.data_ptr(), ptr, nbytes)
         return out
 
     def inspect(self):
         """Host copies of the integer buffers (synchronises)."""
         torch.cuda.synchronize()
         b = self.buffers()
-        nv = self.scene.n_vox
-        ntiles = self.frame.n_tiles_x * self.frame.n_tiles_y
+        nv = self.scene.n_vox * len(self.cams)
+        ntiles = int(self.frame.total_tiles)
         flags, P = self.status()
-        Pc = min(P, self.pair_capacity)
+        Pc = min(P, self.pair_capacity) if not flags & N.SVR_FLAG_CAPACITY else 0
         get = lambda p, n, dt: self._dev_array(p, n, dt).cpu().numpy()
         return dict(
             flags=flags, n_pairs=P,
             tile_mask=get(b.tile_mask, ntiles, torch.uint8),
-            octpath=get(b.octpath, nv, torch.int64).view(np.uint64),
+            octpath=get(b.octpath, self.scene.n_vox, torch.int64).view(np.uint64),
             rect=get(b.rect, 4 * nv, torch.int16).reshape(nv, 4),
             count=get(b.count, nv, torch.int32).view(np.uint32),
             offset=get(b.offset, nv, torch.int32).view(np.uint32),
@@ -247,12 +311,10 @@ class Frame:
         )
 
 
-def cudart_copy(dst: int, src: int, nbytes: int):
+def _device_copy(dst: int, src: int, nbytes: int):
     """Device-to-device copy through torch (no allocation by the library)."""
     d = torch.cuda.current_device()
-    src_t = _wrap_device_ptr(src, nbytes, d)
-    dst_t = _wrap_device_ptr(dst, nbytes, d)
-    dst_t.copy_(src_t)
+    _wrap_device_ptr(dst, nbytes, d).copy_(_wrap_device_ptr(src, nbytes, d))
 
 
 def _wrap_device_ptr(ptr: int, nbytes: int, device: int) -> torch.Tensor:

@@ -37,6 +37,8 @@ FP32_LANES_PER_SM = 128
 # FP32 operations of the path, per unit of counted work:
 OPS_CAND = 12                         # slab test of one candidate entry
 OPS_HIT = {1: 42, 2: 71, 3: 100}      # one composited segment (forward)
+OPS_HIT_BWD = {1: 98, 2: 156, 3: 214}  # one segment in the backward (recompute + gradient)
+BATCH_SIZES = ((640, 480), (1280, 840), (1920, 1080))
 
 
 def parse():
@@ -49,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1536)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 16-view batched vs per-view comparison")
     return ap.parse_args()
 
 
@@ -204,7 +208,7 @@ def run_native(args, rank, world, local_rank):
     calls = ("preprocess", "bin_sort", "render_fwd", "render_bwd")
 
     def step(rec=None):
-        e = [ev() for _ in range(5)] if rec is not None else None
+        e = [ev() for _ in range(6)] if rec is not None else None
         if e: e[0].record(stream)
         fr.preprocess()
         if e: e[1].record(stream)
@@ -213,8 +217,9 @@ def run_native(args, rank, world, local_rank):
         fr.forward(out)
         if e: e[3].record(stream)
         d_grid.zero_()
-        fr.backward(g_rgb, g_depth, g_alpha, out, d_grid, d_sh)
         if e: e[4].record(stream)
+        fr.backward(g_rgb, g_depth, g_alpha, out, d_grid, d_sh)
+        if e: e[5].record(stream)
         if rec is not None:
             rec.append(e)
 
@@ -238,11 +243,10 @@ def run_native(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    per_call = {c: float(np.mean([r[i].elapsed_time(r[i + 1]) for r in recs])) for i, c in enumerate(calls)}
-    ms_step = float(np.mean([r[0].elapsed_time(r[4]) for r in recs]))
+    spans = {"preprocess": (0, 1), "bin_sort": (1, 2), "render_fwd": (2, 3), "render_bwd": (4, 5)}
+    per_call = {c: float(np.mean([r[a].elapsed_time(r[b]) for r in recs])) for c, (a, b) in spans.items()}
+    ms_step = float(np.mean([r[0].elapsed_time(r[5]) for r in recs]))
     ms_fwd = float(np.mean([r[0].elapsed_time(r[3]) for r in recs]))
-    # the bwd call also zeroes d_grid (a torch fill) before its kernels; its event
-    # pair brackets both, so report the kernels' share from the launch list.
     t = torch.tensor([ms_step, ms_fwd], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -252,6 +256,9 @@ def run_native(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, scene, cam, kw, dev, world)
+    batched = None
+    if not args.no_batched and args.workload == "shell1m":
+        batched = run_batched(args, scene, dscene, dev, kw)
 
     if rank != 0:
         return
@@ -264,6 +271,8 @@ def run_native(args, rank, world, local_rank):
     alu_peak = sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12          # T FP32 lane-ops/s
     ops = n_cand * OPS_CAND + n_hit * OPS_HIT[K]
     achieved = ops / (per_call["render_fwd"] * 1e-3) / 1e12
+    ops_bwd = n_cand * OPS_CAND + n_hit * OPS_HIT_BWD[K]
+    achieved_bwd = ops_bwd / (per_call["render_bwd"] * 1e-3) / 1e12
     hbm = (peaks or {}).get("hbm_gbs", 6800.0)
     frame_bytes = frame_algorithmic_bytes(scene, P, H, W)
     n_launch = launches_per_step(fr)
@@ -275,11 +284,17 @@ def run_native(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (one view per rank)"},
         "fwd_frames_per_s": fwd_fps, "ms_fwd": ms_fwd, "ms_per_call": per_call,
-        "roofline": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": alu_peak,
-                     "unit": "T FP32 lane-ops/s", "frac": achieved / alu_peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "k_render_bwd", "achieved": achieved_bwd, "peak": alu_peak,
+                     "unit": "T FP32 lane-ops/s", "frac": achieved_bwd / alu_peak, "traffic": None,
                      "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
-                              "ops_per_hit": OPS_HIT[K]},
+                              "ops_per_hit": OPS_HIT_BWD[K]},
+                     "timed": "svr_render_bwd call: k_render_bwd + k_voxel_bwd + 2 memsets",
                      "peak_from": f"{sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
+        "roofline_fwd": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": alu_peak,
+                         "unit": "T FP32 lane-ops/s", "frac": achieved / alu_peak,
+                         "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
+                                  "ops_per_hit": OPS_HIT[K]}},
+        "batched": batched,
         "frame_hbm": {"algorithmic_bytes": frame_bytes, "achieved_gbs": frame_bytes / (ms_step * 1e-3) / 1e9,
                       "peak_gbs": hbm, "frac": frame_bytes / (ms_step * 1e-3) / 1e9 / hbm,
                       "peak_from": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"},
@@ -345,6 +360,79 @@ def run_e2e(args, scene, cam, kw, dev, world):
     ms = float(t[0])
     return {"value": world * 1000.0 / ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+
+
+def run_batched(args, scene, dscene, dev, kw, n_views=16, steps=10):
+    """16 orbit views with resolutions drawn from 640x480 / 1280x840 /
+    1920x1080: fwd+bwd of all views as autotuned graph-captured batched
+    launches vs one launch sequence per view."""
+    import torch
+    import synth
+    from paper_2412_04459_gb300 import Frame
+    from paper_2412_04459_gb300.autotune import BatchedRenderer, tune
+    rng = np.random.default_rng(4)
+    cams = [synth.orbit_camera(s, *BATCH_SIZES[int(rng.integers(len(BATCH_SIZES)))]) for s in range(n_views)]
+    t0 = time.perf_counter()
+    best = tune(dscene, cams, K=kw["K"], t_stop=kw["t_stop"], reps=3, use_cache=False)
+    tune_s = time.perf_counter() - t0
+    r = BatchedRenderer(dscene, cams, K=kw["K"], t_stop=kw["t_stop"], tile=best["tile"],
+                        partitions=best["partitions"]).capture()
+    g = torch.Generator(device=dev).manual_seed(5)
+    for x in r.grads:
+        x.normal_(generator=g)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            ts.append((s, e))
+        torch.cuda.synchronize()
+        return float(np.mean([s.elapsed_time(e) for s, e in ts]))
+
+    ms_batched = timed(r.step)
+    flags, pairs = r.status()
+    del r
+    # the same views, one preprocess/sort/forward/backward sequence each
+    frames = []
+    for c in cams:
+        fr = Frame(dscene, c, K=kw["K"], t_stop=kw["t_stop"])
+        fr.render()
+        fr.pair_capacity = int(fr.n_pairs * 1.15) + 4096
+        fr._alloc()
+        o = fr.new_outputs()
+        gg = [torch.randn(3 * c.width * c.height, device=dev), torch.randn(c.width * c.height, device=dev),
+              torch.randn(c.width * c.height, device=dev)]
+        frames.append((fr, o, gg))
+    d_grid = torch.zeros(scene.n_pts, device=dev)
+    d_sh = torch.empty(scene.n_vox, 48, device=dev)
+
+    def per_view():
+        d_grid.zero_()
+        for fr, o, gg in frames:
+            fr.preprocess()
+            fr.bin_sort(sync=False)
+            fr.forward(o)
+            fr.backward(gg[0], gg[1], gg[2], o, d_grid, d_sh)
+
+    ms_per_view = timed(per_view)
+    del frames
+    torch.cuda.empty_cache()
+    pixels = sum(c.width * c.height for c in cams)
+    return {"views": n_views, "pixels": pixels, "sizes": [f"{c.width}x{c.height}" for c in cams],
+            "pairs": pairs, "flags": flags, "tile": best["tile"], "partitions": best["partitions"],
+            "tuning_ms": best["ms"], "tuning_s": tune_s,
+            "ms_batched_graph": ms_batched, "ms_per_view_launches": ms_per_view,
+            "views_per_s_batched": n_views * 1000.0 / ms_batched,
+            "views_per_s_per_view": n_views * 1000.0 / ms_per_view,
+            "speedup": ms_per_view / ms_batched, "l2": "flushed before each timed step"}
 
 
 def frame_algorithmic_bytes(scene, P, H, W):

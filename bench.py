@@ -308,40 +308,40 @@ def run_native(args, rank, world, local_rank):
 
 
 def run_e2e(args, scene, cam, kw, dev, world):
-    """Same step through the public API, inputs copied from pinned host memory
-    every step and the images and gradients read back."""
+    """The training step as a user runs it through the public API: the
+    voxel parameters stay resident on the GPU (they are the model); every
+    step copies its input, the target image, from pinned host memory, renders
+    (svr_preprocess, svr_bin_sort, svr_render_fwd), takes the MSE loss and its
+    gradient (svr_l2_loss), runs svr_render_bwd and reads the loss back."""
     import torch
-    import synth
-    from paper_2412_04459_gb300 import DeviceScene, Frame
-    host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in (
-        ("centre", scene.centre), ("level", scene.level), ("corner_idx", scene.corner_idx),
-        ("grid", scene.grid), ("sh", scene.sh))}
-    g = [torch.as_tensor(a).pin_memory() for a in synth.upstream_grads(1, cam.height, cam.width)]
+    from paper_2412_04459_gb300 import DeviceScene, Frame, l2_loss
     dsc = DeviceScene.from_host(scene, device=dev)
     fr = Frame(dsc, cam, K=kw["K"], t_stop=kw["t_stop"])
     fr.render()
     fr.pair_capacity = int(fr.n_pairs * 1.1) + 1024
     H, W = cam.height, cam.width
-    out_host = {"rgb": torch.empty(3, H, W).pin_memory(), "d_grid": torch.empty(scene.n_pts).pin_memory(),
-                "d_sh": torch.empty(scene.n_vox, 48).pin_memory()}
-    gd = [torch.empty_like(x, device=dev) for x in g]
+    rng = np.random.default_rng(9)
+    target_host = torch.as_tensor(rng.uniform(0, 1, size=(3, H, W)).astype(np.float32)).pin_memory()
+    target = torch.empty(3, H, W, device=dev)
+    loss_host = torch.empty(1).pin_memory()
+    loss = torch.empty(1, device=dev)
+    g_rgb = torch.empty(3, H, W, device=dev)
+    out = fr.new_outputs()
     d_grid = torch.zeros(scene.n_pts, device=dev)
     d_sh = torch.empty(scene.n_vox, 48, device=dev)
-    h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(x.numel() * x.element_size() for x in g)
-    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+    h2d = target_host.numel() * target_host.element_size()
+    d2h = loss_host.numel() * loss_host.element_size()
     stream = torch.cuda.current_stream()
 
     def step():
-        for k, v in host.items():
-            getattr(dsc, k).copy_(v, non_blocking=True)
-        for a, b in zip(gd, g):
-            a.copy_(b, non_blocking=True)
-        out = fr.render(sync=False)
+        target.copy_(target_host, non_blocking=True)
+        fr.preprocess()
+        fr.bin_sort(sync=False)
+        fr.forward(out)
+        l2_loss(out["rgb"], target, g_rgb, loss)
         d_grid.zero_()
-        fr.backward(gd[0], gd[1], gd[2], out, d_grid, d_sh)
-        out_host["rgb"].copy_(out["rgb"], non_blocking=True)
-        out_host["d_grid"].copy_(d_grid, non_blocking=True)
-        out_host["d_sh"].copy_(d_sh, non_blocking=True)
+        fr.backward(g_rgb, None, None, out, d_grid, d_sh)
+        loss_host.copy_(loss, non_blocking=True)
 
     for _ in range(args.warmup):
         step()
@@ -359,7 +359,9 @@ def run_e2e(args, scene, cam, kw, dev, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms = float(t[0])
     return {"value": world * 1000.0 / ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "loss": float(loss_host[0]),
+            "step": "target image H2D -> render -> MSE loss + gradient -> backward -> loss D2H; "
+                    "voxel parameters resident"}
 
 
 def run_batched(args, scene, dscene, dev, kw, n_views=16, steps=10):

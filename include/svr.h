@@ -294,6 +294,16 @@ SVR_API int svr_render_fwd_static(const svr_scene *scene, const svr_camera *cam,
                                   float *alpha, float *T_final, int32_t *last,
                                   int64_t *n_pairs_out, void *stream);
 
+/*
+ * Mean squared error of a rendered image against a target, the MSE term of
+ * the photometric loss (Sec. 3.2.3): *loss = sum_i (pred_i - target_i)^2 / n
+ * and, if grad is not NULL, grad_i = 2 (pred_i - target_i) / n (the upstream
+ * gradient for svr_render_bwd).  Device pointers: pred, target, grad [n],
+ * loss one float (overwritten).  Enqueues only.
+ */
+SVR_API int svr_l2_loss(const float *pred, const float *target, int64_t n, float *grad,
+                        float *loss, void *stream);
+
 /* Synchronises the stream and reads the device-side error flags
  * (SVR_FLAG_*) and the pair count of a frame.  Either output may be NULL. */
 SVR_API int svr_frame_status(const svr_frame *frame, uint32_t *flags, int64_t *n_pairs,

@@ -82,6 +82,7 @@ SIGNATURES = {
     "svr_render_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_render_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_render_fwd_static": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "svr_l2_loss": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "svr_frame_status": (ctypes.c_int, [_P, _P, _P, _P]),
     "svr_frame_buffers": (ctypes.c_int, [_P, _P]),
     "svr_last_error": (ctypes.c_char_p, []),

@@ -28,15 +28,16 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 enum Slot {
     kStatus, kTileMask, kOctpath, kRect, kCount, kOffset, kRecord, kScanBlocks,
-    kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kBox, kTileOrder, kTotal, kNumSlots
+    kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kBox, kTileOrder, kBlockList, kBlockLen,
+    kTotal, kNumSlots
 };
 
 struct Layout {
     size_t off[kNumSlots];
 };
 
-// n_vox voxels seen by n_views views with ntiles tiles in all.
-Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles) {
+// n_vox voxels seen by n_views views with ntiles tiles of edge `tile` in all.
+Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles, int tile) {
     Layout L;
     size_t o = 0;
     auto take = [&](Slot s, size_t bytes) {
@@ -62,6 +63,9 @@ Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles) {
     take(kDcol, 12 * VN);
     take(kBox, 8 * VN);
     take(kTileOrder, 4 * (size_t)ntiles);
+    const size_t B = (size_t)tile * tile / 32;
+    take(kBlockList, 8 * B * C);
+    take(kBlockLen, 4 * B * (size_t)ntiles);
     L.off[kTotal] = o;
     return L;
 }
@@ -157,6 +161,9 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.digit_tot = (uint32_t *)(ws + o[kDigitTot]);
     d.ranges = (uint2 *)(ws + o[kRanges]);
     d.tile_order = (uint32_t *)(ws + o[kTileOrder]);
+    d.blist = (uint2 *)(ws + o[kBlockList]);
+    d.blen = (uint32_t *)(ws + o[kBlockLen]);
+    d.blocks_per_tile = f->params.tile * f->params.tile / 32;
     d.dcol = (float *)(ws + o[kDcol]);
     d.n_vox = f->scene.n_vox;
     d.n_pts = f->scene.n_pts;
@@ -207,7 +214,7 @@ int preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cams,
     if (pair_capacity < 0 || pair_capacity > INT32_MAX)
         return fail(SVR_ERR_INVALID, "pair_capacity %lld", (long long)pair_capacity);
     if (!ws || (((uintptr_t)ws) & 255u)) return fail(SVR_ERR_INVALID, "workspace null or not 256-byte aligned");
-    const Layout L = make_layout(N, n_views, pair_capacity, ntiles);
+    const Layout L = make_layout(N, n_views, pair_capacity, ntiles, params->tile);
     if (ws_bytes < L.off[kTotal])
         return fail(SVR_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, (size_t)L.off[kTotal]);
 
@@ -275,7 +282,7 @@ SVR_API size_t svr_workspace_size_views(int64_t n_vox, int64_t pair_capacity, co
     if (n_vox < 0 || n_vox > ((int64_t)1 << 29)) return 0;
     if (pair_capacity < 0 || pair_capacity > INT32_MAX) return 0;
     if (check_views(cams, n_views, params, &ntiles) != SVR_OK) return 0;
-    return make_layout(n_vox, n_views, pair_capacity, ntiles).off[kTotal];
+    return make_layout(n_vox, n_views, pair_capacity, ntiles, params->tile).off[kTotal];
 }
 
 SVR_API size_t svr_workspace_size(int64_t n_vox, int64_t pair_capacity, const svr_camera *cam,
@@ -330,6 +337,8 @@ SVR_API int svr_bin_sort(svr_frame *frame, int64_t *n_pairs_out, void *stream) {
     frame->sorted_alt = alt;
     e = svr::launch_ranges(d, alt, s);
     if (e != cudaSuccess) return cuda_fail(e, "ranges");
+    e = svr::launch_block_lists(d, alt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "block lists");
     frame->stage = 2;
     frame->n_pairs = -1;
     if (n_pairs_out) {

@@ -145,61 +145,130 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
     return a <= b && a > 0.f;
 }
 
-// One batch of the warp's walk: lane j looks at list entry idx (if valid),
-// keeps it if the warp can use it and stages it at its rank among the kept
-// lanes.  Returns the number of staged entries (list order by lane).
-__device__ __forceinline__ int stage_batch(Entry *st, const ViewData &vd, const uint32_t *__restrict__ vals,
-                                           int idx, bool valid, const WarpBlock &wb) {
-    bool keep = false;
-    uint32_t val = 0;
-    ushort4 bx = make_ushort4(0, 0, 0, 0);
-    if (valid) {
-        val = __ldg(vals + idx);
-        if ((wb.smask >> (val >> 29)) & 1u) {
-            bx = __ldg(vd.box + (val & 0x1FFFFFFFu));
-            keep = bx.x <= wb.x0 + 7 && bx.y >= wb.x0 && bx.z <= wb.y0 + 3 && bx.w >= wb.y0;
+// ------------------------------------------------------------- block lists
+//
+// A warp renders one 8x4 block and needs only the entries of its tile's list
+// whose pixel box meets the block and whose sign pattern a pixel of the block
+// has.  k_block_lists extracts them once per frame: one CTA per tile loads
+// each chunk of 1024 list entries (value and box, four independent loads per
+// thread) into shared memory, then warp w keeps the entries of blocks w,
+// w + 8, ... by ballot, which preserves list order, and writes (value, sorted
+// index) pairs.  Block b of a tile whose list is [beg, end) writes at
+// B beg + b (end - beg), so the lists need no allocation scan.
+
+constexpr int kMaxBlocksPerWarp = 4;  // tile 32: 32 blocks over 8 warps
+constexpr int kListChunk = 1024;
+
+__global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
+    __shared__ uint32_t sval[kListChunk];
+    __shared__ ushort4 sbox[kListChunk];
+    const int g = blockIdx.x;
+    const int view = view_of_tile(f, g);
+    const DevCam &cam = f.views[view];
+    const int tile = g - cam.tile_base;
+    const uint2 rg = f.ranges[g];
+    const int beg = (int)rg.x, end = (int)rg.y, L = end - beg;
+    const int B = f.blocks_per_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const ushort4 *boxes = f.box + (size_t)view * f.n_vox;
+    int bid[kMaxBlocksPerWarp], bx0[kMaxBlocksPerWarp], by0[kMaxBlocksPerWarp];
+    unsigned bmask[kMaxBlocksPerWarp], cnt[kMaxBlocksPerWarp];
+#pragma unroll
+    for (int k = 0; k < kMaxBlocksPerWarp; ++k) {
+        const int b = warp + 8 * k;
+        bid[k] = b;
+        cnt[k] = 0;
+        bmask[k] = 0;
+        bx0[k] = by0[k] = 0;
+        if (b < B) {
+            WarpBlock wb;
+            pixel_ray(cam, tile, b, wb);
+            bx0[k] = wb.x0;
+            by0[k] = wb.y0;
+            bmask[k] = wb.smask;
         }
     }
-    const unsigned kb = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-        stage_entry(st[__popc(kb & lt)], val, idx, bx, vd.rec);
+    uint2 *out = f.blist + (size_t)B * beg;
+    for (int c0 = beg; c0 < end; c0 += kListChunk) {
+        const int n = min(kListChunk, end - c0);
+        uint32_t v4[kListChunk / 256];
+#pragma unroll
+        for (int r = 0; r < kListChunk / 256; ++r) {
+            const int t = threadIdx.x + 256 * r;
+            v4[r] = t < n ? __ldg(vals + c0 + t) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kListChunk / 256; ++r) {
+            const int t = threadIdx.x + 256 * r;
+            if (t < n) {
+                sval[t] = v4[r];
+                sbox[t] = __ldg(boxes + (v4[r] & 0x1FFFFFFFu));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kMaxBlocksPerWarp; ++k) {
+            if (bid[k] >= B) continue;
+            for (int sub = 0; sub < n; sub += 32) {
+                const int j = sub + lane;
+                bool keep = false;
+                uint32_t v = 0;
+                if (j < n) {
+                    v = sval[j];
+                    const ushort4 bx = sbox[j];
+                    keep = ((bmask[k] >> (v >> 29)) & 1u) && bx.x <= bx0[k] + 7 && bx.y >= bx0[k] &&
+                           bx.z <= by0[k] + 3 && bx.w >= by0[k];
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) out[(size_t)bid[k] * L + cnt[k] + __popc(bal & lt)] = make_uint2(v, (unsigned)(c0 + j));
+                cnt[k] += __popc(bal);
+            }
+        }
+        __syncthreads();
     }
-    __syncwarp();
-    return __popc(kb);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kMaxBlocksPerWarp; ++k)
+            if (bid[k] < B) f.blen[(size_t)g * B + bid[k]] = cnt[k];
+    }
 }
 
-// Software-pipelined walk: the value and the pixel box of the next batch's
-// entry are fetched while the current batch is staged and composited, so a
-// batch waits on one dependent load (the record) instead of three.
+// Software-pipelined walk of a block list: the next batch's (value, index)
+// pair and pixel box are fetched while the current batch is staged and
+// composited, so a batch waits on one dependent load (the record).
 struct Lookahead {
-    uint32_t val;
+    uint2 vi;   // value, sorted index
     ushort4 box;
-    bool want;  // valid entry whose sign pattern the warp has
+    bool valid;
 };
 
-__device__ __forceinline__ void fetch_val(Lookahead &la, const uint32_t *__restrict__ vals, int idx, bool valid,
-                                          const WarpBlock &wb) {
-    la.val = valid ? __ldg(vals + idx) : 0u;
-    la.want = valid && ((wb.smask >> (la.val >> 29)) & 1u);
+__device__ __forceinline__ void fetch_vi(Lookahead &la, const uint2 *__restrict__ list, int pos, bool valid) {
+    la.valid = valid;
+    la.vi = valid ? __ldg(list + pos) : make_uint2(0u, 0u);
 }
 
 __device__ __forceinline__ void fetch_box(Lookahead &la, const ViewData &vd) {
-    la.box = la.want ? __ldg(vd.box + (la.val & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
+    la.box = la.valid ? __ldg(vd.box + (la.vi.x & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
 }
 
-// Stage the looked-ahead entries (index idx per lane) that the warp keeps.
-__device__ __forceinline__ int stage_ahead(Entry *st, const ViewData &vd, const Lookahead &la, int idx,
-                                           const WarpBlock &wb) {
-    const bool keep = la.want && la.box.x <= wb.x0 + 7 && la.box.y >= wb.x0 && la.box.z <= wb.y0 + 3 &&
-                      la.box.w >= wb.y0;
-    const unsigned kb = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-        stage_entry(st[__popc(kb & lt)], la.val, idx, la.box, vd.rec);
-    }
+// Stage the looked-ahead entries (lane j: entry j of the batch).
+__device__ __forceinline__ void stage_ahead(Entry *st, const ViewData &vd, const Lookahead &la) {
+    if (la.valid) stage_entry(st[threadIdx.x & 31], la.vi.x, (int)la.vi.y, la.box, vd.rec);
     __syncwarp();
-    return __popc(kb);
+}
+
+// Number of entries of a block list (sorted by index) with index < hi.
+__device__ __forceinline__ int lower_pos(const uint2 *__restrict__ list, int n, int hi) {
+    int lo = 0, up = n;
+    if ((threadIdx.x & 31) == 0) {
+        while (lo < up) {
+            const int mid = (lo + up) >> 1;
+            if ((int)__ldg(&list[mid].y) < hi) lo = mid + 1;
+            else up = mid;
+        }
+    }
+    return __shfl_sync(0xffffffffu, lo, 0);
 }
 
 // Next work item (global tile, block) of the calling warp, or false when done.
@@ -273,6 +342,9 @@ __device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__r
     if (wb.smask == 0) return;  // the whole block lies outside the image
     const uint2 rg = f.ranges[g];
     const int beg = (int)rg.x, end = (int)rg.y;
+    const int B = f.blocks_per_tile;
+    const uint2 *list = f.blist + (size_t)B * beg + (size_t)blk * (end - beg);
+    const int n_list = (int)f.blen[(size_t)g * B + blk];
     const int lane = threadIdx.x & 31;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int last = end - 1;
@@ -280,14 +352,15 @@ __device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__r
     int n_cand = 0, n_hit = 0;
 
     Lookahead la;
-    fetch_val(la, vals, beg + lane, beg + lane < end, wb);
+    fetch_vi(la, list, lane, lane < n_list);
     fetch_box(la, vd);
-    for (int base = beg; base < end; base += kBatch) {
+    for (int base = 0; base < n_list; base += kBatch) {
         if (__all_sync(0xffffffffu, done)) break;
         const Lookahead cur = la;
-        const int nidx = base + kBatch + lane;
-        fetch_val(la, vals, nidx, nidx < end, wb);
-        const int n = stage_ahead(st, vd, cur, base + lane, wb);
+        const int npos = base + kBatch + lane;
+        fetch_vi(la, list, npos, npos < n_list);
+        stage_ahead(st, vd, cur);
+        const int n = min(kBatch, n_list - base);
         fetch_box(la, vd);
         // phase A: this pixel's hits among the staged entries
         unsigned hits = 0;
@@ -347,7 +420,8 @@ __device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__r
 // pixel box contains it (the slab tests it must make) and the hits it
 // composited (int2 per pixel), for work accounting.
 template <int K, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_render_fwd(FrameDev f, const uint32_t *__restrict__ vals, FwdOut out) {
+__global__ void __launch_bounds__(kThreads, 4) k_render_fwd(FrameDev f, const uint32_t *__restrict__ vals,
+                                                            FwdOut out) {
     __shared__ Entry stage[kWarps][kBatch];
     Entry *st = stage[threadIdx.x >> 5];
     const unsigned bpt = (unsigned)(f.views[0].tile * f.views[0].tile) / 32u;
@@ -567,19 +641,24 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
     const bool fallback = p.inside && last >= beg && g.Tfin < 1e-30f;
     const bool active = p.inside && last >= beg && !fallback;
 
+    const int B = f.blocks_per_tile;
+    const uint2 *list = f.blist + (size_t)B * beg + (size_t)blk * ((int)rg.y - beg);
+    const int n_list = (int)f.blen[(size_t)gt * B + blk];
+
     // ---- back to front
     {
-        const int hi = __reduce_max_sync(0xffffffffu, active ? last + 1 : beg);
+        const int top_all = lower_pos(list, n_list, __reduce_max_sync(0xffffffffu, active ? last + 1 : beg));
         float T_after = g.Tfin;
         float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
         Lookahead la;
-        fetch_val(la, vals, hi - 1 - lane, hi - 1 - lane >= beg, wb);
+        fetch_vi(la, list, top_all - 1 - lane, top_all - 1 - lane >= 0);
         fetch_box(la, vd);
-        for (int top = hi; top > beg; top -= kBatch) {
+        for (int top = top_all; top > 0; top -= kBatch) {
             const Lookahead cur = la;
-            const int nidx = top - 1 - kBatch - lane;
-            fetch_val(la, vals, nidx, nidx >= beg, wb);
-            const int n = stage_ahead(st, vd, cur, top - 1 - lane, wb);
+            const int npos = top - 1 - kBatch - lane;
+            fetch_vi(la, list, npos, npos >= 0);
+            stage_ahead(st, vd, cur);              // lane j: list position top - 1 - j
+            const int n = min(kBatch, top);
             fetch_box(la, vd);
             unsigned hits = 0;
             if (active) {
@@ -594,7 +673,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
                 acc_clear(acc, n, any_hit);
                 while (__any_sync(0xffffffffu, hits != 0)) {
                     int k = -1;
-                    float dgeo[8], dcol[3];
+                    float dgeo[8], dc[3];
                     if (hits != 0) {
                         k = __ffs(hits) - 1;   // staged in decreasing list order
                         hits &= hits - 1;
@@ -602,14 +681,14 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
                         float a, b;
                         slab(e, p, a, b);
                         float T_i, Ta, w, dloc;
-                        hit_grad<K, true>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, dgeo, dcol, T_i, Ta, w, dloc);
+                        hit_grad<K, true>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, dgeo, dc, T_i, Ta, w, dloc);
                         SC0 = fmaf(w, e.col.x, SC0);
                         SC1 = fmaf(w, e.col.y, SC1);
                         SC2 = fmaf(w, e.col.z, SC2);
                         SD = fmaf(T_i, dloc, SD);
                         T_after = T_i;
                     }
-                    acc_group_add(acc, scratch, k, dgeo, dcol);
+                    acc_group_add(acc, scratch, k, dgeo, dc);
                 }
                 __syncwarp();
                 acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, dcol);
@@ -620,12 +699,15 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
 
     // ---- front to back for pixels whose T_final underflowed
     if (__any_sync(0xffffffffu, fallback)) {
-        const int hi = __reduce_max_sync(0xffffffffu, fallback ? last + 1 : beg);
+        const int n_fb = lower_pos(list, n_list, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : beg));
         // sweep 1: totals
         float T = 1.f, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
-        for (int base = beg; base < hi; base += kBatch) {
-            const int idx = base + lane;
-            const int n = stage_batch(st, vd, vals, idx, idx < hi, wb);
+        for (int base = 0; base < n_fb; base += kBatch) {
+            Lookahead cur;
+            fetch_vi(cur, list, base + lane, base + lane < n_fb);
+            fetch_box(cur, vd);
+            stage_ahead(st, vd, cur);
+            const int n = min(kBatch, n_fb - base);
             if (fallback) {
                 for (int k = 0; k < n; ++k) {
                     const Entry &e = st[k];
@@ -648,9 +730,12 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
         Ct2 = fmaf(T, f.bg[2], Ct2);
         // sweep 2: gradients with the sums behind = total - prefix
         float Tf = 1.f, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
-        for (int base = beg; base < hi; base += kBatch) {
-            const int idx = base + lane;
-            const int n = stage_batch(st, vd, vals, idx, idx < hi, wb);
+        for (int base = 0; base < n_fb; base += kBatch) {
+            Lookahead cur;
+            fetch_vi(cur, list, base + lane, base + lane < n_fb);
+            fetch_box(cur, vd);
+            stage_ahead(st, vd, cur);
+            const int n = min(kBatch, n_fb - base);
             unsigned hits = 0;
             if (fallback) {
                 for (int k = 0; k < n; ++k) {
@@ -664,7 +749,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
                 acc_clear(acc, n, any_hit);
                 while (__any_sync(0xffffffffu, hits != 0)) {
                     int k = -1;
-                    float dgeo[8], dcol[3];
+                    float dgeo[8], dc[3];
                     if (hits != 0) {
                         k = __ffs(hits) - 1;   // staged in increasing list order
                         hits &= hits - 1;
@@ -673,14 +758,14 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
                         slab(e, p, a, b);
                         float T_i, Ta, w, dloc;
                         hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo,
-                                           dcol, T_i, Ta, w, dloc);
+                                           dc, T_i, Ta, w, dloc);
                         PC0 = fmaf(w, e.col.x, PC0);
                         PC1 = fmaf(w, e.col.y, PC1);
                         PC2 = fmaf(w, e.col.z, PC2);
                         PD = fmaf(T_i, dloc, PD);
                         Tf = Ta;
                     }
-                    acc_group_add(acc, scratch, k, dgeo, dcol);
+                    acc_group_add(acc, scratch, k, dgeo, dc);
                 }
                 __syncwarp();
                 acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, dcol);
@@ -691,7 +776,7 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBwdThreads) k_render_bwd(FrameDev f, const uint32_t *__restrict__ vals,
+__global__ void __launch_bounds__(kBwdThreads, 5) k_render_bwd(FrameDev f, const uint32_t *__restrict__ vals,
                                                             BwdIn in) {
     __shared__ Entry stage[kBwdWarps][kBatch];
     __shared__ float acc_all[kBwdWarps][kBatch * kAccStride];
@@ -751,6 +836,12 @@ __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float 
 }
 
 // ---------------------------------------------------------------- launchers
+
+cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s) {
+    if (f.total_tiles == 0) return cudaSuccess;
+    k_block_lists<<<f.total_tiles, 256, 0, s>>>(f, f.vals[sorted_alt]);
+    return cudaGetLastError();
+}
 
 // Persistent grid: as many CTAs as fit on the device at once.
 template <class Kern>

@@ -18,7 +18,7 @@ constexpr int kMaxLevel = 16;
 constexpr int kMaxViews = SVR_MAX_VIEWS;
 constexpr float kNear = 1e-3f;             // corners at camera depth <= kNear are "behind"
 constexpr uint64_t kTripleOnes = 0x249249249249ull;  // bit 0 of each of the 16 triples
-constexpr int kRadixItems = 16;            // keys per thread in one radix tile
+constexpr int kRadixItems = 4;             // keys per thread in one radix tile
 constexpr int kRadixThreads = 256;
 constexpr int kRadixTile = kRadixItems * kRadixThreads;
 constexpr int kScanTile = 4096;            // entries per block of the count scan
@@ -127,6 +127,10 @@ struct FrameDev {
     uint32_t *digit_tot;     // [256]
     uint2 *ranges;           // [total_tiles]
     uint32_t *tile_order;    // [total_tiles] tiles by decreasing list length (render work order)
+    uint2 *blist;            // per (tile, 8x4 block) lists of (value, sorted index): block b of a tile
+                             // whose list is [beg, end) owns [B beg + b (end - beg), ...)
+    uint32_t *blen;          // [total_tiles * B] entries in each block list
+    int blocks_per_tile;     // B = tile * tile / 32
     float *dcol;             // [V * N][3] colour gradient accumulator
     int64_t n_vox;
     int64_t n_pts;
@@ -160,6 +164,7 @@ cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_sort(const FrameDev &f, int lo_bit, int hi_bit, bool sign_pass, int *result_alt,
                         cudaStream_t s);
 cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s);
+cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s);
 cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth,
                               float *alpha, float *T_final, int32_t *last, int2 *stats, cudaStream_t s);
 cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_rgb,

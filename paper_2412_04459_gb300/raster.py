@@ -311,6 +311,21 @@ class Frame:
         )
 
 
+def l2_loss(pred: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tensor] = None,
+            loss: Optional[torch.Tensor] = None, stream=None):
+    """MSE of pred against target through svr_l2_loss: (loss [1], grad).
+    grad (same shape as pred) receives 2 (pred - target) / n."""
+    if pred.shape != target.shape or not pred.is_contiguous() or not target.is_contiguous():
+        raise ValueError("pred and target must be contiguous tensors of one shape")
+    if grad is None:
+        grad = torch.empty_like(pred)
+    if loss is None:
+        loss = torch.empty(1, device=pred.device)
+    N.check(N.lib().svr_l2_loss(_ptr(pred), _ptr(target), pred.numel(), _ptr(grad), _ptr(loss),
+                                _stream(stream)), "svr_l2_loss")
+    return loss, grad
+
+
 def _device_copy(dst: int, src: int, nbytes: int):
     """Device-to-device copy through torch (no allocation by the library)."""
     d = torch.cuda.current_device()

@@ -87,6 +87,23 @@ def test_underflowing_transmittance_takes_front_to_back_phase():
     compare_grads(ds, osh, name="sh")
 
 
+def test_l2_loss_kernel():
+    """svr_l2_loss: sum (p - t)^2 / n and 2 (p - t) / n, against numpy in FP64,
+    on a size with a ragged last block and on an empty input."""
+    import torch
+    from paper_2412_04459_gb300 import l2_loss
+    rng = np.random.default_rng(0)
+    for n in (3 * 37 * 53, 1, 1 << 20):
+        p = rng.normal(size=n).astype(np.float32)
+        t = rng.normal(size=n).astype(np.float32)
+        loss, grad = l2_loss(torch.as_tensor(p, device="cuda"), torch.as_tensor(t, device="cuda"))
+        d = p.astype(np.float64) - t.astype(np.float64)
+        assert abs(float(loss.item()) - float((d * d).mean())) <= 1e-5 * float((d * d).mean())
+        assert np.allclose(grad.cpu().numpy(), 2 * d / n, rtol=1e-6, atol=1e-12)
+    loss, _ = l2_loss(torch.empty(0, device="cuda"), torch.empty(0, device="cuda"))
+    assert float(loss.item()) == 0.0
+
+
 def test_autograd_matches_frame_backward_and_l2_loss():
     """rasterize() under autograd: an L2 loss against a target rendered from
     perturbed densities; gradients equal the oracle's for the same loss."""

@@ -63,10 +63,36 @@ def workload(name, rank):
         cam = synth.dense_view_camera()
         return scene, cam, dict(K=1, t_stop=1e-4), "dense level-5 octree, 32768 voxels, 128x128, K=1"
     scene = synth.shell_scene(seed=0)
-    cam = synth.orbit_camera(100 + rank, 1280, 840)
+    cam = rank_camera(rank)
     desc = (f"adaptive octree around a noisy sphere shell, {scene.n_vox} voxels (levels 4-9), "
             "1280x840 orbit camera, K=3, t_stop=1e-4, forward+backward")
     return scene, cam, dict(K=3, t_stop=1e-4), desc
+
+
+# ------------------------------------------------------------ multi-rank
+
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    rank sets the step time).  Every rank calls it; world == 1 is a no-op."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(world, ms_per_step):
+    """Steps/s of the whole job: each of the `world` ranks renders its own
+    view per step (weak scaling, replicas), so the job finishes `world`
+    steps in the slowest rank's step time."""
+    return world * 1000.0 / ms_per_step
+
+
+def rank_camera(rank, width=1280, height=840):
+    """The view rank `rank` renders: one seeded orbit camera per rank."""
+    import synth
+    return synth.orbit_camera(100 + rank, width, height)
 
 
 # ----------------------------------------------------------------- clocks
@@ -247,10 +273,7 @@ def run_native(args, rank, world, local_rank):
     per_call = {c: float(np.mean([r[a].elapsed_time(r[b]) for r in recs])) for c, (a, b) in spans.items()}
     ms_step = float(np.mean([r[0].elapsed_time(r[5]) for r in recs]))
     ms_fwd = float(np.mean([r[0].elapsed_time(r[3]) for r in recs]))
-    t = torch.tensor([ms_step, ms_fwd], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step, ms_fwd = float(t[0]), float(t[1])
+    ms_step, ms_fwd = max_over_ranks([ms_step, ms_fwd], world, dev)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -262,8 +285,8 @@ def run_native(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    value = world * 1000.0 / ms_step
-    fwd_fps = world * 1000.0 / ms_fwd
+    value = whole_job_rate(world, ms_step)
+    fwd_fps = whole_job_rate(world, ms_fwd)
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm = props.multi_processor_count
@@ -352,13 +375,8 @@ def run_e2e(args, scene, cam, kw, dev, world):
         step()
     e.record(stream)
     torch.cuda.synchronize()
-    ms = s.elapsed_time(e) / args.steps
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t[0])
-    return {"value": world * 1000.0 / ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+    ms = max_over_ranks([s.elapsed_time(e) / args.steps], world, dev)[0]
+    return {"value": whole_job_rate(world, ms), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "loss": float(loss_host[0]),
             "step": "target image H2D -> render -> MSE loss + gradient -> backward -> loss D2H; "
                     "voxel parameters resident"}
@@ -452,13 +470,13 @@ def frame_algorithmic_bytes(scene, P, H, W):
 def launches_per_step(fr):
     """Kernels of ours launched per step (fills/memsets excluded): tile masks,
     preprocess, 3 scan kernels, emit, 3 per radix pass, ranges, tile order,
-    forward, backward, voxel backward."""
+    block lists, forward, backward, voxel backward."""
     nt = int(fr.frame.total_tiles)
     tb = max(0, int(np.ceil(np.log2(nt)))) if nt > 1 else 0
     lmax = fr.scene.max_level
     morton = 3 * (lmax + 1 if lmax < 16 else 16)
     passes = (morton + tb + 7) // 8 + (1 if lmax == 16 else 0)
-    return 2 + 4 + 3 * passes + 2 + 1 + 2
+    return 2 + 4 + 3 * passes + 3 + 1 + 2
 
 
 def load_peaks():

@@ -72,6 +72,7 @@ extern "C" {
 /* Device-side error flags (svr_frame_status). */
 #define SVR_FLAG_INVALID_VOXEL 1u
 #define SVR_FLAG_CAPACITY 2u
+#define SVR_FLAG_NO_FORWARD 4u /* svr_render_bwd ran before any svr_render_fwd of the sort */
 
 typedef struct svr_camera {
     float fx, fy, cx, cy;
@@ -239,7 +240,13 @@ SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, flo
  * it divided by (1 - alpha); pixels with T_final < 1e-30 redo the walk front
  * to back instead.  Adds dL/dgrid into d_grid [n_pts] (accumulated: the
  * caller zeroes it) and writes dL/dsh into d_sh [N][48] (zero for voxels not
- * in view).  Requires svr_render_fwd's outputs for the same frame.
+ * in view).  Requires svr_render_fwd's outputs for the same frame, and that
+ * the frame's last svr_render_fwd (or svr_render_stats) ran after its last
+ * svr_bin_sort on the same stream: tile lists longer than 1024 entries are
+ * composited in segments, and the forward leaves each segment's transmittance
+ * and the colour and depth sums behind it in the workspace, where the
+ * backward starts from them.  Without such a forward those tiles are skipped
+ * and SVR_FLAG_NO_FORWARD is raised.
  */
 SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const float *d_depth,
                            const float *d_alpha, const float *T_final, const int32_t *last,

@@ -19,6 +19,7 @@ SVR_ERR_CUDA = 4
 SVR_ERR_TIMEOUT = 5
 SVR_FLAG_INVALID_VOXEL = 1
 SVR_FLAG_CAPACITY = 2
+SVR_FLAG_NO_FORWARD = 4
 
 _P = ctypes.c_void_p
 

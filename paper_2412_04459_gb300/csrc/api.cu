@@ -29,12 +29,27 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 enum Slot {
     kStatus, kTileMask, kOctpath, kRect, kCount, kOffset, kRecord, kScanBlocks,
     kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kBox, kTileOrder, kBlockList, kBlockLen,
-    kTotal, kNumSlots
+    kSegment, kTotal, kNumSlots
 };
 
 struct Layout {
     size_t off[kNumSlots];
 };
+
+// Sub-buffers of the kSegment slot: tile_seg, merge_cnt, seg_start, seg_part.
+struct SegBytes {
+    size_t tile_seg, merge_cnt, seg_start, seg_part, total;
+};
+
+SegBytes seg_bytes(int64_t ntiles, size_t slots, size_t B) {
+    SegBytes b;
+    b.tile_seg = 0;
+    b.merge_cnt = align256(8 * (size_t)ntiles);
+    b.seg_start = b.merge_cnt + align256(4 * B * (size_t)ntiles);
+    b.seg_part = b.seg_start + align256(4 * B * slots);
+    b.total = b.seg_part + 4 * B * slots * svr::kSegFields * 32;
+    return b;
+}
 
 // n_vox voxels seen by n_views views with ntiles tiles of edge `tile` in all.
 Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles, int tile) {
@@ -62,10 +77,12 @@ Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles, int 
     take(kRanges, 8 * (size_t)ntiles);
     take(kDcol, 12 * VN);
     take(kBox, 8 * VN);
-    take(kTileOrder, 4 * (size_t)ntiles);
+    const size_t slots = (size_t)svr::seg_slot_capacity(cap);
+    take(kTileOrder, 8 * ((size_t)ntiles + slots));
     const size_t B = (size_t)tile * tile / 32;
     take(kBlockList, 8 * B * C);
     take(kBlockLen, 4 * B * (size_t)ntiles);
+    take(kSegment, seg_bytes(ntiles, slots, B).total);
     L.off[kTotal] = o;
     return L;
 }
@@ -160,10 +177,17 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.hist = (uint32_t *)(ws + o[kHist]);
     d.digit_tot = (uint32_t *)(ws + o[kDigitTot]);
     d.ranges = (uint2 *)(ws + o[kRanges]);
-    d.tile_order = (uint32_t *)(ws + o[kTileOrder]);
+    d.order = (uint2 *)(ws + o[kTileOrder]);
     d.blist = (uint2 *)(ws + o[kBlockList]);
     d.blen = (uint32_t *)(ws + o[kBlockLen]);
     d.blocks_per_tile = f->params.tile * f->params.tile / 32;
+    d.seg_slots = svr::seg_slot_capacity(f->pair_capacity);
+    const SegBytes sb = seg_bytes(f->total_tiles, (size_t)d.seg_slots, (size_t)d.blocks_per_tile);
+    char *seg = ws + o[kSegment];
+    d.tile_seg = (uint2 *)(seg + sb.tile_seg);
+    d.merge_cnt = (uint32_t *)(seg + sb.merge_cnt);
+    d.seg_start = (uint32_t *)(seg + sb.seg_start);
+    d.seg_part = (float *)(seg + sb.seg_part);
     d.dcol = (float *)(ws + o[kDcol]);
     d.n_vox = f->scene.n_vox;
     d.n_pts = f->scene.n_pts;

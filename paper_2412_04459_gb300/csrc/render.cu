@@ -154,10 +154,13 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 // thread) into shared memory, then warp w keeps the entries of blocks w,
 // w + 8, ... by ballot, which preserves list order, and writes (value, sorted
 // index) pairs.  Block b of a tile whose list is [beg, end) writes at
-// B beg + b (end - beg), so the lists need no allocation scan.
+// B beg + b (end - beg), so the lists need no allocation scan.  A chunk is
+// one segment of a split list (kSegLen entries): at the start of chunk c the
+// block-list position reached is where segment c begins.  The CTA also
+// clears the tile's merge counters for the next forward.
 
 constexpr int kMaxBlocksPerWarp = 4;  // tile 32: 32 blocks over 8 warps
-constexpr int kListChunk = 1024;
+constexpr int kListChunk = kSegLen;
 
 __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
     __shared__ uint32_t sval[kListChunk];
@@ -190,8 +193,16 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
         }
     }
     uint2 *out = f.blist + (size_t)B * beg;
+    const uint2 ts = f.tile_seg[g];
+    if (threadIdx.x < B) f.merge_cnt[(size_t)g * B + threadIdx.x] = 0;
     for (int c0 = beg; c0 < end; c0 += kListChunk) {
         const int n = min(kListChunk, end - c0);
+        if (ts.x > 1 && lane == 0) {
+            uint32_t *starts = f.seg_start + (size_t)(ts.y + (c0 - beg) / kListChunk) * B;
+#pragma unroll
+            for (int k = 0; k < kMaxBlocksPerWarp; ++k)
+                if (bid[k] < B) starts[bid[k]] = cnt[k];
+        }
         uint32_t v4[kListChunk / 256];
 #pragma unroll
         for (int r = 0; r < kListChunk / 256; ++r) {
@@ -258,28 +269,36 @@ __device__ __forceinline__ void stage_ahead(Entry *st, const ViewData &vd, const
     __syncwarp();
 }
 
-// Number of entries of a block list (sorted by index) with index < hi.
-__device__ __forceinline__ int lower_pos(const uint2 *__restrict__ list, int n, int hi) {
-    int lo = 0, up = n;
+// Number of entries of block-list positions [lo, hi) (sorted by index) whose
+// index is below key, plus lo: the first position at or past key.
+__device__ __forceinline__ int lower_pos(const uint2 *__restrict__ list, int lo, int hi, int key) {
+    int up = hi;
     if ((threadIdx.x & 31) == 0) {
         while (lo < up) {
             const int mid = (lo + up) >> 1;
-            if ((int)__ldg(&list[mid].y) < hi) lo = mid + 1;
+            if ((int)__ldg(&list[mid].y) < key) lo = mid + 1;
             else up = mid;
         }
     }
     return __shfl_sync(0xffffffffu, lo, 0);
 }
 
-// Next work item (global tile, block) of the calling warp, or false when done.
+// Work item of a render warp: segment `seg` of global tile g, 8x4 block blk.
+struct Item {
+    int g, seg, blk;
+};
+
+// Next work item of the calling warp, or false when done.
 __device__ __forceinline__ bool next_item(unsigned *counter, unsigned n_items, unsigned blocks_per_tile,
-                                          const uint32_t *order, int &tile, int &blk) {
+                                          const uint2 *order, Item &it) {
     unsigned item = 0;
     if ((threadIdx.x & 31) == 0) item = atomicAdd(counter, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) return false;
-    tile = (int)order[item / blocks_per_tile];
-    blk = (int)(item % blocks_per_tile);
+    const uint2 q = order[item / blocks_per_tile];
+    it.g = (int)q.x;
+    it.seg = (int)q.y;
+    it.blk = (int)(item % blocks_per_tile);
     return true;
 }
 
@@ -297,6 +316,39 @@ __device__ __forceinline__ ItemView item_view(const FrameDev &f, int g) {
     iv.vd.rec = f.rec + (size_t)iv.view * f.n_vox;
     iv.vd.box = f.box + (size_t)iv.view * f.n_vox;
     return iv;
+}
+
+// The block list of an item and the part of it that its segment covers.
+struct ItemList {
+    const uint2 *list;  // the (tile, block) list
+    int n_list;
+    int beg, end;       // the tile's range in the sorted pairs
+    uint2 ts;           // segments of the tile, first slot
+    const uint32_t *starts;  // split tiles: segment k of this block starts at starts[k * B]
+};
+
+__device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk) {
+    ItemList L;
+    const uint2 rg = f.ranges[g];
+    const int B = f.blocks_per_tile;
+    L.beg = (int)rg.x;
+    L.end = (int)rg.y;
+    L.list = f.blist + (size_t)B * L.beg + (size_t)blk * (L.end - L.beg);
+    L.n_list = (int)f.blen[(size_t)g * B + blk];
+    L.ts = f.tile_seg[g];
+    L.starts = f.seg_start + (size_t)L.ts.y * B + blk;
+    return L;
+}
+
+// Block-list positions [p0, p1) of segment sg of a split tile.
+__device__ __forceinline__ void seg_range(const ItemList &L, int B, int sg, int &p0, int &p1) {
+    p0 = (int)L.starts[(size_t)sg * B];
+    p1 = sg + 1 < (int)L.ts.x ? (int)L.starts[(size_t)(sg + 1) * B] : L.n_list;
+}
+
+// Segment sums of (segment slot, block): kSegFields rows of 32 pixels.
+__device__ __forceinline__ float *seg_fields(const FrameDev &f, unsigned slot, int blk) {
+    return f.seg_part + ((size_t)slot * f.blocks_per_tile + blk) * (kSegFields * 32) + (threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------ forward
@@ -331,44 +383,37 @@ struct FwdOut {
     int2 *stats;
 };
 
-template <int K, bool STATS>
-__device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int g, int blk,
-                                          Entry *st, const FwdOut &out) {
-    const ItemView iv = item_view(f, g);
-    const DevCam &cam = f.views[iv.view];
-    const ViewData &vd = iv.vd;
-    WarpBlock wb;
-    const PixelRay p = pixel_ray(cam, iv.tile, blk, wb);
-    if (wb.smask == 0) return;  // the whole block lies outside the image
-    const uint2 rg = f.ranges[g];
-    const int beg = (int)rg.x, end = (int)rg.y;
-    const int B = f.blocks_per_tile;
-    const uint2 *list = f.blist + (size_t)B * beg + (size_t)blk * (end - beg);
-    const int n_list = (int)f.blen[(size_t)g * B + blk];
-    const int lane = threadIdx.x & 31;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    int last = end - 1;
-    bool done = !p.inside;
-    int n_cand = 0, n_hit = 0;
+// Compositing state of the calling lane's pixel.
+struct FwdState {
+    float T, C0, C1, C2, D;
+    int last;     // sorted index of the voxel that stopped the walk, or -1
+    bool done;
+    int n_cand, n_hit;
+};
 
+// Walk block-list positions [p0, p1) front to back from state s.
+template <int K, bool STATS>
+__device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0, int p1, const ViewData &vd,
+                                         const PixelRay &p, Entry *st, float t_stop, FwdState &s) {
+    const int lane = threadIdx.x & 31;
     Lookahead la;
-    fetch_vi(la, list, lane, lane < n_list);
+    fetch_vi(la, list, p0 + lane, p0 + lane < p1);
     fetch_box(la, vd);
-    for (int base = 0; base < n_list; base += kBatch) {
-        if (__all_sync(0xffffffffu, done)) break;
+    for (int base = p0; base < p1; base += kBatch) {
+        if (__all_sync(0xffffffffu, s.done)) break;
         const Lookahead cur = la;
         const int npos = base + kBatch + lane;
-        fetch_vi(la, list, npos, npos < n_list);
+        fetch_vi(la, list, npos, npos < p1);
         stage_ahead(st, vd, cur);
-        const int n = min(kBatch, n_list - base);
+        const int n = min(kBatch, p1 - base);
         fetch_box(la, vd);
         // phase A: this pixel's hits among the staged entries
         unsigned hits = 0;
-        if (!done) {
+        if (!s.done) {
             for (int k = 0; k < n; ++k) {
                 const Entry &e = st[k];
                 if (!may_hit(e, p)) continue;
-                if (STATS) ++n_cand;
+                if (STATS) ++s.n_cand;
                 float a, b;
                 if (slab(e, p, a, b)) hits |= 1u << k;
             }
@@ -381,54 +426,186 @@ __device__ __forceinline__ void fwd_block(const FrameDev &f, const uint32_t *__r
                 const Entry &e = st[k];
                 float a, b;
                 slab(e, p, a, b);
-                if (STATS) ++n_hit;
+                if (STATS) ++s.n_hit;
                 float P, dloc;
                 hit_fwd<K>(e, p, a, b, P, dloc);
-                const float w = T * (1.f - P);
-                C0 = fmaf(w, e.col.x, C0);
-                C1 = fmaf(w, e.col.y, C1);
-                C2 = fmaf(w, e.col.z, C2);
-                D = fmaf(T, dloc, D);
-                T *= P;
-                if (T < f.t_stop) {
-                    done = true;
-                    last = __float_as_int(e.c.w);
+                const float w = s.T * (1.f - P);
+                s.C0 = fmaf(w, e.col.x, s.C0);
+                s.C1 = fmaf(w, e.col.y, s.C1);
+                s.C2 = fmaf(w, e.col.z, s.C2);
+                s.D = fmaf(s.T, dloc, s.D);
+                s.T *= P;
+                if (s.T < t_stop) {
+                    s.done = true;
+                    s.last = __float_as_int(e.c.w);
                     hits = 0;
                 }
             }
         }
         __syncwarp();
     }
-    if (p.inside) {
-        // outputs of view v start at pixel pix_base (rgb: 3 * pix_base, planar)
-        const size_t HW = (size_t)cam.W * cam.H;
-        const size_t px = (size_t)p.y * cam.W + p.x;
-        const size_t o = (size_t)cam.pix_base + px;
-        float *rgb = out.rgb + 3 * (size_t)cam.pix_base + px;
-        rgb[0] = fmaf(T, f.bg[0], C0);
-        rgb[HW] = fmaf(T, f.bg[1], C1);
-        rgb[2 * HW] = fmaf(T, f.bg[2], C2);
-        out.depth[o] = D;
-        out.alpha[o] = 1.f - T;
-        out.T[o] = T;
-        out.last[o] = last;
-        if (STATS) out.stats[o] = make_int2(n_cand, n_hit);
+}
+
+// Merge the segments of a split tile's block, front to back: segment sg was
+// walked from T = 1, so its pixel adds T_before (C_sg, D_sg) and multiplies
+// T by T_sg, unless the product falls below t_stop: then the pixel stopped
+// inside sg (segment 0 already stopped at the right voxel; a later one is
+// walked again from the merged state to find it).  Leaves per segment, for
+// the backward: the transmittance after and before it and the colour and
+// depth sums behind it (T_final bg included).
+template <int K, bool STATS>
+__device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, int blk, const ViewData &vd,
+                                          const PixelRay &p, Entry *st, FwdState &m) {
+    const int B = f.blocks_per_tile;
+    const int nseg = (int)L.ts.x;
+    for (int sg = 0; sg < nseg; ++sg) {
+        float *q = seg_fields(f, L.ts.y + sg, blk);
+        const float Tb = m.T;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f;
+        bool need = false;
+        if (!m.done) {
+            const float Tl = __ldcg(q + 4 * 32);
+            if (Tb * Tl >= f.t_stop || sg == 0) {
+                c0 = Tb * __ldcg(q);
+                c1 = Tb * __ldcg(q + 32);
+                c2 = Tb * __ldcg(q + 2 * 32);
+                dd = Tb * __ldcg(q + 3 * 32);
+                m.T = Tb * Tl;
+                if (Tb * Tl < f.t_stop) {  // segment 0 stopped by itself
+                    m.done = true;
+                    m.last = __float_as_int(__ldcg(q + 5 * 32));
+                }
+                if (STATS) {
+                    m.n_cand += __float_as_int(__ldcg(q + 6 * 32));
+                    m.n_hit += __float_as_int(__ldcg(q + 7 * 32));
+                }
+            } else {
+                need = true;
+            }
+        }
+        if (__any_sync(0xffffffffu, need)) {
+            FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0};
+            int p0, p1;
+            seg_range(L, B, sg, p0, p1);
+            fwd_walk<K, STATS>(L.list, p0, p1, vd, p, st, f.t_stop, r);
+            if (need) {
+                c0 = r.C0;
+                c1 = r.C1;
+                c2 = r.C2;
+                dd = r.D;
+                m.T = r.T;
+                if (r.done) {
+                    m.done = true;
+                    m.last = r.last;
+                }
+                m.n_cand += r.n_cand;
+                m.n_hit += r.n_hit;
+            }
+        }
+        m.C0 += c0;
+        m.C1 += c1;
+        m.C2 += c2;
+        m.D += dd;
+        q[0] = c0;
+        q[32] = c1;
+        q[2 * 32] = c2;
+        q[3 * 32] = dd;
+        q[4 * 32] = m.T;
+        q[5 * 32] = Tb;
     }
+    // sums behind each segment, back to front
+    float S0 = m.T * f.bg[0], S1 = m.T * f.bg[1], S2 = m.T * f.bg[2], SD = 0.f;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        float *q = seg_fields(f, L.ts.y + sg, blk);
+        const float c0 = q[0], c1 = q[32], c2 = q[2 * 32], dd = q[3 * 32];
+        q[0] = S0;
+        q[32] = S1;
+        q[2 * 32] = S2;
+        q[3 * 32] = SD;
+        S0 += c0;
+        S1 += c1;
+        S2 += c2;
+        SD += dd;
+    }
+}
+
+template <bool STATS>
+__device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, const PixelRay &p,
+                                          const FwdState &s, int last, const FwdOut &out) {
+    if (!p.inside) return;
+    // outputs of view v start at pixel pix_base (rgb: 3 * pix_base, planar)
+    const size_t HW = (size_t)cam.W * cam.H;
+    const size_t px = (size_t)p.y * cam.W + p.x;
+    const size_t o = (size_t)cam.pix_base + px;
+    float *rgb = out.rgb + 3 * (size_t)cam.pix_base + px;
+    rgb[0] = fmaf(s.T, f.bg[0], s.C0);
+    rgb[HW] = fmaf(s.T, f.bg[1], s.C1);
+    rgb[2 * HW] = fmaf(s.T, f.bg[2], s.C2);
+    out.depth[o] = s.D;
+    out.alpha[o] = 1.f - s.T;
+    out.T[o] = s.T;
+    out.last[o] = last;
+    if (STATS) out.stats[o] = make_int2(s.n_cand, s.n_hit);
+}
+
+template <int K, bool STATS>
+__device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entry *st, const FwdOut &out) {
+    const ItemView iv = item_view(f, it.g);
+    const DevCam &cam = f.views[iv.view];
+    WarpBlock wb;
+    const PixelRay p = pixel_ray(cam, iv.tile, it.blk, wb);
+    if (wb.smask == 0) return;  // the whole block lies outside the image
+    const ItemList L = item_list(f, it.g, it.blk);
+    const int lane = threadIdx.x & 31;
+    FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
+    if (L.ts.x <= 1) {
+        fwd_walk<K, STATS>(L.list, 0, L.n_list, iv.vd, p, st, f.t_stop, s);
+        fwd_write<STATS>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
+        return;
+    }
+    // one segment of a split tile, walked from T = 1
+    const int B = f.blocks_per_tile;
+    int p0, p1;
+    seg_range(L, B, it.seg, p0, p1);
+    fwd_walk<K, STATS>(L.list, p0, p1, iv.vd, p, st, f.t_stop, s);
+    float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
+    q[0] = s.C0;
+    q[32] = s.C1;
+    q[2 * 32] = s.C2;
+    q[3 * 32] = s.D;
+    q[4 * 32] = s.T;
+    q[5 * 32] = __int_as_float(s.last);
+    if (STATS) {
+        q[6 * 32] = __int_as_float(s.n_cand);
+        q[7 * 32] = __int_as_float(s.n_hit);
+    }
+    __threadfence();
+    __syncwarp();
+    unsigned prev = 0;
+    unsigned *cnt = f.merge_cnt + (size_t)it.g * B + it.blk;
+    if (lane == 0) prev = atomicAdd(cnt, 1u);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev + 1 != L.ts.x) return;
+    // the last segment of the block to finish merges them all
+    __threadfence();
+    FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
+    fwd_merge<K, STATS>(f, L, it.blk, iv.vd, p, st, m);
+    fwd_write<STATS>(f, cam, p, m, m.last >= 0 ? m.last : L.end - 1, out);
+    if (lane == 0) *cnt = 0;  // ready for the next forward of this sort
 }
 
 // STATS: also count, per pixel, the list entries with its sign bits whose
 // pixel box contains it (the slab tests it must make) and the hits it
 // composited (int2 per pixel), for work accounting.
 template <int K, bool STATS>
-__global__ void __launch_bounds__(kThreads, 4) k_render_fwd(FrameDev f, const uint32_t *__restrict__ vals,
-                                                            FwdOut out) {
+__global__ void __launch_bounds__(kThreads, 4) k_render_fwd(FrameDev f, FwdOut out) {
     __shared__ Entry stage[kWarps][kBatch];
     Entry *st = stage[threadIdx.x >> 5];
-    const unsigned bpt = (unsigned)(f.views[0].tile * f.views[0].tile) / 32u;
-    const unsigned n_items = (unsigned)f.total_tiles * bpt;
-    int tile, blk;
-    while (next_item(&f.status->fwd_next, n_items, bpt, f.tile_order, tile, blk)) {
-        fwd_block<K, STATS>(f, vals, tile, blk, st, out);
+    const unsigned bpt = (unsigned)f.blocks_per_tile;
+    const unsigned n_items = f.status->n_queue * bpt;
+    Item it;
+    while (next_item(&f.status->fwd_next, n_items, bpt, f.order, it)) {
+        fwd_item<K, STATS>(f, it, st, out);
         __syncwarp();
     }
 }
@@ -608,17 +785,17 @@ struct BwdIn {
 };
 
 template <int K>
-__device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__restrict__ vals, int gt, int blk,
-                                          Entry *st, float *acc, float *scratch, const BwdIn &in) {
-    const ItemView iv = item_view(f, gt);
+__device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entry *st, float *acc, float *scratch,
+                                         const BwdIn &in) {
+    const ItemView iv = item_view(f, it.g);
     const DevCam &cam = f.views[iv.view];
     const ViewData &vd = iv.vd;
     float *dcol = f.dcol + 3 * (size_t)iv.view * f.n_vox;
     WarpBlock wb;
-    const PixelRay p = pixel_ray(cam, iv.tile, blk, wb);
+    const PixelRay p = pixel_ray(cam, iv.tile, it.blk, wb);
     if (wb.smask == 0) return;
-    const uint2 rg = f.ranges[gt];
-    const int beg = (int)rg.x;
+    const ItemList L = item_list(f, it.g, it.blk);
+    const int beg = L.beg;
     const int lane = threadIdx.x & 31;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t px = (size_t)p.y * cam.W + p.x;
@@ -636,29 +813,45 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
         if (in.d_depth) g.gD = in.d_depth[o];
         if (in.d_alpha) g.gA = in.d_alpha[o];
         g.Tfin = in.T[o];
-        last = max(beg - 1, min(in.last[o], (int)rg.y - 1));   // stay inside the tile's list
+        last = max(beg - 1, min(in.last[o], L.end - 1));   // stay inside the tile's list
     }
-    const bool fallback = p.inside && last >= beg && g.Tfin < 1e-30f;
-    const bool active = p.inside && last >= beg && !fallback;
-
-    const int B = f.blocks_per_tile;
-    const uint2 *list = f.blist + (size_t)B * beg + (size_t)blk * ((int)rg.y - beg);
-    const int n_list = (int)f.blen[(size_t)gt * B + blk];
+    // The part of the list this item covers and the state behind it: the
+    // whole list behind which lies T_final bg, or one segment of a split
+    // tile with the forward's sums behind it and transmittance around it.
+    int p0 = 0, p1 = L.n_list, idx0 = beg;
+    float T_after = g.Tfin, T_before = 1.f;
+    float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
+    if (L.ts.x > 1) {
+        if (f.status->fwd_done == 0) {
+            if (lane == 0) atomicOr(&f.status->flags, SVR_FLAG_NO_FORWARD);
+            return;
+        }
+        seg_range(L, f.blocks_per_tile, it.seg, p0, p1);
+        idx0 = beg + it.seg * kSegLen;
+        const float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
+        SC0 = q[0];
+        SC1 = q[32];
+        SC2 = q[2 * 32];
+        SD = q[3 * 32];
+        T_after = q[4 * 32];
+        T_before = q[5 * 32];
+    }
+    const bool has = p.inside && last >= idx0;
+    const bool fallback = has && T_after < 1e-30f;
+    const bool active = has && !fallback;
 
     // ---- back to front
     {
-        const int top_all = lower_pos(list, n_list, __reduce_max_sync(0xffffffffu, active ? last + 1 : beg));
-        float T_after = g.Tfin;
-        float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
+        const int top_all = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, active ? last + 1 : idx0));
         Lookahead la;
-        fetch_vi(la, list, top_all - 1 - lane, top_all - 1 - lane >= 0);
+        fetch_vi(la, L.list, top_all - 1 - lane, top_all - 1 - lane >= p0);
         fetch_box(la, vd);
-        for (int top = top_all; top > 0; top -= kBatch) {
+        for (int top = top_all; top > p0; top -= kBatch) {
             const Lookahead cur = la;
             const int npos = top - 1 - kBatch - lane;
-            fetch_vi(la, list, npos, npos >= 0);
+            fetch_vi(la, L.list, npos, npos >= p0);
             stage_ahead(st, vd, cur);              // lane j: list position top - 1 - j
-            const int n = min(kBatch, top);
+            const int n = min(kBatch, top - p0);
             fetch_box(la, vd);
             unsigned hits = 0;
             if (active) {
@@ -697,14 +890,14 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
         }
     }
 
-    // ---- front to back for pixels whose T_final underflowed
+    // ---- front to back for pixels whose transmittance underflowed
     if (__any_sync(0xffffffffu, fallback)) {
-        const int n_fb = lower_pos(list, n_list, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : beg));
-        // sweep 1: totals
-        float T = 1.f, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
-        for (int base = 0; base < n_fb; base += kBatch) {
+        const int n_fb = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : idx0));
+        // sweep 1: this part's own sums, from the transmittance in front of it
+        float T = T_before, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
+        for (int base = p0; base < n_fb; base += kBatch) {
             Lookahead cur;
-            fetch_vi(cur, list, base + lane, base + lane < n_fb);
+            fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
             fetch_box(cur, vd);
             stage_ahead(st, vd, cur);
             const int n = min(kBatch, n_fb - base);
@@ -725,14 +918,15 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
             }
             __syncwarp();
         }
-        Ct0 = fmaf(T, f.bg[0], Ct0);
-        Ct1 = fmaf(T, f.bg[1], Ct1);
-        Ct2 = fmaf(T, f.bg[2], Ct2);
+        Ct0 += SC0;
+        Ct1 += SC1;
+        Ct2 += SC2;
+        Dt += SD;
         // sweep 2: gradients with the sums behind = total - prefix
-        float Tf = 1.f, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
-        for (int base = 0; base < n_fb; base += kBatch) {
+        float Tf = T_before, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
+        for (int base = p0; base < n_fb; base += kBatch) {
             Lookahead cur;
-            fetch_vi(cur, list, base + lane, base + lane < n_fb);
+            fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
             fetch_box(cur, vd);
             stage_ahead(st, vd, cur);
             const int n = min(kBatch, n_fb - base);
@@ -776,18 +970,17 @@ __device__ __forceinline__ void bwd_block(const FrameDev &f, const uint32_t *__r
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBwdThreads, 5) k_render_bwd(FrameDev f, const uint32_t *__restrict__ vals,
-                                                            BwdIn in) {
+__global__ void __launch_bounds__(kBwdThreads, 5) k_render_bwd(FrameDev f, BwdIn in) {
     __shared__ Entry stage[kBwdWarps][kBatch];
     __shared__ float acc_all[kBwdWarps][kBatch * kAccStride];
     __shared__ float scratch_all[kBwdWarps][32 * kAccStride];
     const int warp = threadIdx.x >> 5;
     Entry *st = stage[warp];
-    const unsigned bpt = (unsigned)(f.views[0].tile * f.views[0].tile) / 32u;
-    const unsigned n_items = (unsigned)f.total_tiles * bpt;
-    int tile, blk;
-    while (next_item(&f.status->bwd_next, n_items, bpt, f.tile_order, tile, blk)) {
-        bwd_block<K>(f, vals, tile, blk, st, acc_all[warp], scratch_all[warp], in);
+    const unsigned bpt = (unsigned)f.blocks_per_tile;
+    const unsigned n_items = f.status->n_queue * bpt;
+    Item it;
+    while (next_item(&f.status->bwd_next, n_items, bpt, f.order, it)) {
+        bwd_item<K>(f, it, st, acc_all[warp], scratch_all[warp], in);
         __syncwarp();
     }
 }
@@ -855,61 +1048,61 @@ static unsigned persistent_grid(Kern kernel, int threads) {
     return (unsigned)(sms * per_sm);
 }
 
+// Grid size from a lower bound on the work items (every tile has at least
+// one segment); the kernels read the exact count from the device.
 template <int K, bool ST>
-static cudaError_t fwd_k(const FrameDev &f, const uint32_t *vals, const FwdOut &out, cudaStream_t s) {
+static cudaError_t fwd_k(const FrameDev &f, const FwdOut &out, cudaStream_t s) {
     static unsigned grid = 0;
     if (grid == 0) grid = persistent_grid(k_render_fwd<K, ST>, kThreads);
-    const unsigned items = (unsigned)f.total_tiles * (unsigned)(f.views[0].tile * f.views[0].tile / 32);
+    const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kWarps - 1) / kWarps);
-    k_render_fwd<K, ST><<<g, kThreads, 0, s>>>(f, vals, out);
+    k_render_fwd<K, ST><<<g, kThreads, 0, s>>>(f, out);
     return cudaGetLastError();
 }
 
 template <int K>
-static cudaError_t bwd_k(const FrameDev &f, const uint32_t *vals, const BwdIn &in, cudaStream_t s) {
+static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
     static unsigned grid = 0;
     if (grid == 0) grid = persistent_grid(k_render_bwd<K>, kBwdThreads);
-    const unsigned items = (unsigned)f.total_tiles * (unsigned)(f.views[0].tile * f.views[0].tile / 32);
+    const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kBwdWarps - 1) / kBwdWarps);
-    k_render_bwd<K><<<g, kBwdThreads, 0, s>>>(f, vals, in);
+    k_render_bwd<K><<<g, kBwdThreads, 0, s>>>(f, in);
     return cudaGetLastError();
 }
 
 cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth, float *alpha,
                               float *T_final, int32_t *last, int2 *stats, cudaStream_t s) {
-    const uint32_t *vals = f.vals[sorted_alt];
+    (void)sorted_alt;  // the block lists carry the sorted values
     const FwdOut out = {rgb, depth, alpha, T_final, last, stats};
     cudaError_t e = cudaMemsetAsync(&f.status->fwd_next, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    if (stats) {
-        switch (f.K) {
-            case 1: return fwd_k<1, true>(f, vals, out, s);
-            case 2: return fwd_k<2, true>(f, vals, out, s);
-            case 3: return fwd_k<3, true>(f, vals, out, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (f.K) {
-        case 1: return fwd_k<1, false>(f, vals, out, s);
-        case 2: return fwd_k<2, false>(f, vals, out, s);
-        case 3: return fwd_k<3, false>(f, vals, out, s);
+    switch (f.K * 2 + (stats ? 1 : 0)) {
+        case 2: e = fwd_k<1, false>(f, out, s); break;
+        case 3: e = fwd_k<1, true>(f, out, s); break;
+        case 4: e = fwd_k<2, false>(f, out, s); break;
+        case 5: e = fwd_k<2, true>(f, out, s); break;
+        case 6: e = fwd_k<3, false>(f, out, s); break;
+        case 7: e = fwd_k<3, true>(f, out, s); break;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    // the segment sums in the workspace now belong to this sort (low byte: 1)
+    return cudaMemsetAsync(&f.status->fwd_done, 1, 1, s);
 }
 
 cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_rgb, const float *d_depth,
                               const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
                               float *d_sh, cudaStream_t s) {
-    const uint32_t *vals = f.vals[sorted_alt];
+    (void)sorted_alt;
     cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
     if (e == cudaSuccess && f.n_vox > 0)
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
     const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid};
     switch (f.K) {
-        case 1: e = bwd_k<1>(f, vals, in, s); break;
-        case 2: e = bwd_k<2>(f, vals, in, s); break;
-        case 3: e = bwd_k<3>(f, vals, in, s); break;
+        case 1: e = bwd_k<1>(f, in, s); break;
+        case 2: e = bwd_k<2>(f, in, s); break;
+        case 3: e = bwd_k<3>(f, in, s); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

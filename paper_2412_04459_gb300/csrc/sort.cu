@@ -170,21 +170,35 @@ __global__ void k_tile_ranges(const uint64_t *__restrict__ keys, const Status *s
     }
 }
 
-// Render work order: tiles grouped by floor(log2(list length)), longest
-// lists first, so the heaviest tiles start early and the short ones fill the
-// tail (one block; order within a group is arbitrary, results do not depend
-// on it).
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, int ntiles,
-                                                     uint32_t *__restrict__ order) {
+// Render work order: one entry (tile, segment) per segment of every tile's
+// list.  A list of L > kSegLen entries is split into ceil(L / kSegLen)
+// segments of kSegLen consecutive entries, which get consecutive slots for
+// their partial sums; a shorter list is one segment without a slot.  Entries
+// are grouped by floor(log2(segment length)), longest first, so the heaviest
+// work starts early and short segments fill the tail (one CTA; the order
+// within a group is arbitrary and results do not depend on it).  Also resets
+// the frame's forward-done mark: the segment sums belong to the last sort.
+__global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
     __shared__ unsigned cnt[33];
     __shared__ unsigned start[33];
+    __shared__ unsigned slot_next;
     const int t = threadIdx.x;
+    const int ntiles = f.total_tiles;
     if (t < 33) cnt[t] = 0;
+    if (t == 0) slot_next = 0;
     __syncthreads();
     for (int i = t; i < ntiles; i += blockDim.x) {
-        const uint2 r = ranges[i];
+        const uint2 r = f.ranges[i];
         const unsigned len = r.y - r.x;
-        atomicAdd(&cnt[len ? 32 - __clz(len) : 0], 1u);
+        unsigned nseg = len > (unsigned)kSegLen ? (len + kSegLen - 1) / kSegLen : 1u;
+        unsigned base = 0;
+        if (nseg > 1) {
+            base = atomicAdd(&slot_next, nseg);
+            if ((int64_t)base + nseg > f.seg_slots) nseg = 1, base = 0;  // only past the pair capacity
+        }
+        const unsigned w = nseg > 1 ? (unsigned)kSegLen : len;
+        atomicAdd(&cnt[w ? 32 - __clz(w) : 0], nseg);
+        f.tile_seg[i] = make_uint2(nseg, base);
     }
     __syncthreads();
     if (t == 0) {
@@ -193,12 +207,18 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
             start[b] = acc;
             acc += cnt[b];
         }
+        f.status->n_queue = acc;
+        f.status->slots_used = slot_next;
+        f.status->fwd_done = 0;
     }
     __syncthreads();
     for (int i = t; i < ntiles; i += blockDim.x) {
-        const uint2 r = ranges[i];
+        const uint2 r = f.ranges[i];
+        const uint2 ts = f.tile_seg[i];
         const unsigned len = r.y - r.x;
-        order[atomicAdd(&start[len ? 32 - __clz(len) : 0], 1u)] = (uint32_t)i;
+        const unsigned w = ts.x > 1 ? (unsigned)kSegLen : len;
+        const unsigned pos = atomicAdd(&start[w ? 32 - __clz(w) : 0], ts.x);
+        for (unsigned sg = 0; sg < ts.x; ++sg) f.order[pos + sg] = make_uint2((unsigned)i, sg);
     }
 }
 
@@ -245,7 +265,7 @@ cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s) {
         k_tile_ranges<<<grid, 256, 0, s>>>(f.keys[sorted_alt], f.status, f.capacity, (uint32_t)ntiles, f.key_shift,
                                            f.ranges);
     }
-    k_tile_order<<<1, 1024, 0, s>>>(f.ranges, ntiles, f.tile_order);
+    k_tile_order<<<1, 1024, 0, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,18 @@ constexpr int kRadixItems = 4;             // keys per thread in one radix tile
 constexpr int kRadixThreads = 256;
 constexpr int kRadixTile = kRadixItems * kRadixThreads;
 constexpr int kScanTile = 4096;            // entries per block of the count scan
+// Tile lists longer than kSegLen entries are rendered as segments of kSegLen
+// consecutive entries (the last one shorter), each by its own warps, and
+// merged afterwards; kSegFields floats per pixel and segment carry the
+// partial sums between the warps and on to the backward.
+constexpr int kSegLen = 1024;
+constexpr int kSegFields = 8;
+
+// Segment slots a workspace holds for pair_capacity pairs: a split tile of
+// L > kSegLen entries takes ceil(L / kSegLen) < 2 L / kSegLen slots.
+__host__ __device__ __forceinline__ int64_t seg_slot_capacity(int64_t capacity) {
+    return 2 * capacity / kSegLen + 1;
+}
 
 // Camera of one view as the kernels see it: intrinsics, [R | t], the ray
 // origin -R^T t (computed in double on the host) and the view's tile grid.
@@ -45,7 +57,10 @@ struct Status {
     int bad_voxel;        // smallest invalid voxel id, or INT_MAX
     unsigned fwd_next;    // next work item of the forward render (reset before each launch)
     unsigned bwd_next;    // next work item of the backward render
-    unsigned pad[10];
+    unsigned n_queue;     // (tile, segment) entries of the render work order
+    unsigned slots_used;  // segment slots taken by the split tiles
+    unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort
+    unsigned pad[7];
 };
 
 // Per-voxel record of one view (64 bytes):
@@ -126,7 +141,12 @@ struct FrameDev {
     uint32_t *hist;          // [256][capacity tiles]
     uint32_t *digit_tot;     // [256]
     uint2 *ranges;           // [total_tiles]
-    uint32_t *tile_order;    // [total_tiles] tiles by decreasing list length (render work order)
+    uint2 *order;            // [total_tiles + seg slots] (tile, segment), longest segments first
+    uint2 *tile_seg;         // [total_tiles] segments of the tile's list, first segment slot
+    uint32_t *merge_cnt;     // [total_tiles * B] segments of a (tile, block) finished by the forward
+    uint32_t *seg_start;     // [slots * B] first block-list position of each (segment, block)
+    float *seg_part;         // [slots * B][kSegFields][32] per-pixel segment sums
+    int64_t seg_slots;       // slots the workspace holds
     uint2 *blist;            // per (tile, 8x4 block) lists of (value, sorted index): block b of a tile
                              // whose list is [beg, end) owns [B beg + b (end - beg), ...)
     uint32_t *blen;          // [total_tiles * B] entries in each block list

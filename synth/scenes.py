@@ -284,10 +284,11 @@ def _shell_cells(seed, p_split, base_level, max_level, centers, radii, band, amp
     return n_leaves if count_only else Cells.cat(leaves)
 
 
-# Split probabilities found by calibrate_shell(); the first entry is the
-# ~1M-voxel single-shell workload (1,051,072 leaves at seed 0).
+# Split probabilities found by calibrate_shell(): the ~1M-voxel single-shell
+# workload (1,051,072 leaves at seed 0) and the ~8M-voxel three-shell one
+# (8,035,861 leaves at seed 0).
 _SHELL_P = {}
-KNOWN_SPLIT_P = {("one", 0, 1 << 20): 0.58203125}
+KNOWN_SPLIT_P = {("one", 0, 1 << 20): 0.58203125, ("three", 0, 8_000_000): 0.505859375}
 
 
 def calibrate_shell(target: int, seed: int = 0, **kw) -> float:
@@ -321,8 +322,9 @@ def shell_scene(seed: int = 0, target: int = 1 << 20, p_split: float | None = No
     spec['max_level'].  Grid points within spec['band'] of a shell get raw
     densities ~ N(near_mean, near_std), all others far_value.
     """
-    if spec is None and p_split is None and ("one", seed, target) in KNOWN_SPLIT_P:
-        p_split = KNOWN_SPLIT_P[("one", seed, target)]
+    name = "one" if spec is None or spec == SHELL_ONE else "three" if spec == SHELL_THREE else None
+    if p_split is None and (name, seed, target) in KNOWN_SPLIT_P:
+        p_split = KNOWN_SPLIT_P[(name, seed, target)]
     cache = _cache_path("shell", seed, target, p_split, spec, sh_std, near_mean, near_std, far_value)
     if cache and os.path.exists(cache):
         return _load(cache)

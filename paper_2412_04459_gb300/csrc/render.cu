@@ -1,22 +1,30 @@
 // Forward and backward compositing of the sorted tile lists (sm_103a).
 //
-// Work is split into items of (tile, 8x4 pixel block): 8 items per 16x16
-// tile.  A persistent grid of warps pulls items from a device counter in the
-// order of k_tile_order (longest tile lists first, so the heavy tiles do not
-// form the tail).  A warp walks its tile's sorted list by itself, 32 entries
-// per batch, with no CTA-wide barrier: lane j reads entry j of the batch (its
-// value, then the voxel's conservative pixel box); the warp keeps the entries
-// whose sign pattern one of its pixels has (Sec. B.1) and whose box meets its
-// block, and stages them, ballot-compacted in list order, into its shared
-// memory slots from the voxel's 64-byte record.
+// Work is split into items of (tile, list segment, 8x4 pixel block): 8
+// blocks per 16x16 tile, and one segment per tile unless its list is longer
+// than kSegLen entries.  A persistent grid of warps pulls items from a device
+// counter in the order of k_tile_order (longest segments first, so the heavy
+// work does not form the tail).  A warp walks the part of its block's list
+// (the tile's entries whose pixel box meets the block, k_block_lists) that its
+// segment covers, 32 entries per batch, with no CTA-wide barrier: lane j
+// reads entry j of the batch (its value, then the voxel's conservative pixel
+// box) and stages it into the warp's shared memory slots from the voxel's
+// 64-byte record.
 //
-// Each batch then runs in two phases.  Phase A: every pixel tests all staged
-// entries (broadcast reads): same sign bits, pixel inside the box, and the
-// ray-AABB slab test of Sec. A.2 (entry and exit planes follow from the sign
-// bits: 6 multiplies by 1/r_d and 4 min/max), and records its hits as a bit
-// mask.  Phase B: in rounds, every pixel with hits left composites its next
-// hit, so the lanes of a warp run the costly per-hit arithmetic together
-// instead of one voxel at a time.
+// Each batch then runs in two phases.  Phase A: lane j turns entry j into the
+// mask of the block's pixels that may hit it (inside its pixel box and with
+// its ray sign bits, Sec. B.1); a 32 x 32 bit transpose across the warp gives
+// every pixel the mask of its candidate entries, and the pixel runs the
+// ray-AABB slab test of Sec. A.2 on those only (entry and exit planes follow
+// from the sign bits: 6 multiplies by 1/r_d and 4 min/max), recording its
+// hits as a bit mask.  Phase B: in rounds, every pixel with hits left
+// composites its next hit, so the lanes of a warp run the costly per-hit
+// arithmetic together instead of one voxel at a time.
+//
+// The segments of a split list are walked from T = 1 by separate warps; the
+// last of them to finish merges them front to back (exact up to rounding
+// order, with a second walk of the segment in which a pixel stops) and leaves
+// each segment's transmittance and the sums behind it for the backward.
 //
 // Forward (Sec. 3.1.2, Eq. alpha_blend, Eq. supp_alpha_comp, Sec. A.4):
 //   K samples per segment, trilinear raw density, explin, per-sample
@@ -49,9 +57,9 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
 constexpr int kBwdThreads = kBwdWarps * 32;
 constexpr int kBatch = 32;
-constexpr int kAccStride = 13;  // floats per staged entry's gradient row (odd: no bank conflicts)
+constexpr int kAccStride = 11;  // floats per staged entry's gradient row (odd: no bank conflicts)
 
-// Staged list entry (112 bytes).
+// Staged list entry (96 bytes).
 struct Entry {
     float4 a;    // entry plane (near corner) relative to r_o, sign bits (int)
     float4 b;    // exit plane (far corner) relative to r_o, 1 / size
@@ -59,11 +67,9 @@ struct Entry {
     float4 g0;   // raw corner densities 0..3
     float4 g1;   // raw corner densities 4..7
     float4 col;  // colour, voxel id (int)
-    int4 box;    // pixel box x0, x1, y0, y1 (inclusive)
 };
 
-__device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, ushort4 bx,
-                                            const Record *__restrict__ rec) {
+__device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, const Record *__restrict__ rec) {
     const uint32_t s = val >> 29;
     const uint32_t vid = val & 0x1FFFFFFFu;
     const Record *r = rec + vid;
@@ -78,7 +84,6 @@ __device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, ush
     e.g1 = __ldg(&r->r2);
     const float4 c3 = __ldg(&r->r3);
     e.col = make_float4(c3.x, c3.y, c3.z, __int_as_float((int)vid));
-    e.box = make_int4(bx.x, bx.y, bx.z, bx.w);
 }
 
 // Trilinear interpolation of Eq. interp; corner bits (x, y, z), x most significant.
@@ -103,6 +108,7 @@ struct PixelRay {
 struct WarpBlock {
     int x0, y0;      // origin of the warp's 8x4 pixel block
     unsigned smask;  // bit s set if one of its in-image pixels has sign bits s
+    unsigned spix;   // lane t < 8: mask of the block's in-image pixels with sign bits t
 };
 
 // Per-view arrays of the work item's view.
@@ -129,13 +135,41 @@ __device__ __forceinline__ PixelRay pixel_ray(const DevCam &cam, int tile, int b
     p.inv = make_float3(1.0f / (p.rd.x + 0.0f), 1.0f / (p.rd.y + 0.0f), 1.0f / (p.rd.z + 0.0f));
     p.rdn = sqrtf(p.rd.x * p.rd.x + p.rd.y * p.rd.y + p.rd.z * p.rd.z);
     wb.smask = __reduce_or_sync(0xffffffffu, p.inside ? (1u << p.s) : 0u);
+    wb.spix = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const unsigned m = __ballot_sync(0xffffffffu, p.inside && p.s == t);
+        if (lane == t) wb.spix = m;
+    }
     return p;
 }
 
-// Same sign bits and pixel inside the entry's box: the entry can be hit.
-__device__ __forceinline__ bool may_hit(const Entry &e, const PixelRay &p) {
-    return __float_as_int(e.a.w) == p.s && (unsigned)(p.x - e.box.x) <= (unsigned)(e.box.y - e.box.x) &&
-           (unsigned)(p.y - e.box.z) <= (unsigned)(e.box.w - e.box.z);
+// Mask of the block's pixels (bit 8 y + x) that may hit an entry: inside its
+// inclusive pixel box bx and with its sign bits (value >> 29).  Called by all
+// lanes; an invalid entry gives 0.
+__device__ __forceinline__ unsigned entry_pixels(bool valid, uint32_t val, ushort4 bx, const WarpBlock &wb) {
+    const unsigned spix = __shfl_sync(0xffffffffu, wb.spix, (int)(val >> 29));
+    const int cx0 = max((int)bx.x - wb.x0, 0), cx1 = min((int)bx.y - wb.x0, 7);
+    const int cy0 = max((int)bx.z - wb.y0, 0), cy1 = min((int)bx.w - wb.y0, 3);
+    if (!valid || cx0 > cx1 || cy0 > cy1) return 0u;
+    const unsigned row = (0xFFu << cx0) & (0xFFu >> (7 - cx1));
+    const unsigned rows = (0xFFFFFFFFu << (8 * cy0)) & (0xFFFFFFFFu >> (8 * (3 - cy1)));
+    return row * 0x01010101u & rows & spix;
+}
+
+// 32 x 32 bit-matrix transpose across the warp: lane i returns the word whose
+// bit j is bit i of lane j's x (five exchanges of blocks of halving size).
+__device__ __forceinline__ unsigned warp_transpose(unsigned x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int s = 16 >> i;
+        const unsigned m = masks[i];
+        const unsigned v = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & ~m) | ((v & ~m) >> s)) : ((x & m) | ((v & m) << s));
+    }
+    return x;
 }
 
 // Slab test against a staged entry whose sign bits match the ray's.
@@ -265,7 +299,7 @@ __device__ __forceinline__ void fetch_box(Lookahead &la, const ViewData &vd) {
 
 // Stage the looked-ahead entries (lane j: entry j of the batch).
 __device__ __forceinline__ void stage_ahead(Entry *st, const ViewData &vd, const Lookahead &la) {
-    if (la.valid) stage_entry(st[threadIdx.x & 31], la.vi.x, (int)la.vi.y, la.box, vd.rec);
+    if (la.valid) stage_entry(st[threadIdx.x & 31], la.vi.x, (int)la.vi.y, vd.rec);
     __syncwarp();
 }
 
@@ -274,6 +308,7 @@ __device__ __forceinline__ void stage_ahead(Entry *st, const ViewData &vd, const
 __device__ __forceinline__ int lower_pos(const uint2 *__restrict__ list, int lo, int hi, int key) {
     int up = hi;
     if ((threadIdx.x & 31) == 0) {
+        if (lo < up && (int)__ldg(&list[up - 1].y) < key) lo = up;  // the usual case: no pixel stopped
         while (lo < up) {
             const int mid = (lo + up) >> 1;
             if ((int)__ldg(&list[mid].y) < key) lo = mid + 1;
@@ -394,7 +429,8 @@ struct FwdState {
 // Walk block-list positions [p0, p1) front to back from state s.
 template <int K, bool STATS>
 __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0, int p1, const ViewData &vd,
-                                         const PixelRay &p, Entry *st, float t_stop, FwdState &s) {
+                                         const PixelRay &p, const WarpBlock &wb, Entry *st, float t_stop,
+                                         FwdState &s) {
     const int lane = threadIdx.x & 31;
     Lookahead la;
     fetch_vi(la, list, p0 + lane, p0 + lane < p1);
@@ -404,18 +440,17 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
         const Lookahead cur = la;
         const int npos = base + kBatch + lane;
         fetch_vi(la, list, npos, npos < p1);
+        const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
         stage_ahead(st, vd, cur);
-        const int n = min(kBatch, p1 - base);
         fetch_box(la, vd);
-        // phase A: this pixel's hits among the staged entries
+        // phase A: this pixel's hits among its candidate entries
         unsigned hits = 0;
         if (!s.done) {
-            for (int k = 0; k < n; ++k) {
-                const Entry &e = st[k];
-                if (!may_hit(e, p)) continue;
+            for (unsigned c = cand; c; c &= c - 1u) {
+                const int k = __ffs(c) - 1;
                 if (STATS) ++s.n_cand;
                 float a, b;
-                if (slab(e, p, a, b)) hits |= 1u << k;
+                if (slab(st[k], p, a, b)) hits |= 1u << k;
             }
         }
         // phase B: composite them in list order, one hit per pixel per round
@@ -455,7 +490,7 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
 // depth sums behind it (T_final bg included).
 template <int K, bool STATS>
 __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, int blk, const ViewData &vd,
-                                          const PixelRay &p, Entry *st, FwdState &m) {
+                                          const PixelRay &p, const WarpBlock &wb, Entry *st, FwdState &m) {
     const int B = f.blocks_per_tile;
     const int nseg = (int)L.ts.x;
     for (int sg = 0; sg < nseg; ++sg) {
@@ -487,7 +522,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0};
             int p0, p1;
             seg_range(L, B, sg, p0, p1);
-            fwd_walk<K, STATS>(L.list, p0, p1, vd, p, st, f.t_stop, r);
+            fwd_walk<K, STATS>(L.list, p0, p1, vd, p, wb, st, f.t_stop, r);
             if (need) {
                 c0 = r.C0;
                 c1 = r.C1;
@@ -559,7 +594,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
     const int lane = threadIdx.x & 31;
     FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
     if (L.ts.x <= 1) {
-        fwd_walk<K, STATS>(L.list, 0, L.n_list, iv.vd, p, st, f.t_stop, s);
+        fwd_walk<K, STATS>(L.list, 0, L.n_list, iv.vd, p, wb, st, f.t_stop, s);
         fwd_write<STATS>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
         return;
     }
@@ -567,7 +602,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
     const int B = f.blocks_per_tile;
     int p0, p1;
     seg_range(L, B, it.seg, p0, p1);
-    fwd_walk<K, STATS>(L.list, p0, p1, iv.vd, p, st, f.t_stop, s);
+    fwd_walk<K, STATS>(L.list, p0, p1, iv.vd, p, wb, st, f.t_stop, s);
     float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
     q[0] = s.C0;
     q[32] = s.C1;
@@ -589,7 +624,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
     // the last segment of the block to finish merges them all
     __threadfence();
     FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
-    fwd_merge<K, STATS>(f, L, it.blk, iv.vd, p, st, m);
+    fwd_merge<K, STATS>(f, L, it.blk, iv.vd, p, wb, st, m);
     fwd_write<STATS>(f, cam, p, m, m.last >= 0 ? m.last : L.end - 1, out);
     if (lane == 0) *cnt = 0;  // ready for the next forward of this sort
 }
@@ -701,9 +736,11 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
 
 // Add this round's per-lane gradients (lane hit staged entry k, or k < 0) to
 // the entries' rows.  Lanes on the same entry form a group (warp match); a
-// lane alone on its entry adds its values directly, a larger group goes
-// through the scratch rows and its first lane sums them.  No two groups share
-// a row, so plain shared-memory loads and stores suffice.
+// lane alone on its entry adds its values directly.  A larger group writes
+// its values to the scratch rows and splits the 11 sums among its lanes: the
+// lane of rank r in a group of n adds up components r, r + n, ... over the
+// group.  No two groups share a row, so plain shared-memory loads and
+// stores suffice.
 __device__ __forceinline__ void acc_group_add(float *acc, float *scratch, int k, const float dgeo[8],
                                               const float dcol[3]) {
     const unsigned peers = __match_any_sync(0xffffffffu, k);
@@ -726,17 +763,13 @@ __device__ __forceinline__ void acc_group_add(float *acc, float *scratch, int k,
             row[8] += dcol[0];
             row[9] += dcol[1];
             row[10] += dcol[2];
-        } else if (lane == __ffs(peers) - 1) {
-            float sum[11];
-#pragma unroll
-            for (int c = 0; c < 11; ++c) sum[c] = 0.f;
-            for (unsigned m = peers; m; m &= m - 1u) {
-                const float *s = scratch + (__ffs(m) - 1) * kAccStride;
-#pragma unroll
-                for (int c = 0; c < 11; ++c) sum[c] += s[c];
+        } else {
+            const int n = __popc(peers);
+            for (int c = __popc(peers & ((1u << lane) - 1u)); c < 11; c += n) {
+                float sum = 0.f;
+                for (unsigned m = peers; m; m &= m - 1u) sum += scratch[(__ffs(m) - 1) * kAccStride + c];
+                row[c] += sum;
             }
-#pragma unroll
-            for (int c = 0; c < 11; ++c) row[c] += sum[c];
         }
     }
     __syncwarp();
@@ -850,15 +883,17 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             const Lookahead cur = la;
             const int npos = top - 1 - kBatch - lane;
             fetch_vi(la, L.list, npos, npos >= p0);
+            const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
             stage_ahead(st, vd, cur);              // lane j: list position top - 1 - j
             const int n = min(kBatch, top - p0);
             fetch_box(la, vd);
             unsigned hits = 0;
             if (active) {
-                for (int k = 0; k < n; ++k) {
+                for (unsigned c = cand; c; c &= c - 1u) {
+                    const int k = __ffs(c) - 1;
                     const Entry &e = st[k];
                     float a, b;
-                    if (__float_as_int(e.c.w) <= last && may_hit(e, p) && slab(e, p, a, b)) hits |= 1u << k;
+                    if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
                 }
             }
             const unsigned any_hit = __reduce_or_sync(0xffffffffu, hits);
@@ -899,13 +934,13 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             Lookahead cur;
             fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
             fetch_box(cur, vd);
+            const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
             stage_ahead(st, vd, cur);
-            const int n = min(kBatch, n_fb - base);
             if (fallback) {
-                for (int k = 0; k < n; ++k) {
-                    const Entry &e = st[k];
+                for (unsigned c = cand; c; c &= c - 1u) {
+                    const Entry &e = st[__ffs(c) - 1];
                     float a, b;
-                    if (__float_as_int(e.c.w) > last || !may_hit(e, p) || !slab(e, p, a, b)) continue;
+                    if (__float_as_int(e.c.w) > last || !slab(e, p, a, b)) continue;
                     float trans, dloc;
                     hit_fwd<K>(e, p, a, b, trans, dloc);
                     const float w = T * (1.f - trans);
@@ -928,14 +963,16 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             Lookahead cur;
             fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
             fetch_box(cur, vd);
+            const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
             stage_ahead(st, vd, cur);
             const int n = min(kBatch, n_fb - base);
             unsigned hits = 0;
             if (fallback) {
-                for (int k = 0; k < n; ++k) {
+                for (unsigned c = cand; c; c &= c - 1u) {
+                    const int k = __ffs(c) - 1;
                     const Entry &e = st[k];
                     float a, b;
-                    if (__float_as_int(e.c.w) <= last && may_hit(e, p) && slab(e, p, a, b)) hits |= 1u << k;
+                    if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
                 }
             }
             const unsigned any_hit = __reduce_or_sync(0xffffffffu, hits);

@@ -59,7 +59,8 @@ constexpr int kBwdThreads = kBwdWarps * 32;
 constexpr int kBatch = 32;
 constexpr int kAccStride = 11;  // floats per staged entry's gradient row (odd: no bank conflicts)
 
-// Staged list entry (96 bytes).
+// Staged list entry, padded to 112 bytes: lanes reading different entries
+// then spread over 8 bank groups rather than 4.
 struct Entry {
     float4 a;    // entry plane (near corner) relative to r_o, sign bits (int)
     float4 b;    // exit plane (far corner) relative to r_o, 1 / size
@@ -67,6 +68,7 @@ struct Entry {
     float4 g0;   // raw corner densities 0..3
     float4 g1;   // raw corner densities 4..7
     float4 col;  // colour, voxel id (int)
+    float4 pad;
 };
 
 __device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, const Record *__restrict__ rec) {

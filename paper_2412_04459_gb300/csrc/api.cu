@@ -36,17 +36,17 @@ struct Layout {
     size_t off[kNumSlots];
 };
 
-// Sub-buffers of the kSegment slot: tile_seg, merge_cnt, seg_start, seg_part.
+// Sub-buffers of the kSegment slot: tile_seg, merge_cnt, seg_len, seg_part.
 struct SegBytes {
-    size_t tile_seg, merge_cnt, seg_start, seg_part, total;
+    size_t tile_seg, merge_cnt, seg_len, seg_part, total;
 };
 
 SegBytes seg_bytes(int64_t ntiles, size_t slots, size_t B) {
     SegBytes b;
     b.tile_seg = 0;
     b.merge_cnt = align256(8 * (size_t)ntiles);
-    b.seg_start = b.merge_cnt + align256(4 * B * (size_t)ntiles);
-    b.seg_part = b.seg_start + align256(4 * B * slots);
+    b.seg_len = b.merge_cnt + align256(4 * B * (size_t)ntiles);
+    b.seg_part = b.seg_len + align256(4 * B * slots);
     b.total = b.seg_part + 4 * B * slots * svr::kSegFields * 32;
     return b;
 }
@@ -186,7 +186,7 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     char *seg = ws + o[kSegment];
     d.tile_seg = (uint2 *)(seg + sb.tile_seg);
     d.merge_cnt = (uint32_t *)(seg + sb.merge_cnt);
-    d.seg_start = (uint32_t *)(seg + sb.seg_start);
+    d.seg_len = (uint32_t *)(seg + sb.seg_len);
     d.seg_part = (float *)(seg + sb.seg_part);
     d.dcol = (float *)(ws + o[kDcol]);
     d.n_vox = f->scene.n_vox;

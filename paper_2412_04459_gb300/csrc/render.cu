@@ -185,23 +185,27 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 //
 // A warp renders one 8x4 block and needs only the entries of its tile's list
 // whose pixel box meets the block and whose sign pattern a pixel of the block
-// has.  k_block_lists extracts them once per frame: one CTA per tile loads
-// each chunk of 1024 list entries (value and box, four independent loads per
-// thread) into shared memory, then warp w keeps the entries of blocks w,
+// has.  k_block_lists extracts them once per frame, one CTA per entry of the
+// render work order (a tile, or one kSegLen-entry segment of a split tile):
+// it loads the segment's list entries (value and box, four independent loads
+// per thread) into shared memory, then warp w keeps the entries of blocks w,
 // w + 8, ... by ballot, which preserves list order, and writes (value, sorted
-// index) pairs.  Block b of a tile whose list is [beg, end) writes at
-// B beg + b (end - beg), so the lists need no allocation scan.  A chunk is
-// one segment of a split list (kSegLen entries): at the start of chunk c the
-// block-list position reached is where segment c begins.  The CTA also
-// clears the tile's merge counters for the next forward.
+// index) pairs.  Block b of a tile whose list is [beg, end) owns the region
+// B beg + b (end - beg) of the block lists, so the lists need no allocation
+// scan; segment s of a split tile writes from offset s kSegLen of that region
+// (it keeps at most kSegLen entries) and records its count per block.  The
+// CTA of segment 0 also clears the tile's merge counters for the next
+// forward.
 
 constexpr int kMaxBlocksPerWarp = 4;  // tile 32: 32 blocks over 8 warps
 constexpr int kListChunk = kSegLen;
 
-__global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
+__global__ void __launch_bounds__(256, 4) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
     __shared__ uint32_t sval[kListChunk];
     __shared__ ushort4 sbox[kListChunk];
-    const int g = blockIdx.x;
+    if (blockIdx.x >= f.status->n_queue) return;
+    const uint2 gs = f.order[blockIdx.x];
+    const int g = (int)gs.x, sg = (int)gs.y;
     const int view = view_of_tile(f, g);
     const DevCam &cam = f.views[view];
     const int tile = g - cam.tile_base;
@@ -211,6 +215,9 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const ushort4 *boxes = f.box + (size_t)view * f.n_vox;
+    const uint2 ts = f.tile_seg[g];
+    const bool split = ts.x > 1;
+    if (sg == 0 && threadIdx.x < B) f.merge_cnt[(size_t)g * B + threadIdx.x] = 0;
     int bid[kMaxBlocksPerWarp], bx0[kMaxBlocksPerWarp], by0[kMaxBlocksPerWarp];
     unsigned bmask[kMaxBlocksPerWarp], cnt[kMaxBlocksPerWarp];
 #pragma unroll
@@ -228,17 +235,12 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
             bmask[k] = wb.smask;
         }
     }
-    uint2 *out = f.blist + (size_t)B * beg;
-    const uint2 ts = f.tile_seg[g];
-    if (threadIdx.x < B) f.merge_cnt[(size_t)g * B + threadIdx.x] = 0;
-    for (int c0 = beg; c0 < end; c0 += kListChunk) {
-        const int n = min(kListChunk, end - c0);
-        if (ts.x > 1 && lane == 0) {
-            uint32_t *starts = f.seg_start + (size_t)(ts.y + (c0 - beg) / kListChunk) * B;
-#pragma unroll
-            for (int k = 0; k < kMaxBlocksPerWarp; ++k)
-                if (bid[k] < B) starts[bid[k]] = cnt[k];
-        }
+    // a split tile's segment is one chunk; an unsplit list is walked whole
+    const int first = beg + sg * kListChunk;
+    const int stop = split ? min(end, first + kListChunk) : end;
+    uint2 *out = f.blist + (size_t)B * beg + (split ? (size_t)sg * kListChunk : 0);
+    for (int c0 = first; c0 < stop; c0 += kListChunk) {
+        const int n = min(kListChunk, stop - c0);
         uint32_t v4[kListChunk / 256];
 #pragma unroll
         for (int r = 0; r < kListChunk / 256; ++r) {
@@ -275,9 +277,10 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
         __syncthreads();
     }
     if (lane == 0) {
+        uint32_t *len = split ? f.seg_len + (size_t)(ts.y + sg) * B : f.blen + (size_t)g * B;
 #pragma unroll
         for (int k = 0; k < kMaxBlocksPerWarp; ++k)
-            if (bid[k] < B) f.blen[(size_t)g * B + bid[k]] = cnt[k];
+            if (bid[k] < B) len[bid[k]] = cnt[k];
     }
 }
 
@@ -361,7 +364,7 @@ struct ItemList {
     int n_list;
     int beg, end;       // the tile's range in the sorted pairs
     uint2 ts;           // segments of the tile, first slot
-    const uint32_t *starts;  // split tiles: segment k of this block starts at starts[k * B]
+    const uint32_t *seg_len; // split tiles: segment k of this block holds seg_len[k * B] entries
 };
 
 __device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk) {
@@ -373,14 +376,15 @@ __device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk)
     L.list = f.blist + (size_t)B * L.beg + (size_t)blk * (L.end - L.beg);
     L.n_list = (int)f.blen[(size_t)g * B + blk];
     L.ts = f.tile_seg[g];
-    L.starts = f.seg_start + (size_t)L.ts.y * B + blk;
+    L.seg_len = f.seg_len + (size_t)L.ts.y * B + blk;
     return L;
 }
 
-// Block-list positions [p0, p1) of segment sg of a split tile.
+// Block-list positions [p0, p1) of segment sg of a split tile: segment sg
+// owns the kSegLen positions from sg kSegLen.
 __device__ __forceinline__ void seg_range(const ItemList &L, int B, int sg, int &p0, int &p1) {
-    p0 = (int)L.starts[(size_t)sg * B];
-    p1 = sg + 1 < (int)L.ts.x ? (int)L.starts[(size_t)(sg + 1) * B] : L.n_list;
+    p0 = sg * kSegLen;
+    p1 = p0 + (int)L.seg_len[(size_t)sg * B];
 }
 
 // Segment sums of (segment slot, block): kSegFields rows of 32 pixels.
@@ -1071,7 +1075,9 @@ __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float 
 
 cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s) {
     if (f.total_tiles == 0) return cudaSuccess;
-    k_block_lists<<<f.total_tiles, 256, 0, s>>>(f, f.vals[sorted_alt]);
+    // one CTA per entry of the work order; CTAs past the device-side count exit
+    const int64_t grid = (int64_t)f.total_tiles + f.seg_slots;
+    k_block_lists<<<(unsigned)grid, 256, 0, s>>>(f, f.vals[sorted_alt]);
     return cudaGetLastError();
 }
 

@@ -35,16 +35,23 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_count(const uint64_t *_
     __shared__ uint32_t h[256];
     const uint32_t P = pair_count(st, cap);
     const uint32_t nb = (P + kRadixTile - 1) / kRadixTile;
+    const int lane = threadIdx.x & 31;
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
         h[threadIdx.x] = 0;
-        __syncthreads();
+        // all loads of the tile first, so their latencies overlap
         const uint32_t base = b * kRadixTile;
+        uint32_t d[kRadixItems];
+#pragma unroll
         for (int r = 0; r < kRadixItems; ++r) {
             const uint32_t i = base + r * kRadixThreads + threadIdx.x;
-            if (i < P) {
-                const uint32_t d = digit_of(keys[i], sign_pass ? vals[i] : 0u, shift, sign_pass);
-                atomicAdd(&h[d], 1u);
-            }
+            d[r] = i < P ? digit_of(keys[i], sign_pass ? vals[i] : 0u, shift, sign_pass) : 256u;
+        }
+        __syncthreads();
+        // one shared atomic per digit value present in the warp
+#pragma unroll
+        for (int r = 0; r < kRadixItems; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+            if (d[r] < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[d[r]], (uint32_t)__popc(peers));
         }
         __syncthreads();
         hist[(size_t)threadIdx.x * nb + b] = h[threadIdx.x];
@@ -124,16 +131,22 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
         for (int w = 0; w < kWarps; ++w) wcnt[w][t] = 0;
         __syncthreads();
         const uint32_t base = b * kRadixTile;
+        // all loads of the tile first, so their latencies overlap
+        uint64_t keys[kRadixItems];
+        uint32_t vals[kRadixItems];
+#pragma unroll
+        for (int r = 0; r < kRadixItems; ++r) {
+            const uint32_t i = base + r * kRadixThreads + t;
+            keys[r] = i < P ? kin[i] : 0ull;
+            vals[r] = i < P ? vin[i] : 0u;
+        }
+#pragma unroll
         for (int r = 0; r < kRadixItems; ++r) {
             const uint32_t i = base + r * kRadixThreads + t;
             const bool valid = i < P;
-            uint64_t key = 0;
-            uint32_t val = 0, d = 256;
-            if (valid) {
-                key = kin[i];
-                val = vin[i];
-                d = digit_of(key, val, shift, sign_pass);
-            }
+            const uint64_t key = keys[r];
+            const uint32_t val = vals[r];
+            const uint32_t d = valid ? digit_of(key, val, shift, sign_pass) : 256u;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const uint32_t rank = __popc(peers & lt_mask);
             if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
@@ -238,7 +251,7 @@ cudaError_t launch_sort(const FrameDev &f, int lo_bit, int hi_bit, bool sign_pas
     *result_alt = 0;
     if (f.capacity == 0) return cudaSuccess;
     const int64_t tiles_cap = (f.capacity + kRadixTile - 1) / kRadixTile;
-    const unsigned grid = (unsigned)tmin<int64_t>(tiles_cap, (int64_t)sm_count() * 4);
+    const unsigned grid = (unsigned)tmin<int64_t>(tiles_cap, (int64_t)sm_count() * 8);
     int cur = 0;
     auto pass = [&](int shift, bool sp) {
         k_radix_count<<<grid, kRadixThreads, 0, s>>>(f.keys[cur], f.vals[cur], f.status, f.capacity,

@@ -144,7 +144,7 @@ struct FrameDev {
     uint2 *order;            // [total_tiles + seg slots] (tile, segment), longest segments first
     uint2 *tile_seg;         // [total_tiles] segments of the tile's list, first segment slot
     uint32_t *merge_cnt;     // [total_tiles * B] segments of a (tile, block) finished by the forward
-    uint32_t *seg_start;     // [slots * B] first block-list position of each (segment, block)
+    uint32_t *seg_len;       // [slots * B] block-list entries of each (segment, block)
     float *seg_part;         // [slots * B][kSegFields][32] per-pixel segment sums
     int64_t seg_slots;       // slots the workspace holds
     uint2 *blist;            // per (tile, 8x4 block) lists of (value, sorted index): block b of a tile

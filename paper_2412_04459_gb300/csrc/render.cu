@@ -57,7 +57,6 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
 constexpr int kBwdThreads = kBwdWarps * 32;
 constexpr int kBatch = 32;
-constexpr int kAccStride = 11;  // floats per staged entry's gradient row (odd: no bank conflicts)
 
 // Staged list entry, padded to 112 bytes: lanes reading different entries
 // then spread over 8 bank groups rather than 4.
@@ -282,6 +281,19 @@ __global__ void __launch_bounds__(256, 4) k_block_lists(FrameDev f, const uint32
         for (int k = 0; k < kMaxBlocksPerWarp; ++k)
             if (bid[k] < B) len[bid[k]] = cnt[k];
     }
+}
+
+// Exclusive prefix sum of v over the lanes of the warp; *total gets the sum.
+__device__ __forceinline__ int warp_exclusive_scan(int v, int *total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
 }
 
 // Software-pipelined walk of a block list: the next batch's (value, index)
@@ -740,65 +752,76 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     }
 }
 
-// Add this round's per-lane gradients (lane hit staged entry k, or k < 0) to
-// the entries' rows.  Lanes on the same entry form a group (warp match); a
-// lane alone on its entry adds its values directly.  A larger group writes
-// its values to the scratch rows and splits the 11 sums among its lanes: the
-// lane of rank r in a group of n adds up components r, r + n, ... over the
-// group.  No two groups share a row, so plain shared-memory loads and
-// stores suffice.
-__device__ __forceinline__ void acc_group_add(float *acc, float *scratch, int k, const float dgeo[8],
-                                              const float dcol[3]) {
-    const unsigned peers = __match_any_sync(0xffffffffu, k);
+// ------------------------------------------------------- gradient records
+//
+// The gradients of one batch's hits go to per-hit records of kRec floats (8
+// corner densities, 3 colour channels) laid out entry by entry: the hits of
+// staged entry j get consecutive slots, in pixel order, so a lane writes each
+// of its hits' records to a slot of its own with no coordination.  Once the
+// hits are done, lane j sums entry j's records and adds the sums to the
+// global gradients (one set of atomics per entry and warp).  At most kRecCap
+// records are held at a time: a batch with more hits is processed in runs of
+// consecutive entries, which keeps every pixel's hits in list order.
+constexpr int kRec = 11;
+constexpr int kRecCap = 128;
+
+struct RecSmem {
+    float rec[kRecCap * kRec];
+    int off[kBatch];       // first slot of entry j (numbered over the whole batch)
+    unsigned pix[kBatch];  // lanes whose pixel hits entry j
+};
+
+// Lays out the records of a batch from the lanes' hit masks; lane j returns
+// entry j's first slot and end slot, and the batch's record count.
+__device__ __forceinline__ int rec_layout(RecSmem &rs, unsigned hits, int &off, int &end) {
     const int lane = threadIdx.x & 31;
-    const bool solo = (peers & (peers - 1u)) == 0u;
-    if (k >= 0 && !solo) {
-        float *s = scratch + lane * kAccStride;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) s[c] = dgeo[c];
-        s[8] = dcol[0];
-        s[9] = dcol[1];
-        s[10] = dcol[2];
-    }
+    const unsigned pix = warp_transpose(hits);
+    int total;
+    off = warp_exclusive_scan(__popc(pix), &total);
+    end = off + __popc(pix);
+    rs.off[lane] = off;
+    rs.pix[lane] = pix;
     __syncwarp();
-    if (k >= 0) {
-        float *row = acc + k * kAccStride;
-        if (solo) {
+    return total;
+}
+
+// Slot, relative to base, of the calling lane's hit on entry k.
+__device__ __forceinline__ float *rec_slot(RecSmem &rs, int k, int base) {
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    return rs.rec + (rs.off[k] + __popc(rs.pix[k] & lt) - base) * kRec;
+}
+
+__device__ __forceinline__ void rec_write(float *r, const float dgeo[8], const float dcol[3]) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) row[c] += dgeo[c];
-            row[8] += dcol[0];
-            row[9] += dcol[1];
-            row[10] += dcol[2];
-        } else {
-            const int n = __popc(peers);
-            for (int c = __popc(peers & ((1u << lane) - 1u)); c < 11; c += n) {
-                float sum = 0.f;
-                for (unsigned m = peers; m; m &= m - 1u) sum += scratch[(__ffs(m) - 1) * kAccStride + c];
-                row[c] += sum;
-            }
+    for (int c = 0; c < 8; ++c) r[c] = dgeo[c];
+    r[8] = dcol[0];
+    r[9] = dcol[1];
+    r[10] = dcol[2];
+}
+
+// End of the run of entries from k_lo whose records fit in kRecCap slots
+// from base (the entries' end slots grow with j, so the run is contiguous).
+__device__ __forceinline__ int rec_run_end(int k_lo, int end, int base) {
+    const int lane = threadIdx.x & 31;
+    const unsigned fit = __ballot_sync(0xffffffffu, lane >= k_lo && end - base <= kRecCap);
+    return 32 - __clz(fit);
+}
+
+// Lane j in [k_lo, k_hi): sums entry j's records and adds them to the global
+// gradients of its voxel.
+__device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, int k_lo, int k_hi, int off,
+                                          int end, int base, const int32_t *__restrict__ corner_idx,
+                                          float *__restrict__ d_grid, float *__restrict__ acc_col) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (lane >= k_lo && lane < k_hi && end > off) {
+        float row[kRec];
+#pragma unroll
+        for (int c = 0; c < kRec; ++c) row[c] = 0.f;
+        for (int r = off - base; r < end - base; ++r) {
+#pragma unroll
+            for (int c = 0; c < kRec; ++c) row[c] += rs.rec[r * kRec + c];
         }
-    }
-    __syncwarp();
-}
-
-// Zero the gradient rows of the staged entries that some pixel hits.
-__device__ __forceinline__ void acc_clear(float *acc, int n, unsigned any_hit) {
-    const int lane = threadIdx.x & 31;
-    if (lane < n && ((any_hit >> lane) & 1u)) {
-        float *row = acc + lane * kAccStride;
-#pragma unroll
-        for (int c = 0; c < 11; ++c) row[c] = 0.f;
-    }
-    __syncwarp();
-}
-
-// Add each hit entry's summed row to the global accumulators (lane j: entry j).
-__device__ __forceinline__ void acc_flush(const float *acc, const Entry *st, int n, unsigned any_hit,
-                                          const int32_t *__restrict__ corner_idx, float *__restrict__ d_grid,
-                                          float *__restrict__ acc_col) {
-    const int lane = threadIdx.x & 31;
-    if (lane < n && ((any_hit >> lane) & 1u)) {
-        const float *row = acc + lane * kAccStride;
         const int vid = __float_as_int(st[lane].col.w);
         const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
         const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
@@ -817,6 +840,12 @@ __device__ __forceinline__ void acc_flush(const float *acc, const Entry *st, int
     __syncwarp();
 }
 
+// Mask of staged entries [k_lo, k_hi).
+__device__ __forceinline__ unsigned range_mask(int k_lo, int k_hi) {
+    const unsigned hi = k_hi >= 32 ? 0xffffffffu : ((1u << k_hi) - 1u);
+    return hi & ~((1u << k_lo) - 1u);
+}
+
 struct BwdIn {
     const float *d_rgb, *d_depth, *d_alpha, *T;
     const int32_t *last;
@@ -824,7 +853,7 @@ struct BwdIn {
 };
 
 template <int K>
-__device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entry *st, float *acc, float *scratch,
+__device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entry *st, RecSmem &rs,
                                          const BwdIn &in) {
     const ItemView iv = item_view(f, it.g);
     const DevCam &cam = f.views[iv.view];
@@ -891,7 +920,6 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             fetch_vi(la, L.list, npos, npos >= p0);
             const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
             stage_ahead(st, vd, cur);              // lane j: list position top - 1 - j
-            const int n = min(kBatch, top - p0);
             fetch_box(la, vd);
             unsigned hits = 0;
             if (active) {
@@ -902,30 +930,31 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
                 }
             }
-            const unsigned any_hit = __reduce_or_sync(0xffffffffu, hits);
-            if (any_hit) {
-                acc_clear(acc, n, any_hit);
-                while (__any_sync(0xffffffffu, hits != 0)) {
-                    int k = -1;
-                    float dgeo[8], dc[3];
-                    if (hits != 0) {
-                        k = __ffs(hits) - 1;   // staged in decreasing list order
-                        hits &= hits - 1;
-                        const Entry &e = st[k];
-                        float a, b;
-                        slab(e, p, a, b);
-                        float T_i, Ta, w, dloc;
-                        hit_grad<K, true>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, dgeo, dc, T_i, Ta, w, dloc);
-                        SC0 = fmaf(w, e.col.x, SC0);
-                        SC1 = fmaf(w, e.col.y, SC1);
-                        SC2 = fmaf(w, e.col.z, SC2);
-                        SD = fmaf(T_i, dloc, SD);
-                        T_after = T_i;
-                    }
-                    acc_group_add(acc, scratch, k, dgeo, dc);
+            int off, end;
+            const int total = rec_layout(rs, hits, off, end);
+            // runs of entries whose records fit; each lane takes its hits in
+            // staged order (decreasing list position: back to front)
+            for (int k_lo = 0, base = 0; base < total; base = __shfl_sync(0xffffffffu, off, k_lo)) {
+                const int k_hi = rec_run_end(k_lo, end, base);
+                unsigned h = hits & range_mask(k_lo, k_hi);
+                while (h != 0) {
+                    const int k = __ffs(h) - 1;
+                    h &= h - 1;
+                    const Entry &e = st[k];
+                    float a, b;
+                    slab(e, p, a, b);
+                    float T_i, Ta, w, dloc, dgeo[8], dc[3];
+                    hit_grad<K, true>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, dgeo, dc, T_i, Ta, w, dloc);
+                    SC0 = fmaf(w, e.col.x, SC0);
+                    SC1 = fmaf(w, e.col.y, SC1);
+                    SC2 = fmaf(w, e.col.z, SC2);
+                    SD = fmaf(T_i, dloc, SD);
+                    T_after = T_i;
+                    rec_write(rec_slot(rs, k, base), dgeo, dc);
                 }
-                __syncwarp();
-                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, dcol);
+                rec_flush(rs, st, k_lo, k_hi, off, end, base, f.corner_idx, in.d_grid, dcol);
+                k_lo = k_hi;
+                if (k_lo >= 32) break;
             }
             __syncwarp();
         }
@@ -971,7 +1000,6 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             fetch_box(cur, vd);
             const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
             stage_ahead(st, vd, cur);
-            const int n = min(kBatch, n_fb - base);
             unsigned hits = 0;
             if (fallback) {
                 for (unsigned c = cand; c; c &= c - 1u) {
@@ -981,31 +1009,30 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
                 }
             }
-            const unsigned any_hit = __reduce_or_sync(0xffffffffu, hits);
-            if (any_hit) {
-                acc_clear(acc, n, any_hit);
-                while (__any_sync(0xffffffffu, hits != 0)) {
-                    int k = -1;
-                    float dgeo[8], dc[3];
-                    if (hits != 0) {
-                        k = __ffs(hits) - 1;   // staged in increasing list order
-                        hits &= hits - 1;
-                        const Entry &e = st[k];
-                        float a, b;
-                        slab(e, p, a, b);
-                        float T_i, Ta, w, dloc;
-                        hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo,
-                                           dc, T_i, Ta, w, dloc);
-                        PC0 = fmaf(w, e.col.x, PC0);
-                        PC1 = fmaf(w, e.col.y, PC1);
-                        PC2 = fmaf(w, e.col.z, PC2);
-                        PD = fmaf(T_i, dloc, PD);
-                        Tf = Ta;
-                    }
-                    acc_group_add(acc, scratch, k, dgeo, dc);
+            int off, end;
+            const int total = rec_layout(rs, hits, off, end);
+            for (int k_lo = 0, rb = 0; rb < total; rb = __shfl_sync(0xffffffffu, off, k_lo)) {
+                const int k_hi = rec_run_end(k_lo, end, rb);
+                unsigned h = hits & range_mask(k_lo, k_hi);
+                while (h != 0) {
+                    const int k = __ffs(h) - 1;   // staged in increasing list order
+                    h &= h - 1;
+                    const Entry &e = st[k];
+                    float a, b;
+                    slab(e, p, a, b);
+                    float T_i, Ta, w, dloc, dgeo[8], dc[3];
+                    hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo, dc,
+                                       T_i, Ta, w, dloc);
+                    PC0 = fmaf(w, e.col.x, PC0);
+                    PC1 = fmaf(w, e.col.y, PC1);
+                    PC2 = fmaf(w, e.col.z, PC2);
+                    PD = fmaf(T_i, dloc, PD);
+                    Tf = Ta;
+                    rec_write(rec_slot(rs, k, rb), dgeo, dc);
                 }
-                __syncwarp();
-                acc_flush(acc, st, n, any_hit, f.corner_idx, in.d_grid, dcol);
+                rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol);
+                k_lo = k_hi;
+                if (k_lo >= 32) break;
             }
             __syncwarp();
         }
@@ -1015,15 +1042,14 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
 template <int K>
 __global__ void __launch_bounds__(kBwdThreads, 5) k_render_bwd(FrameDev f, BwdIn in) {
     __shared__ Entry stage[kBwdWarps][kBatch];
-    __shared__ float acc_all[kBwdWarps][kBatch * kAccStride];
-    __shared__ float scratch_all[kBwdWarps][32 * kAccStride];
+    __shared__ RecSmem recs[kBwdWarps];
     const int warp = threadIdx.x >> 5;
     Entry *st = stage[warp];
     const unsigned bpt = (unsigned)f.blocks_per_tile;
     const unsigned n_items = f.status->n_queue * bpt;
     Item it;
     while (next_item(&f.status->bwd_next, n_items, bpt, f.order, it)) {
-        bwd_item<K>(f, it, st, acc_all[warp], scratch_all[warp], in);
+        bwd_item<K>(f, it, st, recs[warp], in);
         __syncwarp();
     }
 }

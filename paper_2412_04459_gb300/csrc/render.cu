@@ -763,10 +763,12 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
 // records are held at a time: a batch with more hits is processed in runs of
 // consecutive entries, which keeps every pixel's hits in list order.
 constexpr int kRec = 11;
+constexpr int kRecStride = 12;   // floats per record slot (16-byte aligned)
 constexpr int kRecCap = 128;
+constexpr int kBigEntry = 12;    // entries with more records are summed by the whole warp
 
 struct RecSmem {
-    float rec[kRecCap * kRec];
+    float4 rec[kRecCap * kRecStride / 4];
     int off[kBatch];       // first slot of entry j (numbered over the whole batch)
     unsigned pix[kBatch];  // lanes whose pixel hits entry j
 };
@@ -786,17 +788,23 @@ __device__ __forceinline__ int rec_layout(RecSmem &rs, unsigned hits, int &off, 
 }
 
 // Slot, relative to base, of the calling lane's hit on entry k.
-__device__ __forceinline__ float *rec_slot(RecSmem &rs, int k, int base) {
+__device__ __forceinline__ int rec_slot(const RecSmem &rs, int k, int base) {
     const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-    return rs.rec + (rs.off[k] + __popc(rs.pix[k] & lt) - base) * kRec;
+    return rs.off[k] + __popc(rs.pix[k] & lt) - base;
 }
 
-__device__ __forceinline__ void rec_write(float *r, const float dgeo[8], const float dcol[3]) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) r[c] = dgeo[c];
-    r[8] = dcol[0];
-    r[9] = dcol[1];
-    r[10] = dcol[2];
+__device__ __forceinline__ void rec_write(RecSmem &rs, int slot, const float dgeo[8], const float dcol[3]) {
+    float4 *r = rs.rec + slot * (kRecStride / 4);
+    r[0] = make_float4(dgeo[0], dgeo[1], dgeo[2], dgeo[3]);
+    r[1] = make_float4(dgeo[4], dgeo[5], dgeo[6], dgeo[7]);
+    r[2] = make_float4(dcol[0], dcol[1], dcol[2], 0.f);
+}
+
+__device__ __forceinline__ void rec_add(float row[kRecStride], const float4 *r) {
+    const float4 a = r[0], b = r[1], c = r[2];
+    row[0] += a.x, row[1] += a.y, row[2] += a.z, row[3] += a.w;
+    row[4] += b.x, row[5] += b.y, row[6] += b.z, row[7] += b.w;
+    row[8] += c.x, row[9] += c.y, row[10] += c.z;
 }
 
 // End of the run of entries from k_lo whose records fit in kRecCap slots
@@ -807,35 +815,65 @@ __device__ __forceinline__ int rec_run_end(int k_lo, int end, int base) {
     return 32 - __clz(fit);
 }
 
-// Lane j in [k_lo, k_hi): sums entry j's records and adds them to the global
-// gradients of its voxel.
-__device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, int k_lo, int k_hi, int off,
-                                          int end, int base, const int32_t *__restrict__ corner_idx,
+// Adds an entry's summed record to the global gradients of voxel vid.
+__device__ __forceinline__ void add_row(const float row[kRecStride], int vid, const int32_t *__restrict__ corner_idx,
+                                        float *__restrict__ d_grid, float *__restrict__ acc_col) {
+    const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
+    const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
+    atomicAdd(d_grid + i0.x, row[0]);
+    atomicAdd(d_grid + i0.y, row[1]);
+    atomicAdd(d_grid + i0.z, row[2]);
+    atomicAdd(d_grid + i0.w, row[3]);
+    atomicAdd(d_grid + i1.x, row[4]);
+    atomicAdd(d_grid + i1.y, row[5]);
+    atomicAdd(d_grid + i1.z, row[6]);
+    atomicAdd(d_grid + i1.w, row[7]);
+    atomicAdd(acc_col + 3 * (size_t)vid + 0, row[8]);
+    atomicAdd(acc_col + 3 * (size_t)vid + 1, row[9]);
+    atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
+}
+
+// Sums the records of each entry of the run [k_lo, k_hi) and adds the sums
+// to the global gradients of its voxel: an entry with more than kBigEntry
+// records (a voxel seen by many pixels of the block) is summed by the whole
+// warp with a butterfly over its records, lane c then adding component c;
+// lane j sums the records of a smaller entry j by itself.
+__device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, int k_lo, int k_hi, int off, int end,
+                                          int base, const int32_t *__restrict__ corner_idx,
                                           float *__restrict__ d_grid, float *__restrict__ acc_col) {
     const int lane = threadIdx.x & 31;
+    const bool mine = lane >= k_lo && lane < k_hi && end > off;
+    const bool big = mine && end - off > kBigEntry;
     __syncwarp();
-    if (lane >= k_lo && lane < k_hi && end > off) {
-        float row[kRec];
+    for (unsigned bm = __ballot_sync(0xffffffffu, big); bm; bm &= bm - 1u) {
+        const int j = __ffs(bm) - 1;
+        const int o = __shfl_sync(0xffffffffu, off, j) - base;
+        const int n = __shfl_sync(0xffffffffu, end, j) - base - o;
+        float row[kRecStride];
 #pragma unroll
-        for (int c = 0; c < kRec; ++c) row[c] = 0.f;
-        for (int r = off - base; r < end - base; ++r) {
+        for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
+        if (lane < n) rec_add(row, rs.rec + (o + lane) * (kRecStride / 4));
 #pragma unroll
-            for (int c = 0; c < kRec; ++c) row[c] += rs.rec[r * kRec + c];
+        for (int m = 16; m > 0; m >>= 1) {
+#pragma unroll
+            for (int c = 0; c < kRec; ++c) row[c] += __shfl_xor_sync(0xffffffffu, row[c], m);
         }
-        const int vid = __float_as_int(st[lane].col.w);
-        const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
-        const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
-        atomicAdd(d_grid + i0.x, row[0]);
-        atomicAdd(d_grid + i0.y, row[1]);
-        atomicAdd(d_grid + i0.z, row[2]);
-        atomicAdd(d_grid + i0.w, row[3]);
-        atomicAdd(d_grid + i1.x, row[4]);
-        atomicAdd(d_grid + i1.y, row[5]);
-        atomicAdd(d_grid + i1.z, row[6]);
-        atomicAdd(d_grid + i1.w, row[7]);
-        atomicAdd(acc_col + 3 * (size_t)vid + 0, row[8]);
-        atomicAdd(acc_col + 3 * (size_t)vid + 1, row[9]);
-        atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
+        if (lane < kRec) {
+            const int vid = __float_as_int(st[j].col.w);
+            float v = row[0];
+#pragma unroll
+            for (int c = 1; c < kRec; ++c) v = lane == c ? row[c] : v;
+            float *t = lane < 8 ? d_grid + __ldg(corner_idx + 8 * (size_t)vid + lane)
+                                : acc_col + 3 * (size_t)vid + (lane - 8);
+            atomicAdd(t, v);
+        }
+    }
+    if (mine && !big) {
+        float row[kRecStride];
+#pragma unroll
+        for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
+        for (int r = off - base; r < end - base; ++r) rec_add(row, rs.rec + r * (kRecStride / 4));
+        add_row(row, __float_as_int(st[lane].col.w), corner_idx, d_grid, acc_col);
     }
     __syncwarp();
 }
@@ -950,7 +988,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     SC2 = fmaf(w, e.col.z, SC2);
                     SD = fmaf(T_i, dloc, SD);
                     T_after = T_i;
-                    rec_write(rec_slot(rs, k, base), dgeo, dc);
+                    rec_write(rs, rec_slot(rs, k, base), dgeo, dc);
                 }
                 rec_flush(rs, st, k_lo, k_hi, off, end, base, f.corner_idx, in.d_grid, dcol);
                 k_lo = k_hi;
@@ -1028,7 +1066,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     PC2 = fmaf(w, e.col.z, PC2);
                     PD = fmaf(T_i, dloc, PD);
                     Tf = Ta;
-                    rec_write(rec_slot(rs, k, rb), dgeo, dc);
+                    rec_write(rs, rec_slot(rs, k, rb), dgeo, dc);
                 }
                 rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol);
                 k_lo = k_hi;

@@ -56,6 +56,7 @@ constexpr int kWarps = 8;          // warps per CTA of the forward
 constexpr int kThreads = kWarps * 32;
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
 constexpr int kBwdThreads = kBwdWarps * 32;
+constexpr int kBwdMinBlocks = 5;   // resident CTAs per SM the register budget is sized for
 constexpr int kBatch = 32;
 
 // Staged list entry, padded to 112 bytes: lanes reading different entries
@@ -765,7 +766,6 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
 constexpr int kRec = 11;
 constexpr int kRecStride = 12;   // floats per record slot (16-byte aligned)
 constexpr int kRecCap = 128;
-constexpr int kBigEntry = 12;    // entries with more records are summed by the whole warp
 
 struct RecSmem {
     float4 rec[kRecCap * kRecStride / 4];
@@ -833,42 +833,14 @@ __device__ __forceinline__ void add_row(const float row[kRecStride], int vid, co
     atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
 }
 
-// Sums the records of each entry of the run [k_lo, k_hi) and adds the sums
-// to the global gradients of its voxel: an entry with more than kBigEntry
-// records (a voxel seen by many pixels of the block) is summed by the whole
-// warp with a butterfly over its records, lane c then adding component c;
-// lane j sums the records of a smaller entry j by itself.
+// Lane j in [k_lo, k_hi) sums entry j's records and adds the sums to the
+// global gradients of its voxel.
 __device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, int k_lo, int k_hi, int off, int end,
                                           int base, const int32_t *__restrict__ corner_idx,
                                           float *__restrict__ d_grid, float *__restrict__ acc_col) {
     const int lane = threadIdx.x & 31;
-    const bool mine = lane >= k_lo && lane < k_hi && end > off;
-    const bool big = mine && end - off > kBigEntry;
     __syncwarp();
-    for (unsigned bm = __ballot_sync(0xffffffffu, big); bm; bm &= bm - 1u) {
-        const int j = __ffs(bm) - 1;
-        const int o = __shfl_sync(0xffffffffu, off, j) - base;
-        const int n = __shfl_sync(0xffffffffu, end, j) - base - o;
-        float row[kRecStride];
-#pragma unroll
-        for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
-        if (lane < n) rec_add(row, rs.rec + (o + lane) * (kRecStride / 4));
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) {
-#pragma unroll
-            for (int c = 0; c < kRec; ++c) row[c] += __shfl_xor_sync(0xffffffffu, row[c], m);
-        }
-        if (lane < kRec) {
-            const int vid = __float_as_int(st[j].col.w);
-            float v = row[0];
-#pragma unroll
-            for (int c = 1; c < kRec; ++c) v = lane == c ? row[c] : v;
-            float *t = lane < 8 ? d_grid + __ldg(corner_idx + 8 * (size_t)vid + lane)
-                                : acc_col + 3 * (size_t)vid + (lane - 8);
-            atomicAdd(t, v);
-        }
-    }
-    if (mine && !big) {
+    if (lane >= k_lo && lane < k_hi && end > off) {
         float row[kRecStride];
 #pragma unroll
         for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
@@ -1078,7 +1050,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBwdThreads, 5) k_render_bwd(FrameDev f, BwdIn in) {
+__global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(FrameDev f, BwdIn in) {
     __shared__ Entry stage[kBwdWarps][kBatch];
     __shared__ RecSmem recs[kBwdWarps];
     const int warp = threadIdx.x >> 5;

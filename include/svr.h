@@ -144,7 +144,7 @@ typedef struct svr_buffers {
     const uint64_t *octpath;  /* [N] Morton code (Sec. A.1) */
     const int16_t *rect;      /* [V][N][4] tx0, tx1, ty0, ty1 (empty: tx0 > tx1) */
     const uint32_t *count;    /* [V][N] pairs emitted per (view, voxel) */
-    const uint32_t *offset;   /* [V][N] exclusive scan of count */
+    const uint32_t *offset;   /* NULL: pairs are written per tile, not at per-voxel offsets */
     const float *record;      /* [V][N][16] per-voxel record of each view */
     const uint64_t *keys;     /* [pair_capacity] sorted keys: tile << key_shift | Morton order */
     const uint32_t *values;   /* [pair_capacity] sorted values: s << 29 | voxel id */
@@ -198,16 +198,20 @@ SVR_API int svr_preprocess_views(svr_frame *frame, const svr_scene *scene, const
 
 /*
  * Pair emission and sort (Sec. B.1).  Enqueues: the exclusive scan of the
- * per-voxel counts; one pair per (voxel, tile of its rectangle, sign pattern
- * s of that tile), key = tile << 48 | (octpath XOR s replicated in all 16
- * triples) (the direction-dependent Morton order of Sec. B.2), value = s << 29
- * | voxel id; a stable LSD radix sort over the key bits that can differ
- * (tile bits and the top 3 (max_level + 1) Morton bits; with max_level = 16
- * first the value's sign bits), which orders the pairs by (key, value); the
- * [begin, end) range of every tile.
+ * per-tile pair counts (counted by svr_preprocess), which gives every tile
+ * its [begin, end) range of the pair list; one pair per (voxel, tile of its
+ * rectangle, sign pattern s of that tile) written into that tile's range,
+ * key = tile << 48 | (octpath XOR s replicated in all 16 triples) (the
+ * direction-dependent Morton order of Sec. B.2), value = s << 29 | voxel id;
+ * then a sort of each tile's range by the Morton bits that can differ (the
+ * top 3 (max_level + 1) of the 48; with max_level = 16 all of them and the
+ * value first), done tile by tile in shared memory: stable LSD radix sorts of
+ * 1024-pair chunks, whose runs are merged per tile.  The result equals a sort
+ * of all pairs by (key, value): within a tile distinct pairs have distinct
+ * (key, value).  Also builds the render work order and the per-block lists.
  * n_pairs_out: if not NULL, the call synchronises the stream, stores the
  * true pair count there, and returns SVR_ERR_CAPACITY if it exceeds the
- * capacity (pairs beyond it were dropped; re-run with a larger workspace) or
+ * capacity (no pair was written; re-run with a larger workspace) or
  * SVR_ERR_INVALID if a voxel failed its lattice or level check.  If NULL the
  * call only enqueues work (CUDA-graph capturable) and such errors are left
  * for svr_frame_status().

@@ -27,8 +27,8 @@ int cuda_fail(cudaError_t e, const char *where) {
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 enum Slot {
-    kStatus, kTileMask, kOctpath, kRect, kCount, kOffset, kRecord, kScanBlocks,
-    kKeys0, kKeys1, kVals0, kVals1, kHist, kDigitTot, kRanges, kDcol, kBox, kTileOrder, kBlockList, kBlockLen,
+    kStatus, kTileMask, kOctpath, kRect, kCount, kTileCount, kRecord, kScanBlocks,
+    kKeys0, kKeys1, kVals0, kVals1, kRanges, kDcol, kBox, kTileOrder, kBlockList, kBlockLen,
     kSegment, kTotal, kNumSlots
 };
 
@@ -65,15 +65,13 @@ Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles, int 
     take(kOctpath, 8 * N);
     take(kRect, 8 * VN);
     take(kCount, 4 * VN);
-    take(kOffset, 4 * VN);
+    take(kTileCount, 4 * (2 * svr::kTileSub + 1) * (size_t)ntiles);
     take(kRecord, sizeof(svr::Record) * VN);
-    take(kScanBlocks, 4 * ((VN + svr::kScanTile - 1) / svr::kScanTile + 1));
+    take(kScanBlocks, 4 * (((size_t)ntiles * svr::kTileSub + svr::kScanTile - 1) / svr::kScanTile + 1));
     take(kKeys0, 8 * C);
     take(kKeys1, 8 * C);
     take(kVals0, 4 * C);
     take(kVals1, 4 * C);
-    take(kHist, 4 * 256 * ((C + svr::kRadixTile - 1) / svr::kRadixTile + 1));
-    take(kDigitTot, 4 * 256);
     take(kRanges, 8 * (size_t)ntiles);
     take(kDcol, 12 * VN);
     take(kBox, 8 * VN);
@@ -166,7 +164,9 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.octpath = (uint64_t *)(ws + o[kOctpath]);
     d.rect = (short4 *)(ws + o[kRect]);
     d.count = (uint32_t *)(ws + o[kCount]);
-    d.offset = (uint32_t *)(ws + o[kOffset]);
+    d.tile_cnt = (uint32_t *)(ws + o[kTileCount]);
+    d.cursor = d.tile_cnt + (size_t)svr::kTileSub * f->total_tiles;
+    d.tile_end = d.cursor + (size_t)svr::kTileSub * f->total_tiles;
     d.rec = (svr::Record *)(ws + o[kRecord]);
     d.box = (ushort4 *)(ws + o[kBox]);
     d.scan_blocks = (uint32_t *)(ws + o[kScanBlocks]);
@@ -174,8 +174,6 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.keys[1] = (uint64_t *)(ws + o[kKeys1]);
     d.vals[0] = (uint32_t *)(ws + o[kVals0]);
     d.vals[1] = (uint32_t *)(ws + o[kVals1]);
-    d.hist = (uint32_t *)(ws + o[kHist]);
-    d.digit_tot = (uint32_t *)(ws + o[kDigitTot]);
     d.ranges = (uint2 *)(ws + o[kRanges]);
     d.order = (uint2 *)(ws + o[kTileOrder]);
     d.blist = (uint2 *)(ws + o[kBlockList]);
@@ -273,6 +271,7 @@ int preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cams,
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(svr::Status), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&d.status->bad_voxel, 0xFF, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.tile_cnt, 0, sizeof(uint32_t) * svr::kTileSub * (size_t)ntiles, s);
     if (e != cudaSuccess) return cuda_fail(e, "status reset");
     e = svr::launch_tile_mask(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "tile mask");
@@ -349,20 +348,18 @@ SVR_API int svr_bin_sort(svr_frame *frame, int64_t *n_pairs_out, void *stream) {
     if (!frame || frame->stage < 1) return fail(SVR_ERR_INVALID, "frame not preprocessed");
     const svr::FrameDev d = frame_dev(frame);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = svr::launch_scan_emit(d, s);
-    if (e != cudaSuccess) return cuda_fail(e, "scan/emit");
-    const int lmax = frame->scene.max_level;
-    const int morton_bits = 3 * (lmax < 16 ? lmax + 1 : 16);
-    const int lo_bit = frame->key_shift - morton_bits;
-    const int hi_bit = frame->key_shift + tile_bits(frame->total_tiles);
-    int alt = 0;
-    e = svr::launch_sort(d, lo_bit, hi_bit, lmax == 16, &alt, s);
+    cudaError_t e = svr::launch_scan(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scan");
+    e = svr::launch_order(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ranges and work order");
+    e = svr::launch_emit(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "emit");
+    e = svr::launch_tile_sort(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "sort");
-    frame->sorted_alt = alt;
-    e = svr::launch_ranges(d, alt, s);
-    if (e != cudaSuccess) return cuda_fail(e, "ranges");
-    e = svr::launch_block_lists(d, alt, s);
+    frame->sorted_alt = 0;
+    e = svr::launch_block_lists(d, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "block lists");
+    const int lmax = frame->scene.max_level;
     frame->stage = 2;
     frame->n_pairs = -1;
     if (n_pairs_out) {
@@ -444,7 +441,7 @@ SVR_API int svr_frame_buffers(const svr_frame *frame, svr_buffers *out) {
     out->octpath = d.octpath;
     out->rect = (const int16_t *)d.rect;
     out->count = d.count;
-    out->offset = d.offset;
+    out->offset = nullptr;
     out->record = (const float *)d.rec;
     out->keys = d.keys[frame->sorted_alt];
     out->values = d.vals[frame->sorted_alt];

@@ -7,8 +7,14 @@
 //                 tile rectangle of the projected corners (Sec. 3.1.2), pair
 //                 count, conservative pixel box, view-dependent colour
 //                 (Eq. vox_color), gathered densities
-//   k_scan_*      exclusive scan of the pair counts (three phases)
-//   k_emit        key = tile << S | top S bits of (octpath ^ s replicated),
+//                 and, per tile, the pairs it will hold (atomics)
+//   k_scan_*      exclusive scan of the tiles' pair counts (three phases;
+//                 kTileSub sub-buckets per tile, adjacent): each sub-bucket's
+//                 start, each tile's end, the total, the capacity check
+//   k_emit        writes each (voxel, tile, sign pattern s) pair into its
+//                 tile's range (an atomic cursor per sub-bucket; the order
+//                 within a tile is left to the per-tile sort):
+//                 key = tile << S | top S bits of (octpath ^ s replicated),
 //                 value = s << 29 | voxel id (Sec. B.1; the per-triple
 //                 permutation of Sec. B.2 is b ^ s, applied to all 16
 //                 triples at once).  S = 48 for one view (the paper's layout:
@@ -156,8 +162,15 @@ __global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
     }
     uint32_t cnt = 0;
     const uint8_t *mask = f.tile_mask + cam.tile_base;
-    for (int ty = rc.z; ty <= rc.w; ++ty)
-        for (int tx = rc.x; tx <= rc.y; ++tx) cnt += __popc(mask[ty * cam.ntx + tx]);
+    for (int ty = rc.z; ty <= rc.w; ++ty) {
+        for (int tx = rc.x; tx <= rc.y; ++tx) {
+            const uint32_t c = __popc(mask[ty * cam.ntx + tx]);
+            if (c)
+                atomicAdd(f.tile_cnt + (size_t)(v & (kTileSub - 1)) * f.total_tiles + cam.tile_base + ty * cam.ntx + tx,
+                          c);
+            cnt += c;
+        }
+    }
     f.rect[iv] = rc;
     f.count[iv] = cnt;
     if (cnt == 0) return;
@@ -225,18 +238,25 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
     return wpre + inc - x;
 }
 
-__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ count, int64_t n,
+// Scan position i is sub-bucket i % kTileSub of tile i / kTileSub, stored
+// sub-bucket-major (count[sub * ntiles + tile]).
+__device__ __forceinline__ int64_t sub_index(int64_t i, int64_t ntiles) {
+    return (i % kTileSub) * ntiles + i / kTileSub;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ count, int64_t ntiles,
                                                      uint32_t *__restrict__ block_sums) {
     __shared__ uint32_t ws[8];
+    const int64_t n = ntiles * kTileSub;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint64_t acc = 0;
     for (int r = 0; r < kScanTile / 256; ++r) {
         int64_t i = base + r * 256 + threadIdx.x;
-        if (i < n) acc += count[i];
+        if (i < n) acc += count[sub_index(i, ntiles)];
     }
     uint32_t tot;
-    // counts per voxel are < 2^24 in practice; a block sum beyond 2^32 is
-    // caught by the capacity check on the 64-bit total
+    // a block sum beyond 2^32 saturates; the capacity check on the 64-bit
+    // total catches it
     block_exclusive_scan((uint32_t)tmin<uint64_t>(acc, 0xFFFFFFFFull), ws, tot);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
@@ -277,18 +297,24 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ block_
     }
 }
 
-__global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ count, int64_t n,
+// Sub-bucket starts (the emission cursors) and tile ends from the scanned
+// counts; k_tile_order turns them into the tiles' ranges.
+__global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ count, int64_t ntiles,
                                                    const uint32_t *__restrict__ block_off,
-                                                   uint32_t *__restrict__ offset) {
+                                                   uint32_t *__restrict__ cursor, uint32_t *__restrict__ tile_end) {
     __shared__ uint32_t ws[8];
+    const int64_t n = ntiles * kTileSub;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint32_t carry = block_off[blockIdx.x];
     for (int r = 0; r < kScanTile / 256; ++r) {
         const int64_t i = base + r * 256 + threadIdx.x;
-        const uint32_t x = i < n ? count[i] : 0u;
+        const uint32_t x = i < n ? count[sub_index(i, ntiles)] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(x, ws, tot);
-        if (i < n) offset[i] = carry + ex;
+        if (i < n) {
+            cursor[sub_index(i, ntiles)] = carry + ex;
+            if (i % kTileSub == kTileSub - 1) tile_end[i / kTileSub] = carry + ex + x;
+        }
         carry += tot;
     }
 }
@@ -303,9 +329,7 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
     const int view = blockIdx.y;
     const DevCam &cam = f.views[view];
     const int64_t iv = (int64_t)view * f.n_vox + v;
-    const uint32_t cnt = f.count[iv];
-    if (cnt == 0) return;
-    uint32_t o = f.offset[iv];
+    if (f.count[iv] == 0) return;
     const short4 rc = f.rect[iv];
     const uint64_t code = f.octpath[v];
     const int drop = 48 - f.key_shift;
@@ -313,13 +337,18 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
     uint32_t *vals = f.vals[0];
     for (int ty = rc.z; ty <= rc.w; ++ty) {
         for (int tx = rc.x; tx <= rc.y; ++tx) {
-            const int tile = ty * cam.ntx + tx;
-            const uint64_t g = (uint64_t)(cam.tile_base + tile);
-            unsigned m = f.tile_mask[cam.tile_base + tile];
+            const int g = cam.tile_base + ty * cam.ntx + tx;
+            unsigned m = f.tile_mask[g];
+            if (!m) continue;
+            uint32_t o = atomicAdd(f.cursor + (size_t)(v & (kTileSub - 1)) * f.total_tiles + g, (uint32_t)__popc(m));
+            if ((int64_t)o + __popc(m) > f.capacity) {  // counts and emission disagree: never expected
+                atomicOr(&f.status->flags, SVR_FLAG_CAPACITY);
+                return;
+            }
             while (m) {
                 const unsigned s = __ffs(m) - 1;
                 m &= m - 1;
-                keys[o] = (g << f.key_shift) | ((code ^ ((uint64_t)s * kTripleOnes)) >> drop);
+                keys[o] = ((uint64_t)g << f.key_shift) | ((code ^ ((uint64_t)s * kTripleOnes)) >> drop);
                 vals[o] = (s << 29) | (uint32_t)v;
                 ++o;
             }
@@ -342,18 +371,20 @@ cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s) {
-    const int64_t n = f.n_vox * f.n_views;
-    if (n == 0) {
-        k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, 0, f.status, f.capacity);
-        return cudaGetLastError();
-    }
-    const int nb = (int)((n + kScanTile - 1) / kScanTile);
-    k_scan_reduce<<<nb, 256, 0, s>>>(f.count, n, f.scan_blocks);
+cudaError_t launch_scan(const FrameDev &f, cudaStream_t s) {
+    const int64_t T = f.total_tiles;
+    const int nb = (int)((T * kTileSub + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, 256, 0, s>>>(f.tile_cnt, T, f.scan_blocks);
     k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, nb, f.status, f.capacity);
-    k_scan_down<<<nb, 256, 0, s>>>(f.count, n, f.scan_blocks, f.offset);
-    const dim3 grid((unsigned)((f.n_vox + 255) / 256), (unsigned)f.n_views);
-    k_emit<<<grid, 256, 0, s>>>(f);
+    k_scan_down<<<nb, 256, 0, s>>>(f.tile_cnt, T, f.scan_blocks, f.cursor, f.tile_end);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const FrameDev &f, cudaStream_t s) {
+    if (f.n_vox > 0) {
+        const dim3 grid((unsigned)((f.n_vox + 255) / 256), (unsigned)f.n_views);
+        k_emit<<<grid, 256, 0, s>>>(f);
+    }
     return cudaGetLastError();
 }
 

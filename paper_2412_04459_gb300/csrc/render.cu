@@ -763,8 +763,7 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
 // global gradients (one set of atomics per entry and warp).  At most kRecCap
 // records are held at a time: a batch with more hits is processed in runs of
 // consecutive entries, which keeps every pixel's hits in list order.
-constexpr int kRec = 11;
-constexpr int kRecStride = 12;   // floats per record slot (16-byte aligned)
+constexpr int kRecStride = 12;   // floats per record slot: 11 used, 16-byte aligned
 constexpr int kRecCap = 128;
 
 struct RecSmem {

@@ -1,203 +1,52 @@
-// Stable LSD radix sort of the (key, value) pairs and per-tile ranges.
+// Tile ranges, render work order and the per-tile sort of the (key, value)
+// pairs.
 //
-// The pair count lives on the device (written by the count scan); every
-// kernel reads it, so the host enqueues the sort without knowing it and the
-// sequence can be captured in a CUDA graph.  One pass sorts 8 key bits:
-//   k_radix_count     per tile of 4096 pairs: digit histogram -> hist[digit][tile]
-//   k_radix_digit     per digit: exclusive scan over the tiles, digit total
-//   k_radix_scatter   per tile: stable rank of each pair among the pairs of
-//                     its digit (warp match + per-warp counts, in index
-//                     order), written to digit base + tile offset + rank
-// Pairs with equal keys keep their order (emission order), so sorting the
-// value's sign bits first and then the key bits orders pairs by (key, value).
-//
-//   k_tile_ranges     [begin, end) of each tile id (key >> 48) in the sorted list
+// Pairs arrive grouped by tile (k_emit writes each tile's pairs into its own
+// range, in no particular order), so each tile's range is sorted on its own,
+// in shared memory, by (key, value) (the keys of one tile share the tile id):
+//   k_tile_order   the tiles' ranges from the scanned counts, and the render
+//                  work order: one entry per tile, or per 1024-entry segment
+//                  of a longer list, longest first
+//   k_sort_small   one CTA per list of at most 1024 pairs, and per 1024-pair
+//                  chunk of a longer list: bitonic sort in shared memory
+//   k_merge_runs   lists longer than 1024 pairs: their sorted chunks merged
+//                  in rounds of pairwise merges (merge-path partitioning over
+//                  the CTA's threads), in shared memory up to 8192 pairs
+// The result equals a sort of all pairs by (key, value).
 #include "svr_internal.cuh"
 
 namespace svr {
-
-// Pairs to sort: the emitted count, or none when the emission was skipped
-// because the count exceeded the capacity (the buffers then hold stale data).
-__device__ __forceinline__ uint32_t pair_count(const Status *st, int64_t cap) {
-    if (st->flags & SVR_FLAG_CAPACITY) return 0u;
-    const unsigned long long p = ((unsigned long long)st->n_pairs_hi << 32) | st->n_pairs_lo;
-    return (uint32_t)tmin<unsigned long long>(p, (unsigned long long)cap);
-}
-
-__device__ __forceinline__ uint32_t digit_of(uint64_t key, uint32_t val, int shift, bool sign_pass) {
-    return sign_pass ? (val >> 29) : (uint32_t)((key >> shift) & 0xFFu);
-}
-
-__global__ void __launch_bounds__(kRadixThreads) k_radix_count(const uint64_t *__restrict__ keys,
-                                                               const uint32_t *__restrict__ vals,
-                                                               const Status *st, int64_t cap, int shift,
-                                                               bool sign_pass, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t h[256];
-    const uint32_t P = pair_count(st, cap);
-    const uint32_t nb = (P + kRadixTile - 1) / kRadixTile;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-        h[threadIdx.x] = 0;
-        // all loads of the tile first, so their latencies overlap
-        const uint32_t base = b * kRadixTile;
-        uint32_t d[kRadixItems];
-#pragma unroll
-        for (int r = 0; r < kRadixItems; ++r) {
-            const uint32_t i = base + r * kRadixThreads + threadIdx.x;
-            d[r] = i < P ? digit_of(keys[i], sign_pass ? vals[i] : 0u, shift, sign_pass) : 256u;
-        }
-        __syncthreads();
-        // one shared atomic per digit value present in the warp
-#pragma unroll
-        for (int r = 0; r < kRadixItems; ++r) {
-            const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-            if (d[r] < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[d[r]], (uint32_t)__popc(peers));
-        }
-        __syncthreads();
-        hist[(size_t)threadIdx.x * nb + b] = h[threadIdx.x];
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_radix_digit(uint32_t *__restrict__ hist, const Status *st,
-                                                      int64_t cap, uint32_t *__restrict__ digit_tot) {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    const uint32_t P = pair_count(st, cap);
-    const uint32_t nb = (P + kRadixTile - 1) / kRadixTile;
-    const int d = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    uint32_t *row = hist + (size_t)d * nb;
-    for (uint32_t base = 0; base < nb; base += 1024) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t x = i < nb ? row[i] : 0u;
-        uint32_t inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        uint32_t wpre = 0, tot = 0;
-        for (int w = 0; w < 32; ++w) {
-            const uint32_t s = wsum[w];
-            wpre += (w < warp) ? s : 0u;
-            tot += s;
-        }
-        if (i < nb) row[i] = carry + wpre + inc - x;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) digit_tot[d] = carry;
-}
-
-__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
-    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const Status *st, int64_t cap, int shift, bool sign_pass,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ digit_tot) {
-    constexpr int kWarps = kRadixThreads / 32;
-    __shared__ uint32_t base_d[256];     // global start of each digit in this tile
-    __shared__ uint32_t run[256];        // pairs of each digit already placed in this tile
-    __shared__ uint32_t wcnt[kWarps][256];
-    __shared__ uint32_t wpre[kWarps][256];
-    __shared__ uint32_t wsum[kWarps];
-
-    const uint32_t P = pair_count(st, cap);
-    const uint32_t nb = (P + kRadixTile - 1) / kRadixTile;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-
-    // exclusive scan of the digit totals (one digit per thread)
-    uint32_t tot_d = digit_tot[t];
-    uint32_t inc = tot_d;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    uint32_t wp = 0;
-    for (int w = 0; w < warp; ++w) wp += wsum[w];
-    const uint32_t digit_start = wp + inc - tot_d;
-
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-        base_d[t] = digit_start + hist[(size_t)t * nb + b];
-        run[t] = 0;
-        for (int w = 0; w < kWarps; ++w) wcnt[w][t] = 0;
-        __syncthreads();
-        const uint32_t base = b * kRadixTile;
-        // all loads of the tile first, so their latencies overlap
-        uint64_t keys[kRadixItems];
-        uint32_t vals[kRadixItems];
-#pragma unroll
-        for (int r = 0; r < kRadixItems; ++r) {
-            const uint32_t i = base + r * kRadixThreads + t;
-            keys[r] = i < P ? kin[i] : 0ull;
-            vals[r] = i < P ? vin[i] : 0u;
-        }
-#pragma unroll
-        for (int r = 0; r < kRadixItems; ++r) {
-            const uint32_t i = base + r * kRadixThreads + t;
-            const bool valid = i < P;
-            const uint64_t key = keys[r];
-            const uint32_t val = vals[r];
-            const uint32_t d = valid ? digit_of(key, val, shift, sign_pass) : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t rank = __popc(peers & lt_mask);
-            if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-            __syncthreads();
-            {
-                uint32_t acc = run[t];
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) {
-                    wpre[w][t] = acc;
-                    acc += wcnt[w][t];
-                    wcnt[w][t] = 0;
-                }
-                run[t] = acc;
-            }
-            __syncthreads();
-            if (valid) {
-                const uint32_t pos = base_d[d] + wpre[warp][d] + rank;
-                kout[pos] = key;
-                vout[pos] = val;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void k_tile_ranges(const uint64_t *__restrict__ keys, const Status *st, int64_t cap,
-                              uint32_t ntiles, int shift, uint2 *__restrict__ ranges) {
-    const uint32_t P = pair_count(st, cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-        const uint32_t tile = (uint32_t)(keys[i] >> shift);
-        if (tile >= ntiles) continue;
-        if (i == 0 || (uint32_t)(keys[i - 1] >> shift) != tile) ranges[tile].x = i;
-        if (i == P - 1 || (uint32_t)(keys[i + 1] >> shift) != tile) ranges[tile].y = i + 1;
-    }
-}
 
 // Render work order: one entry (tile, segment) per segment of every tile's
 // list.  A list of L > kSegLen entries is split into ceil(L / kSegLen)
 // segments of kSegLen consecutive entries, which get consecutive slots for
 // their partial sums; a shorter list is one segment without a slot.  Entries
-// are grouped by floor(log2(segment length)), longest first, so the heaviest
-// work starts early and short segments fill the tail (one CTA; the order
-// within a group is arbitrary and results do not depend on it).  Also resets
-// the frame's forward-done mark: the segment sums belong to the last sort.
+// are grouped by floor(log2(list length)), longest lists first, so the
+// heaviest work starts early and short lists fill the tail (one CTA; the
+// order within a group is arbitrary and results do not depend on it).  Also
+// resets the frame's forward-done mark (the segment sums belong to the last
+// sort) and the merge's work counter.
+// Group of a list in the work order: floor(log2(length)) + 1, one more for a
+// split list, so that every split list (longer than kSegLen) precedes every
+// unsplit one.
+__device__ __forceinline__ int order_bucket(unsigned len, unsigned nseg) {
+    return len ? 32 - __clz(len) + (nseg > 1 ? 1 : 0) : 0;
+}
+
 __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
-    __shared__ unsigned cnt[33];
-    __shared__ unsigned start[33];
+    __shared__ unsigned cnt[34];
+    __shared__ unsigned start[34];
     __shared__ unsigned slot_next;
     const int t = threadIdx.x;
     const int ntiles = f.total_tiles;
-    if (t < 33) cnt[t] = 0;
+    // ranges: a tile starts at its first sub-bucket; empty tiles, and all
+    // tiles when the pairs exceed the capacity, get (0, 0)
+    const bool over = (f.status->flags & SVR_FLAG_CAPACITY) != 0;
+    for (int i = t; i < ntiles; i += blockDim.x) {
+        const uint32_t b = f.cursor[i], e = f.tile_end[i];
+        f.ranges[i] = over || e == b ? make_uint2(0u, 0u) : make_uint2(b, e);
+    }
+    if (t < 34) cnt[t] = 0;
     if (t == 0) slot_next = 0;
     __syncthreads();
     for (int i = t; i < ntiles; i += blockDim.x) {
@@ -209,29 +58,189 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
             base = atomicAdd(&slot_next, nseg);
             if ((int64_t)base + nseg > f.seg_slots) nseg = 1, base = 0;  // only past the pair capacity
         }
-        const unsigned w = nseg > 1 ? (unsigned)kSegLen : len;
-        atomicAdd(&cnt[w ? 32 - __clz(w) : 0], nseg);
+        atomicAdd(&cnt[order_bucket(len, nseg)], nseg);
         f.tile_seg[i] = make_uint2(nseg, base);
     }
     __syncthreads();
     if (t == 0) {
         unsigned acc = 0;
-        for (int b = 32; b >= 0; --b) {
+        for (int b = 33; b >= 0; --b) {
             start[b] = acc;
             acc += cnt[b];
         }
         f.status->n_queue = acc;
         f.status->slots_used = slot_next;
         f.status->fwd_done = 0;
+        f.status->merge_next = 0;
     }
     __syncthreads();
     for (int i = t; i < ntiles; i += blockDim.x) {
         const uint2 r = f.ranges[i];
         const uint2 ts = f.tile_seg[i];
         const unsigned len = r.y - r.x;
-        const unsigned w = ts.x > 1 ? (unsigned)kSegLen : len;
-        const unsigned pos = atomicAdd(&start[w ? 32 - __clz(w) : 0], ts.x);
+        const unsigned pos = atomicAdd(&start[order_bucket(len, ts.x)], ts.x);
         for (unsigned sg = 0; sg < ts.x; ++sg) f.order[pos + sg] = make_uint2((unsigned)i, sg);
+    }
+}
+
+// ------------------------------------------------------------ bitonic sort
+
+constexpr int kSmallThreads = 512;
+constexpr int kSmallPairs = kSegLen;
+
+__device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
+    return ka < kb || (ka == kb && va < vb);
+}
+
+__device__ __forceinline__ int pow2_at_least(int n) {
+    return n <= 1 ? 1 : 1 << (32 - __clz(n - 1));
+}
+
+// Sorts the n pairs at (gk, gv) by (key, value) in shared memory (sk, sv hold
+// N = pow2_at_least(n) pairs; the padding sorts last): bitonic network, one
+// compare-exchange per thread and step.
+template <int THREADS>
+__device__ void smem_sort(uint64_t *__restrict__ gk, uint32_t *__restrict__ gv, int n, uint64_t *sk, uint32_t *sv) {
+    const int N = pow2_at_least(n);
+    for (int i = threadIdx.x; i < N; i += THREADS) {
+        sk[i] = i < n ? gk[i] : ~0ull;
+        sv[i] = i < n ? gv[i] : ~0u;
+    }
+    __syncthreads();
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < N / 2; t += THREADS) {
+                const int i = 2 * t - (t & (stride - 1));  // the pair (i, i + stride) of step stride
+                const int l = i + stride;
+                const uint64_t ki = sk[i], kl = sk[l];
+                const uint32_t vi = sv[i], vl = sv[l];
+                const bool up = (i & size) == 0;
+                if (pair_less(kl, vl, ki, vi) == up) {
+                    sk[i] = kl, sk[l] = ki;
+                    sv[i] = vl, sv[l] = vi;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += THREADS) {
+        gk[i] = sk[i];
+        gv[i] = sv[i];
+    }
+}
+
+// A whole list of at most kSmallPairs pairs, or one kSegLen-pair chunk of a
+// longer list (merged afterwards); one CTA per work-order entry.
+__global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f) {
+    __shared__ uint64_t sk[kSmallPairs];
+    __shared__ uint32_t sv[kSmallPairs];
+    if (blockIdx.x >= f.status->n_queue) return;
+    const uint2 q = f.order[blockIdx.x];
+    const uint2 rg = f.ranges[q.x];
+    const int L = (int)(rg.y - rg.x);
+    int c0, n;
+    if (L <= kSmallPairs) {
+        c0 = (int)rg.x;
+        n = L;
+    } else if (f.tile_seg[q.x].x > 1) {
+        c0 = (int)rg.x + (int)q.y * kSegLen;
+        n = min(kSegLen, (int)rg.y - c0);
+    } else {
+        return;
+    }
+    if (n < 2) return;
+    smem_sort<kSmallThreads>(f.keys[0] + c0, f.vals[0] + c0, n, sk, sv);
+}
+
+// ----------------------------------------------------------- merge of runs
+
+constexpr int kMergeThreads = 1024;
+constexpr int kMergePairs = 8192;  // longest list merged in shared memory (2 x 96 KB)
+constexpr size_t kMergeSmemBytes = (size_t)kMergePairs * 2 * (sizeof(uint64_t) + sizeof(uint32_t));
+
+// One round: the runs of width w of (sk, sv)[0, L) merged pairwise into
+// (dk, dv); thread t writes a contiguous share of the outputs, finding its
+// start in each pair of runs by a merge-path binary search (ties: first run).
+__device__ void merge_round(const uint64_t *sk, const uint32_t *sv, uint64_t *dk, uint32_t *dv, int L, int w) {
+    const int per = (L + kMergeThreads - 1) / kMergeThreads;
+    int o = threadIdx.x * per;
+    const int o_end = min(L, o + per);
+    while (o < o_end) {
+        const int p0 = o / (2 * w) * (2 * w);
+        const int mid = min(L, p0 + w), pend = min(L, p0 + 2 * w);
+        const int stop = min(o_end, pend);
+        const int k = o - p0, lenA = mid - p0, lenB = pend - mid;
+        int lo = max(0, k - lenB), hi = min(k, lenA);
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            // A[m] goes before B[k - 1 - m] unless B's is strictly smaller
+            if (pair_less(sk[mid + k - 1 - m], sv[mid + k - 1 - m], sk[p0 + m], sv[p0 + m])) hi = m;
+            else lo = m + 1;
+        }
+        int ia = p0 + lo, ib = mid + (k - lo);
+        for (; o < stop; ++o) {
+            const bool take_a = ib >= pend || (ia < mid && !pair_less(sk[ib], sv[ib], sk[ia], sv[ia]));
+            if (take_a) {
+                dk[o] = sk[ia];
+                dv[o] = sv[ia++];
+            } else {
+                dk[o] = sk[ib];
+                dv[o] = sv[ib++];
+            }
+        }
+    }
+}
+
+// Lists longer than kSmallPairs: their sorted kSegLen-pair chunks merged in
+// place, in shared memory up to kMergePairs pairs, else through the second
+// key/value buffer.  CTAs take work-order entries from a counter; the split
+// lists come first in that order, longest first.
+__global__ void __launch_bounds__(kMergeThreads) k_merge_runs(FrameDev f) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ unsigned entry;
+    const unsigned nq = f.status->n_queue;
+    for (;;) {
+        if (threadIdx.x == 0) entry = atomicAdd(&f.status->merge_next, 1u);
+        __syncthreads();
+        const unsigned e = entry;
+        __syncthreads();
+        if (e >= nq) return;
+        const uint2 q = f.order[e];
+        const uint2 ts = f.tile_seg[q.x];
+        if (ts.x < 2) return;  // unsplit lists follow all split ones: nothing left to merge
+        if (q.y != 0) continue;
+        const uint2 rg = f.ranges[q.x];
+        const int L = (int)(rg.y - rg.x);
+        uint64_t *gk = f.keys[0] + rg.x;
+        uint32_t *gv = f.vals[0] + rg.x;
+        const bool in_smem = L <= kMergePairs;
+        uint64_t *k[2];
+        uint32_t *v[2];
+        if (in_smem) {
+            k[0] = reinterpret_cast<uint64_t *>(dyn);
+            k[1] = k[0] + kMergePairs;
+            v[0] = reinterpret_cast<uint32_t *>(k[1] + kMergePairs);
+            v[1] = v[0] + kMergePairs;
+            for (int i = threadIdx.x; i < L; i += kMergeThreads) {
+                k[0][i] = gk[i];
+                v[0][i] = gv[i];
+            }
+            __syncthreads();
+        } else {
+            k[0] = gk, k[1] = f.keys[1] + rg.x, v[0] = gv, v[1] = f.vals[1] + rg.x;
+        }
+        int cur = 0;
+        for (int w = kSegLen; w < L; w *= 2, cur ^= 1) {
+            merge_round(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], L, w);
+            __syncthreads();
+        }
+        if (in_smem || cur == 1) {
+            for (int i = threadIdx.x; i < L; i += kMergeThreads) {
+                gk[i] = k[cur][i];
+                gv[i] = v[cur][i];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -246,39 +255,27 @@ static int sm_count() {
     return n;
 }
 
-cudaError_t launch_sort(const FrameDev &f, int lo_bit, int hi_bit, bool sign_pass, int *result_alt,
-                        cudaStream_t s) {
-    *result_alt = 0;
-    if (f.capacity == 0) return cudaSuccess;
-    const int64_t tiles_cap = (f.capacity + kRadixTile - 1) / kRadixTile;
-    const unsigned grid = (unsigned)tmin<int64_t>(tiles_cap, (int64_t)sm_count() * 8);
-    int cur = 0;
-    auto pass = [&](int shift, bool sp) {
-        k_radix_count<<<grid, kRadixThreads, 0, s>>>(f.keys[cur], f.vals[cur], f.status, f.capacity,
-                                                    shift, sp, f.hist);
-        k_radix_digit<<<256, 1024, 0, s>>>(f.hist, f.status, f.capacity, f.digit_tot);
-        k_radix_scatter<<<grid, kRadixThreads, 0, s>>>(f.keys[cur], f.vals[cur], f.keys[cur ^ 1],
-                                                      f.vals[cur ^ 1], f.status, f.capacity, shift, sp,
-                                                      f.hist, f.digit_tot);
-        cur ^= 1;
-    };
-    if (sign_pass) pass(0, true);
-    for (int b = lo_bit; b < hi_bit; b += 8) pass(b, false);
-    *result_alt = cur;
+cudaError_t launch_order(const FrameDev &f, cudaStream_t s) {
+    k_tile_order<<<1, 1024, 0, s>>>(f);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s) {
-    const int ntiles = f.total_tiles;
-    cudaError_t e = cudaMemsetAsync(f.ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
-    if (e != cudaSuccess) return e;
-    if (f.capacity > 0) {
-        const int64_t need = (f.capacity + 255) / 256;
-        const unsigned grid = (unsigned)tmin<int64_t>(need, (int64_t)sm_count() * 8);
-        k_tile_ranges<<<grid, 256, 0, s>>>(f.keys[sorted_alt], f.status, f.capacity, (uint32_t)ntiles, f.key_shift,
-                                           f.ranges);
+cudaError_t launch_tile_sort(const FrameDev &f, cudaStream_t s) {
+    if (f.capacity == 0) return cudaSuccess;
+    // one CTA per possible work-order entry; those past the device-side count exit
+    const unsigned grid = (unsigned)((int64_t)f.total_tiles + f.seg_slots);
+    k_sort_small<<<grid, kSmallThreads, 0, s>>>(f);
+    // the shared-memory opt-in is a per-device function attribute
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
+        cudaError_t e = cudaFuncSetAttribute(k_merge_runs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMergeSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr_set |= 1ull << dev;
     }
-    k_tile_order<<<1, 1024, 0, s>>>(f);
+    k_merge_runs<<<tmin(grid, (unsigned)sm_count()), kMergeThreads, kMergeSmemBytes, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -18,9 +18,6 @@ constexpr int kMaxLevel = 16;
 constexpr int kMaxViews = SVR_MAX_VIEWS;
 constexpr float kNear = 1e-3f;             // corners at camera depth <= kNear are "behind"
 constexpr uint64_t kTripleOnes = 0x249249249249ull;  // bit 0 of each of the 16 triples
-constexpr int kRadixItems = 4;             // keys per thread in one radix tile
-constexpr int kRadixThreads = 256;
-constexpr int kRadixTile = kRadixItems * kRadixThreads;
 constexpr int kScanTile = 4096;            // entries per block of the count scan
 // Tile lists longer than kSegLen entries are rendered as segments of kSegLen
 // consecutive entries (the last one shorter), each by its own warps, and
@@ -28,6 +25,10 @@ constexpr int kScanTile = 4096;            // entries per block of the count sca
 // partial sums between the warps and on to the backward.
 constexpr int kSegLen = 1024;
 constexpr int kSegFields = 8;
+// A tile's pairs are counted and emitted through kTileSub sub-buckets (by
+// voxel id), so that the atomics on a busy tile spread over separate cache
+// lines; the sub-buckets of a tile are adjacent in its range.
+constexpr int kTileSub = 8;
 
 // Segment slots a workspace holds for pair_capacity pairs: a split tile of
 // L > kSegLen entries takes ceil(L / kSegLen) < 2 L / kSegLen slots.
@@ -60,7 +61,8 @@ struct Status {
     unsigned n_queue;     // (tile, segment) entries of the render work order
     unsigned slots_used;  // segment slots taken by the split tiles
     unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort
-    unsigned pad[7];
+    unsigned merge_next;  // next work-order entry of the run merge
+    unsigned pad[6];
 };
 
 // Per-voxel record of one view (64 bytes):
@@ -131,15 +133,15 @@ struct FrameDev {
     uint8_t *tile_mask;      // [total_tiles]
     uint64_t *octpath;       // [N]
     short4 *rect;            // [V * N] tile rectangle tx0, tx1, ty0, ty1
-    uint32_t *count;         // [V * N]
-    uint32_t *offset;        // [V * N]
+    uint32_t *count;         // [V * N] pairs of each (view, voxel)
+    uint32_t *tile_cnt;      // [kTileSub][total_tiles] pairs of each tile's sub-buckets (k_preprocess)
+    uint32_t *cursor;        // [kTileSub][total_tiles] next free slot of each sub-bucket
+    uint32_t *tile_end;      // [total_tiles] end of each tile's range (from the scan)
     Record *rec;             // [V * N]
     ushort4 *box;            // [V * N] inclusive pixel range x0, x1, y0, y1 a hit can fall in
-    uint32_t *scan_blocks;   // [ceil(V * N / kScanTile)]
+    uint32_t *scan_blocks;   // [ceil(total_tiles / kScanTile) + 1]
     uint64_t *keys[2];
     uint32_t *vals[2];
-    uint32_t *hist;          // [256][capacity tiles]
-    uint32_t *digit_tot;     // [256]
     uint2 *ranges;           // [total_tiles]
     uint2 *order;            // [total_tiles + seg slots] (tile, segment), longest segments first
     uint2 *tile_seg;         // [total_tiles] segments of the tile's list, first segment slot
@@ -180,10 +182,10 @@ int set_error(int code, const char *fmt, ...);
 
 cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s);
-cudaError_t launch_scan_emit(const FrameDev &f, cudaStream_t s);
-cudaError_t launch_sort(const FrameDev &f, int lo_bit, int hi_bit, bool sign_pass, int *result_alt,
-                        cudaStream_t s);
-cudaError_t launch_ranges(const FrameDev &f, int sorted_alt, cudaStream_t s);
+cudaError_t launch_scan(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_order(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_emit(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_tile_sort(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s);
 cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth,
                               float *alpha, float *T_final, int32_t *last, int2 *stats, cudaStream_t s);

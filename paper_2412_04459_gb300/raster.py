@@ -304,7 +304,6 @@ class Frame:
             octpath=get(b.octpath, self.scene.n_vox, torch.int64).view(np.uint64),
             rect=get(b.rect, 4 * nv, torch.int16).reshape(nv, 4),
             count=get(b.count, nv, torch.int32).view(np.uint32),
-            offset=get(b.offset, nv, torch.int32).view(np.uint32),
             keys=get(b.keys, Pc, torch.int64).view(np.uint64),
             values=get(b.values, Pc, torch.int32).view(np.uint32),
             ranges=get(b.ranges, 2 * ntiles, torch.int32).view(np.uint32).reshape(ntiles, 2),

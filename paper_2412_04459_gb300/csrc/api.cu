@@ -354,12 +354,13 @@ SVR_API int svr_bin_sort(svr_frame *frame, int64_t *n_pairs_out, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e, "ranges and work order");
     e = svr::launch_emit(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "emit");
-    e = svr::launch_tile_sort(d, s);
+    const int lmax = frame->scene.max_level;
+    const int morton_bits = 3 * (lmax < 16 ? lmax + 1 : 16);
+    e = svr::launch_tile_sort(d, frame->key_shift - morton_bits, morton_bits, lmax == 16, s);
     if (e != cudaSuccess) return cuda_fail(e, "sort");
     frame->sorted_alt = 0;
     e = svr::launch_block_lists(d, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "block lists");
-    const int lmax = frame->scene.max_level;
     frame->stage = 2;
     frame->n_pairs = -1;
     if (n_pairs_out) {

@@ -8,7 +8,8 @@
 //                  work order: one entry per tile, or per 1024-entry segment
 //                  of a longer list, longest first
 //   k_sort_small   one CTA per list of at most 1024 pairs, and per 1024-pair
-//                  chunk of a longer list: bitonic sort in shared memory
+//                  chunk of a longer list: bitonic sort, warp shuffles for
+//                  the short strides, shared memory for the long ones
 //   k_merge_runs   lists longer than 1024 pairs: their sorted chunks merged
 //                  in rounds of pairwise merges (merge-path partitioning over
 //                  the CTA's threads), in shared memory up to 8192 pairs
@@ -96,44 +97,112 @@ __device__ __forceinline__ int pow2_at_least(int n) {
     return n <= 1 ? 1 : 1 << (32 - __clz(n - 1));
 }
 
-// Sorts the n pairs at (gk, gv) by (key, value) in shared memory (sk, sv hold
-// N = pow2_at_least(n) pairs; the padding sorts last): bitonic network, one
-// compare-exchange per thread and step.
-template <int THREADS>
-__device__ void smem_sort(uint64_t *__restrict__ gk, uint32_t *__restrict__ gv, int n, uint64_t *sk, uint32_t *sv) {
-    const int N = pow2_at_least(n);
-    for (int i = threadIdx.x; i < N; i += THREADS) {
-        sk[i] = i < n ? gk[i] : ~0ull;
-        sv[i] = i < n ? gv[i] : ~0u;
-    }
-    __syncthreads();
+// Compare-exchange of a warp-held element with the element `stride` lanes
+// away (stride < 32): the element at index i keeps the smaller of the two
+// when (i & stride) == 0 matches the direction `up`, else the larger.
+__device__ __forceinline__ void cx_shfl(uint64_t &x, int i, int stride, bool up) {
+    const uint64_t p = __shfl_xor_sync(0xffffffffu, x, stride);
+    const bool keep_min = ((i & stride) == 0) == up;
+    if ((p < x) == keep_min) x = p;
+}
+
+// Bitonic sort of N (power of two, 64 <= N <= kSmallPairs) distinct 64-bit
+// words.  Warp w holds elements 64w + lane (a) and 64w + 32 + lane (b) in
+// registers: steps of stride < 32 are warp shuffles, stride 32 an exchange
+// within the lane, and only strides >= 64 go through shared memory (sx).
+__device__ void bitonic_words(uint64_t &a, uint64_t &b, int N, uint64_t *sx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool active = warp < N / 64;  // warps past the padded length only join the barriers
+    const int ia = 64 * warp + lane, ib = ia + 32;
     for (int size = 2; size <= N; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < N / 2; t += THREADS) {
-                const int i = 2 * t - (t & (stride - 1));  // the pair (i, i + stride) of step stride
-                const int l = i + stride;
-                const uint64_t ki = sk[i], kl = sk[l];
-                const uint32_t vi = sv[i], vl = sv[l];
-                const bool up = (i & size) == 0;
-                if (pair_less(kl, vl, ki, vi) == up) {
-                    sk[i] = kl, sk[l] = ki;
-                    sv[i] = vl, sv[l] = vi;
+        if (size > 64) {
+            if (active) sx[ia] = a, sx[ib] = b;
+            __syncthreads();
+            for (int stride = size >> 1; stride >= 64; stride >>= 1) {
+                for (int t = threadIdx.x; t < N / 2; t += kSmallThreads) {
+                    const int i = 2 * t - (t & (stride - 1));
+                    const int l = i + stride;
+                    const uint64_t xi = sx[i], xl = sx[l];
+                    if ((xl < xi) == ((i & size) == 0)) sx[i] = xl, sx[l] = xi;
                 }
+                __syncthreads();
             }
+            if (active) a = sx[ia], b = sx[ib];
             __syncthreads();
         }
+        if (active) {
+            const bool up_a = (ia & size) == 0, up_b = (ib & size) == 0;
+            int stride = size >> 1;
+            if (stride >= 32) {  // a and b are each other's partner (ia has bit 32 clear)
+                if ((b < a) == up_a) {
+                    const uint64_t t = a;
+                    a = b, b = t;
+                }
+                stride = 16;
+            }
+            for (; stride > 0; stride >>= 1) {
+                cx_shfl(a, ia, stride, up_a);
+                cx_shfl(b, ib, stride, up_b);
+            }
+        }
     }
-    for (int i = threadIdx.x; i < n; i += THREADS) {
-        gk[i] = sk[i];
-        gv[i] = sv[i];
+}
+
+// Sorts the n <= kSmallPairs pairs at (gk, gv) of one tile by (key, value).
+// The keys of a tile share the tile id, so the order is that of bits
+// [lo_bit, lo_bit + nbits) of the key.  Below max level 16 these bits differ
+// between any two pairs of a tile, and each pair is sorted as the word
+// (bits << 10 | its index), then gathered by index.  With max level 16
+// (ties: equal bits possible) the word is (bits << 16 | rank of the value
+// among the tile's values), the ranks coming from a first sort of
+// (value << 10 | index).
+__device__ void chunk_sort(uint64_t *__restrict__ gk, uint32_t *__restrict__ gv, int n, int lo_bit, int nbits,
+                           bool ties, uint64_t *sx, uint64_t *ok, uint32_t *ov, uint16_t *inv) {
+    const int N = max(64, pow2_at_least(n));
+    const int warp = threadIdx.x >> 5;
+    const bool active = warp < N / 64;
+    const int ia = 64 * warp + (threadIdx.x & 31), ib = ia + 32;
+    const uint64_t mask = nbits >= 64 ? ~0ull : (1ull << nbits) - 1ull;
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) ok[i] = gk[i], ov[i] = gv[i];
+    __syncthreads();
+    uint64_t a = ~0ull, b = ~0ull;
+    if (ties) {
+        if (ia < n) a = ((uint64_t)ov[ia] << 10) | (uint64_t)ia;
+        if (ib < n) b = ((uint64_t)ov[ib] << 10) | (uint64_t)ib;
+        bitonic_words(a, b, N, sx);
+        __syncthreads();
+        uint32_t *rank = reinterpret_cast<uint32_t *>(sx);  // sx is free until the next sort
+        if (active) {
+            if (ia < n) rank[a & 1023u] = (uint32_t)ia, inv[ia] = (uint16_t)(a & 1023u);
+            if (ib < n) rank[b & 1023u] = (uint32_t)ib, inv[ib] = (uint16_t)(b & 1023u);
+        }
+        __syncthreads();
+        a = ia < n ? (((ok[ia] >> lo_bit) & mask) << 16) | rank[ia] : ~0ull;
+        b = ib < n ? (((ok[ib] >> lo_bit) & mask) << 16) | rank[ib] : ~0ull;
+        __syncthreads();
+    } else {
+        if (ia < n) a = (((ok[ia] >> lo_bit) & mask) << 10) | (uint64_t)ia;
+        if (ib < n) b = (((ok[ib] >> lo_bit) & mask) << 10) | (uint64_t)ib;
+    }
+    bitonic_words(a, b, N, sx);
+    __syncthreads();
+    if (active) sx[ia] = a, sx[ib] = b;  // position p: the word of the pair that sorts p-th
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+        const uint64_t w = sx[i];
+        const int src = ties ? (int)inv[w & 0xFFFFu] : (int)(w & 1023u);
+        gk[i] = ok[src];
+        gv[i] = ov[src];
     }
 }
 
 // A whole list of at most kSmallPairs pairs, or one kSegLen-pair chunk of a
 // longer list (merged afterwards); one CTA per work-order entry.
-__global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f) {
-    __shared__ uint64_t sk[kSmallPairs];
-    __shared__ uint32_t sv[kSmallPairs];
+__global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f, int lo_bit, int nbits, bool ties) {
+    __shared__ uint64_t sx[kSmallPairs];
+    __shared__ uint64_t ok[kSmallPairs];
+    __shared__ uint32_t ov[kSmallPairs];
+    __shared__ uint16_t inv[kSmallPairs];
     if (blockIdx.x >= f.status->n_queue) return;
     const uint2 q = f.order[blockIdx.x];
     const uint2 rg = f.ranges[q.x];
@@ -149,7 +218,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f) {
         return;
     }
     if (n < 2) return;
-    smem_sort<kSmallThreads>(f.keys[0] + c0, f.vals[0] + c0, n, sk, sv);
+    chunk_sort(f.keys[0] + c0, f.vals[0] + c0, n, lo_bit, nbits, ties, sx, ok, ov, inv);
 }
 
 // ----------------------------------------------------------- merge of runs
@@ -260,11 +329,11 @@ cudaError_t launch_order(const FrameDev &f, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_sort(const FrameDev &f, cudaStream_t s) {
+cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties, cudaStream_t s) {
     if (f.capacity == 0) return cudaSuccess;
     // one CTA per possible work-order entry; those past the device-side count exit
     const unsigned grid = (unsigned)((int64_t)f.total_tiles + f.seg_slots);
-    k_sort_small<<<grid, kSmallThreads, 0, s>>>(f);
+    k_sort_small<<<grid, kSmallThreads, 0, s>>>(f, lo_bit, nbits, ties);
     // the shared-memory opt-in is a per-device function attribute
     static unsigned long long attr_set = 0;
     int dev = 0;

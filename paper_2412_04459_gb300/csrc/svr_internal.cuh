@@ -185,7 +185,7 @@ cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_scan(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_order(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_emit(const FrameDev &f, cudaStream_t s);
-cudaError_t launch_tile_sort(const FrameDev &f, cudaStream_t s);
+cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties, cudaStream_t s);
 cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s);
 cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth,
                               float *alpha, float *T_final, int32_t *last, int2 *stats, cudaStream_t s);

@@ -170,3 +170,20 @@ def test_deterministic_outputs():
         assert np.array_equal(i1[k], i2[k])
     for k in ("rgb", "depth", "alpha", "T_final", "last"):
         assert np.array_equal(to_np(o1)[k], to_np(o2)[k])
+
+
+def test_max_level_16_sort_path():
+    """A scene declared with max_level 16 keeps all 48 Morton bits in the keys
+    and sorts each tile by (key, value) through the value-rank path; sorted
+    pairs, ranges and images still equal the oracle's."""
+    from paper_2412_04459_gb300 import DeviceScene, Frame
+    sc = synth.random_octree_scene(12, max_level=4, p_split=0.6, grid_fn=synth.normal_grid(1.0, 1.0))
+    cam = synth.orbit_camera(3, 96, 64, distance=1.8)
+    fr = Frame(DeviceScene.from_host(sc, max_level=16), cam, K=2)
+    fr.preprocess()
+    fr.bin_sort()
+    out = fr.forward()
+    ins = fr.inspect()
+    assert ins["n_pairs"] > 1500
+    compare_integers(sc, cam, ins)
+    compare_images(out, oracle.render(sc, cam, K=2))

@@ -221,18 +221,27 @@ def random_octree_scene(seed: int, max_level: int = 3, p_split: float = 0.5,
 
 def value_noise(p: np.ndarray, freq: float, seed: int, octave: int) -> np.ndarray:
     """Lattice value noise in [-1, 1]: hashed lattice values, smoothstep
-    trilinear interpolation, `freq` lattice cells per unit length."""
+    trilinear interpolation, `freq` lattice cells per unit length.  The
+    lattice values over the points' bounding box are hashed once into a table
+    and gathered (the same values as hashing per point)."""
     g = p * freq
     i0 = np.floor(g).astype(np.int64)
     f = g - i0
     s = f * f * (3.0 - 2.0 * f)
+    if len(p) == 0:
+        return np.zeros(0)
+    lo = i0.min(axis=0)
+    ext = i0.max(axis=0) - lo + 2
+    ax = [np.arange(lo[a], lo[a] + ext[a]) for a in range(3)]
+    li, lj, lk = np.meshgrid(ax[0], ax[1], ax[2], indexing="ij")
+    table = (2.0 * hash_uniform(seed, 7919 + octave, li.ravel(), lj.ravel(), lk.ravel()) - 1.0)
+    rel = i0 - lo
+    base = (rel[:, 0] * ext[1] + rel[:, 1]) * ext[2] + rel[:, 2]
     out = np.zeros(len(p))
     for b in range(8):
         o = _BITS[b]
         w = np.prod(np.where(o[None] == 1, s, 1.0 - s), axis=1)
-        ii = i0 + o[None]
-        v = 2.0 * hash_uniform(seed, 7919 + octave, ii[:, 0], ii[:, 1], ii[:, 2]) - 1.0
-        out += w * v
+        out += w * table[base + (o[0] * ext[1] + o[1]) * ext[2] + o[2]]
     return out
 
 

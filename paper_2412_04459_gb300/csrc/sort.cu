@@ -1,18 +1,19 @@
-// Tile ranges, render work order and the per-tile sort of the (key, value)
-// pairs.
+// Tile ranges, render work order and the radix sort of the (key, value)
+// pairs by (tile id, Morton order).
 //
-// Pairs arrive grouped by tile (k_emit writes each tile's pairs into its own
-// range, in no particular order), so each tile's range is sorted on its own,
-// in shared memory, by (key, value) (the keys of one tile share the tile id):
+// The tile id is the most significant digit and is sorted by counting: the
+// scan of the per-tile counts gives every tile its range and k_emit writes
+// each pair into its tile's range (order within a tile arbitrary).  The
+// Morton bits that can differ are then sorted tile by tile:
 //   k_tile_order   the tiles' ranges from the scanned counts, and the render
 //                  work order: one entry per tile, or per 1024-entry segment
 //                  of a longer list, longest first
-//   k_sort_small   one CTA per list of at most 1024 pairs, and per 1024-pair
-//                  chunk of a longer list: bitonic sort, warp shuffles for
-//                  the short strides, shared memory for the long ones
-//   k_merge_runs   lists longer than 1024 pairs: their sorted chunks merged
-//                  in rounds of pairwise merges (merge-path partitioning over
-//                  the CTA's threads), in shared memory up to 8192 pairs
+//   k_sort_small   one CTA per list of at most 1024 pairs and per 1024-pair
+//                  chunk of a longer list: stable LSD radix passes of 8-bit
+//                  digits in shared memory
+//   k_merge_runs   lists longer than 1024 pairs: their sorted chunks merged in
+//                  rounds of pairwise stable merges (merge-path partitioning
+//                  over the CTA's threads), in shared memory up to 8192 pairs
 // The result equals a sort of all pairs by (key, value).
 #include "svr_internal.cuh"
 
@@ -26,7 +27,7 @@ namespace svr {
 // heaviest work starts early and short lists fill the tail (one CTA; the
 // order within a group is arbitrary and results do not depend on it).  Also
 // resets the frame's forward-done mark (the segment sums belong to the last
-// sort) and the merge's work counter.
+// sort) and the long-list sort's work counter.
 // Group of a list in the work order: floor(log2(length)) + 1, one more for a
 // split list, so that every split list (longer than kSegLen) precedes every
 // unsplit one.
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
         f.status->n_queue = acc;
         f.status->slots_used = slot_next;
         f.status->fwd_done = 0;
-        f.status->merge_next = 0;
+        f.status->sort_next = 0;
     }
     __syncthreads();
     for (int i = t; i < ntiles; i += blockDim.x) {
@@ -84,124 +85,148 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
     }
 }
 
-// ------------------------------------------------------------ bitonic sort
+// -------------------------------------------------------- per-tile radix
 
-constexpr int kSmallThreads = 512;
-constexpr int kSmallPairs = kSegLen;
+constexpr int kSmallThreads = 256;
+constexpr int kSmallPairs = kSegLen;    // lists up to this length: one CTA each, shared memory
+constexpr int kIdxBits = 16;            // low bits of a sort word: index (or value rank) in the list
 
-__device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
-    return ka < kb || (ka == kb && va < vb);
+// Digit counts and per-warp offsets of one counting pass.
+template <int THREADS>
+struct RadixTables {
+    uint32_t run[256];                  // next output position of each digit
+    uint32_t wcnt[THREADS / 32][256];   // pairs of each digit in each warp's part of a round
+    uint32_t wpre[THREADS / 32][256];   // output position of each warp's first pair of each digit
+    uint32_t wsum[8];
+};
+
+template <int THREADS>
+__device__ void radix_tables_clear(RadixTables<THREADS> &tb) {
+    for (int i = threadIdx.x; i < (THREADS / 32) * 256; i += THREADS) (&tb.wcnt[0][0])[i] = 0;
 }
 
-__device__ __forceinline__ int pow2_at_least(int n) {
-    return n <= 1 ? 1 : 1 << (32 - __clz(n - 1));
-}
-
-// Compare-exchange of a warp-held element with the element `stride` lanes
-// away (stride < 32): the element at index i keeps the smaller of the two
-// when (i & stride) == 0 matches the direction `up`, else the larger.
-__device__ __forceinline__ void cx_shfl(uint64_t &x, int i, int stride, bool up) {
-    const uint64_t p = __shfl_xor_sync(0xffffffffu, x, stride);
-    const bool keep_min = ((i & stride) == 0) == up;
-    if ((p < x) == keep_min) x = p;
-}
-
-// Bitonic sort of N (power of two, 64 <= N <= kSmallPairs) distinct 64-bit
-// words.  Warp w holds elements 64w + lane (a) and 64w + 32 + lane (b) in
-// registers: steps of stride < 32 are warp shuffles, stride 32 an exchange
-// within the lane, and only strides >= 64 go through shared memory (sx).
-__device__ void bitonic_words(uint64_t &a, uint64_t &b, int N, uint64_t *sx) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool active = warp < N / 64;  // warps past the padded length only join the barriers
-    const int ia = 64 * warp + lane, ib = ia + 32;
-    for (int size = 2; size <= N; size <<= 1) {
-        if (size > 64) {
-            if (active) sx[ia] = a, sx[ib] = b;
-            __syncthreads();
-            for (int stride = size >> 1; stride >= 64; stride >>= 1) {
-                for (int t = threadIdx.x; t < N / 2; t += kSmallThreads) {
-                    const int i = 2 * t - (t & (stride - 1));
-                    const int l = i + stride;
-                    const uint64_t xi = sx[i], xl = sx[l];
-                    if ((xl < xi) == ((i & size) == 0)) sx[i] = xl, sx[l] = xi;
-                }
-                __syncthreads();
-            }
-            if (active) a = sx[ia], b = sx[ib];
-            __syncthreads();
-        }
-        if (active) {
-            const bool up_a = (ia & size) == 0, up_b = (ib & size) == 0;
-            int stride = size >> 1;
-            if (stride >= 32) {  // a and b are each other's partner (ia has bit 32 clear)
-                if ((b < a) == up_a) {
-                    const uint64_t t = a;
-                    a = b, b = t;
-                }
-                stride = 16;
-            }
-            for (; stride > 0; stride >>= 1) {
-                cx_shfl(a, ia, stride, up_a);
-                cx_shfl(b, ib, stride, up_b);
-            }
-        }
+// One stable counting pass of the n words src -> dst by the 8-bit digit at
+// bit `shift`: digit histogram (one shared atomic per digit value present in
+// a warp), exclusive scan, then rounds of THREADS words in index order, each
+// word going to its digit's next position plus its rank among the earlier
+// words of the round with the same digit (warp match, per-warp counts).
+template <int THREADS, class Src, class Dst>
+__device__ void radix_pass(Src src, Dst dst, int n, int shift, RadixTables<THREADS> &tb) {
+    constexpr int W = THREADS / 32;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    if (t < 256) tb.run[t] = 0;
+    __syncthreads();
+    for (int c = 0; c < n; c += THREADS) {
+        const int i = c + t;
+        const uint32_t d = i < n ? (uint32_t)(src(i) >> shift) & 0xFFu : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&tb.run[d], (uint32_t)__popc(peers));
     }
+    __syncthreads();
+    uint32_t x = 0, inc = 0;
+    if (t < 256) {
+        x = tb.run[t];
+        inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) tb.wsum[warp] = inc;
+    }
+    __syncthreads();
+    if (t < 256) {
+        uint32_t wp = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) wp += w < warp ? tb.wsum[w] : 0u;
+        tb.run[t] = wp + inc - x;
+    }
+    __syncthreads();
+    for (int c = 0; c < n; c += THREADS) {
+        const int i = c + t;
+        const bool valid = i < n;
+        const uint64_t word = valid ? src(i) : 0ull;
+        const uint32_t d = valid ? (uint32_t)(word >> shift) & 0xFFu : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) tb.wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (t < 256) {
+            uint32_t acc = tb.run[t];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                tb.wpre[w][t] = acc;
+                acc += tb.wcnt[w][t];
+                tb.wcnt[w][t] = 0;
+            }
+            tb.run[t] = acc;
+        }
+        __syncthreads();
+        if (valid) dst(tb.wpre[warp][d] + rank, word, i);
+    }
+    __syncthreads();
 }
 
-// Sorts the n <= kSmallPairs pairs at (gk, gv) of one tile by (key, value).
-// The keys of a tile share the tile id, so the order is that of bits
-// [lo_bit, lo_bit + nbits) of the key.  Below max level 16 these bits differ
-// between any two pairs of a tile, and each pair is sorted as the word
-// (bits << 10 | its index), then gathered by index.  With max level 16
-// (ties: equal bits possible) the word is (bits << 16 | rank of the value
-// among the tile's values), the ranks coming from a first sort of
-// (value << 10 | index).
-__device__ void chunk_sort(uint64_t *__restrict__ gk, uint32_t *__restrict__ gv, int n, int lo_bit, int nbits,
-                           bool ties, uint64_t *sx, uint64_t *ok, uint32_t *ov, uint16_t *inv) {
-    const int N = max(64, pow2_at_least(n));
-    const int warp = threadIdx.x >> 5;
-    const bool active = warp < N / 64;
-    const int ia = 64 * warp + (threadIdx.x & 31), ib = ia + 32;
+// Sorts one tile's n <= cap pairs (gk, gv) in shared memory: each pair
+// becomes the word (Morton bits << kIdxBits | its index), stable LSD passes
+// over the Morton bits [lo_bit, lo_bit + nbits) sort the words, and the
+// pairs are gathered by index from ok/ov (their unsorted copy).  Within a
+// tile the Morton bits differ between any two pairs below max level 16;
+// with max level 16 (ties) the low word bits hold the pair's value rank
+// instead, from a first sort of (value << kIdxBits | index), so that equal
+// keys end in value order.
+template <int THREADS>
+__device__ void tile_radix_sort(uint64_t *__restrict__ gk, uint32_t *__restrict__ gv, int n, int lo_bit, int nbits,
+                                bool ties, uint64_t *w0, uint64_t *w1, const uint64_t *ok, const uint32_t *ov,
+                                uint16_t *inv, RadixTables<THREADS> &tb) {
     const uint64_t mask = nbits >= 64 ? ~0ull : (1ull << nbits) - 1ull;
-    for (int i = threadIdx.x; i < n; i += kSmallThreads) ok[i] = gk[i], ov[i] = gv[i];
-    __syncthreads();
-    uint64_t a = ~0ull, b = ~0ull;
+    auto from0 = [&](int i) { return w0[i]; };
+    auto from1 = [&](int i) { return w1[i]; };
+    auto to0 = [&](uint32_t p, uint64_t w, int) { w0[p] = w; };
+    auto to1 = [&](uint32_t p, uint64_t w, int) { w1[p] = w; };
+    radix_tables_clear<THREADS>(tb);
+    int cur = 0;  // words in w0
     if (ties) {
-        if (ia < n) a = ((uint64_t)ov[ia] << 10) | (uint64_t)ia;
-        if (ib < n) b = ((uint64_t)ov[ib] << 10) | (uint64_t)ib;
-        bitonic_words(a, b, N, sx);
-        __syncthreads();
-        uint32_t *rank = reinterpret_cast<uint32_t *>(sx);  // sx is free until the next sort
-        if (active) {
-            if (ia < n) rank[a & 1023u] = (uint32_t)ia, inv[ia] = (uint16_t)(a & 1023u);
-            if (ib < n) rank[b & 1023u] = (uint32_t)ib, inv[ib] = (uint16_t)(b & 1023u);
+        for (int i = threadIdx.x; i < n; i += THREADS) w0[i] = ((uint64_t)ov[i] << kIdxBits) | (uint64_t)i;
+        for (int b = 0; b < 32; b += 8, cur ^= 1) {
+            if (cur == 0) radix_pass<THREADS>(from0, to1, n, kIdxBits + b, tb);
+            else radix_pass<THREADS>(from1, to0, n, kIdxBits + b, tb);
         }
+        const uint64_t *ws = cur ? w1 : w0;
+        uint64_t *wd = cur ? w0 : w1;
+        for (int p = threadIdx.x; p < n; p += THREADS) inv[p] = (uint16_t)(ws[p] & 0xFFFFu);
         __syncthreads();
-        a = ia < n ? (((ok[ia] >> lo_bit) & mask) << 16) | rank[ia] : ~0ull;
-        b = ib < n ? (((ok[ib] >> lo_bit) & mask) << 16) | rank[ib] : ~0ull;
-        __syncthreads();
+        for (int p = threadIdx.x; p < n; p += THREADS) {
+            const int i = inv[p];
+            wd[i] = (((ok[i] >> lo_bit) & mask) << kIdxBits) | (uint64_t)p;  // p = value rank of pair i
+        }
+        cur ^= 1;
     } else {
-        if (ia < n) a = (((ok[ia] >> lo_bit) & mask) << 10) | (uint64_t)ia;
-        if (ib < n) b = (((ok[ib] >> lo_bit) & mask) << 10) | (uint64_t)ib;
+        for (int i = threadIdx.x; i < n; i += THREADS)
+            w0[i] = (((ok[i] >> lo_bit) & mask) << kIdxBits) | (uint64_t)i;
     }
-    bitonic_words(a, b, N, sx);
     __syncthreads();
-    if (active) sx[ia] = a, sx[ib] = b;  // position p: the word of the pair that sorts p-th
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
-        const uint64_t w = sx[i];
-        const int src = ties ? (int)inv[w & 0xFFFFu] : (int)(w & 1023u);
-        gk[i] = ok[src];
-        gv[i] = ov[src];
+    for (int b = 0; b < nbits; b += 8, cur ^= 1) {
+        if (cur == 0) radix_pass<THREADS>(from0, to1, n, kIdxBits + b, tb);
+        else radix_pass<THREADS>(from1, to0, n, kIdxBits + b, tb);
+    }
+    const uint64_t *ws = cur ? w1 : w0;
+    for (int p = threadIdx.x; p < n; p += THREADS) {
+        const int low = (int)(ws[p] & 0xFFFFu);
+        const int i = ties ? inv[low] : low;
+        gk[p] = ok[i];
+        gv[p] = ov[i];
     }
 }
 
 // A whole list of at most kSmallPairs pairs, or one kSegLen-pair chunk of a
 // longer list (merged afterwards); one CTA per work-order entry.
 __global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f, int lo_bit, int nbits, bool ties) {
-    __shared__ uint64_t sx[kSmallPairs];
+    __shared__ uint64_t w[2][kSmallPairs];
     __shared__ uint64_t ok[kSmallPairs];
     __shared__ uint32_t ov[kSmallPairs];
+    __shared__ RadixTables<kSmallThreads> tb;
     __shared__ uint16_t inv[kSmallPairs];
     if (blockIdx.x >= f.status->n_queue) return;
     const uint2 q = f.order[blockIdx.x];
@@ -218,10 +243,16 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f, int lo
         return;
     }
     if (n < 2) return;
-    chunk_sort(f.keys[0] + c0, f.vals[0] + c0, n, lo_bit, nbits, ties, sx, ok, ov, inv);
+    uint64_t *gk = f.keys[0] + c0;
+    uint32_t *gv = f.vals[0] + c0;
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) ok[i] = gk[i], ov[i] = gv[i];
+    __syncthreads();
+    tile_radix_sort<kSmallThreads>(gk, gv, n, lo_bit, nbits, ties, w[0], w[1], ok, ov, inv, tb);
 }
 
-// ----------------------------------------------------------- merge of runs
+__device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
+    return ka < kb || (ka == kb && va < vb);
+}
 
 constexpr int kMergeThreads = 1024;
 constexpr int kMergePairs = 8192;  // longest list merged in shared memory (2 x 96 KB)
@@ -269,7 +300,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_runs(FrameDev f) {
     __shared__ unsigned entry;
     const unsigned nq = f.status->n_queue;
     for (;;) {
-        if (threadIdx.x == 0) entry = atomicAdd(&f.status->merge_next, 1u);
+        if (threadIdx.x == 0) entry = atomicAdd(&f.status->sort_next, 1u);
         __syncthreads();
         const unsigned e = entry;
         __syncthreads();

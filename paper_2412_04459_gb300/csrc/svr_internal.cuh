@@ -61,7 +61,7 @@ struct Status {
     unsigned n_queue;     // (tile, segment) entries of the render work order
     unsigned slots_used;  // segment slots taken by the split tiles
     unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort
-    unsigned merge_next;  // next work-order entry of the run merge
+    unsigned sort_next;   // next work-order entry of the long-list sort
     unsigned pad[6];
 };
 

@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["shell1m", "dense5"], default="shell1m")
+    ap.add_argument("--workload", choices=["shell1m", "dense5", "shell8m"], default="shell1m",
+                    help="shell8m: the large batched workload (8 x 2560x1440 views of ~8M voxels), "
+                         "timed on its own")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1536)
@@ -455,6 +457,134 @@ def run_batched(args, scene, dscene, dev, kw, n_views=16, steps=10):
             "speedup": ms_per_view / ms_batched, "l2": "flushed before each timed step"}
 
 
+def sampled_parity(scene, cams, out, pixel_base, n_px, seed):
+    """Largest absolute difference of rgb, depth and alpha between batched
+    outputs (numpy, batch layout) and the oracle on n_px seeded pixels of
+    every view, pixels near the stop threshold excluded."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    err = 0.0
+    for v, cam in enumerate(cams):
+        W, H = cam.width, cam.height
+        px = np.stack([rng.integers(0, W, n_px), rng.integers(0, H, n_px)], 1)
+        ref = oracle.render(scene, cam, K=3, t_stop=1e-4, pixels=px)
+        keep = ref["near_stop"] == 0
+        base = int(pixel_base[v])
+        lin = px[:, 1] * W + px[:, 0]
+        rgb = np.stack([out["rgb"][3 * base + c * W * H + lin] for c in range(3)], 0)
+        err = max(err, float(np.abs(rgb[:, keep] - ref["rgb"].T[:, keep]).max(initial=0.0)),
+                  float(np.abs(out["depth"][base + lin][keep] - ref["depth"][keep]).max(initial=0.0)),
+                  float(np.abs(out["alpha"][base + lin][keep] - ref["alpha"][keep]).max(initial=0.0)))
+    return err
+
+
+def run_large_batched(args, n_views=8, width=2560, height=1440):
+    """The large batched workload: ~8M voxels (three noisy shells, levels
+    4..11, at most 4 levels between touching voxels), 8 orbit views at
+    2560x1440, K = 3, forward + backward in graph-captured batched launches
+    (tile size and partitions tuned among a few candidates) vs one launch
+    sequence per view; device memory in use against 180 GB; parity of the
+    images on a seeded pixel sample against the oracle."""
+    import torch
+    import synth
+    from paper_2412_04459_gb300 import DeviceScene, Frame
+    from paper_2412_04459_gb300 import build as gbuild
+    from paper_2412_04459_gb300.autotune import BatchedRenderer, tune
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    scene = synth.shell_scene(0, 8_000_000, spec=synth.scenes.SHELL_THREE)
+    gen_s = time.perf_counter() - t0
+    free0, total = torch.cuda.mem_get_info(dev)
+    dscene = DeviceScene.from_host(scene, device=dev)
+    cams = [synth.orbit_camera(200 + v, width, height) for v in range(n_views)]
+    best = tune(dscene, cams, K=3, t_stop=1e-4, tiles=(16, 32), partitions=(1, 2), reps=2, use_cache=False)
+    r = BatchedRenderer(dscene, cams, K=3, t_stop=1e-4, tile=best["tile"], partitions=best["partitions"]).capture()
+    g = torch.Generator(device=dev).manual_seed(5)
+    for x in r.grads:
+        x.normal_(generator=g)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ts]))
+
+    steps = max(3, min(args.steps, 10))
+    clk = ClockSampler(0)
+    clk.start()
+    ms_batched = timed(r.step, steps)
+    clocks = clk.stop()
+    flags, pairs = r.status()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    used = total - free1
+    allocated = torch.cuda.memory_allocated(dev)
+    ws_bytes = sum(fr.ws_bytes() for fr in r.frames)
+    # parity on a seeded pixel sample of every view (forward outputs)
+    out = {k: v.detach().cpu().numpy() for k, v in r.out.items()}
+    n_px = 128
+    t1 = time.perf_counter()
+    max_err = sampled_parity(scene, cams, out, r.pixel_base, n_px, seed=11)
+    parity_s = time.perf_counter() - t1
+    del r
+    torch.cuda.empty_cache()
+    # the same views as one launch sequence per view
+    frames = []
+    for c in cams:
+        fr = Frame(dscene, c, K=3, t_stop=1e-4, tile=best["tile"])
+        fr.render()
+        fr.pair_capacity = int(fr.n_pairs * 1.15) + 4096
+        fr.ws = None
+        fr._alloc()
+        o = fr.new_outputs()
+        gg = [torch.randn(3 * c.width * c.height, device=dev), torch.randn(c.width * c.height, device=dev),
+              torch.randn(c.width * c.height, device=dev)]
+        frames.append((fr, o, gg))
+    d_grid = torch.zeros(scene.n_pts, device=dev)
+    d_sh = torch.empty(scene.n_vox, 48, device=dev)
+
+    def per_view():
+        d_grid.zero_()
+        for fr, o, gg in frames:
+            fr.preprocess()
+            fr.bin_sort(sync=False)
+            fr.forward(o)
+            fr.backward(gg[0], gg[1], gg[2], o, d_grid, d_sh)
+
+    ms_per_view = timed(per_view, steps)
+    pixels = n_views * width * height
+    line = {
+        "metric": "large batched fwd+bwd views/s (8 x 2560x1440, ~8M voxels)", "value": n_views * 1000.0 / ms_batched,
+        "unit": "views/s", "n_gpus": 1, "steps": steps, "ms_per_step": ms_batched, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"three noisy shells, {scene.n_vox} voxels (levels 4-11, at most 4 levels between "
+                               f"touching voxels), {n_views} orbit views {width}x{height}, K=3, t_stop=1e-4, "
+                               "forward+backward", "voxels": scene.n_vox, "grid_points": scene.n_pts,
+                   "pixels": pixels, "pairs": pairs, "flags": flags, "tile": best["tile"],
+                   "partitions": best["partitions"], "tuning_ms": best["ms"],
+                   "l2": "flushed before each timed step"},
+        "ms_per_view_launches": ms_per_view, "speedup_vs_per_view": ms_per_view / ms_batched,
+        "memory": {"device_used_gb": used / 1e9, "allocated_gb": allocated / 1e9,
+                   "before_scene_used_gb": (total - free0) / 1e9,
+                   "workspace_gb": ws_bytes / 1e9, "budget_gb": 180.0, "frac_of_budget": used / 180e9,
+                   "total_gb": total / 1e9},
+        "parity": {"pixels": n_px * n_views, "max_abs_err": max_err, "tolerance": 1e-4,
+                   "oracle_s": parity_s},
+        "scene_generation_s": gen_s, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def frame_algorithmic_bytes(scene, P, H, W):
     """Minimal HBM bytes of one forward+backward step (FP32 storage): scene
     read once, pairs written/sorted/read once, images written and read, the
@@ -494,6 +624,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "shell8m":
+        if rank == 0:
+            run_large_batched(args)
         return
     if world > 1:
         import torch

@@ -54,6 +54,7 @@ class BatchedRenderer:
         for fr in self.frames:
             fr.render()
             fr.pair_capacity = int(fr.n_pairs * 1.15) + 4096
+            fr.ws = None        # the sizing render's workspace is larger than needed
             fr._alloc()
         pix = [c.width * c.height for c in self.cams]
         self.pixel_base = np.concatenate([[0], np.cumsum(pix)]).astype(np.int64)

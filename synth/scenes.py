@@ -133,6 +133,59 @@ class Scene:
         return int(self.level.max()) if self.n_vox else 0
 
 
+_N26 = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)
+                 if (a, b, c) != (0, 0, 0)], np.int64)
+
+
+def _cell_key(level, ijk: np.ndarray) -> np.ndarray:
+    level = np.broadcast_to(np.asarray(level, np.int64), ijk.shape[:1])
+    return (level << 51) | (ijk[:, 0] << 34) | (ijk[:, 1] << 17) | ijk[:, 2]
+
+
+def balance_levels(cells: Cells, max_diff: int) -> Cells:
+    """Split leaves until no two leaves that touch (share a face, edge or
+    corner) differ by more than max_diff levels.
+
+    A leaf B at level l touches a leaf coarser than l - max_diff exactly when
+    one of the 26 neighbours of B's level-(l - max_diff) ancestor is not a node
+    of the tree (it lies inside a coarser leaf); that coarser leaf is split,
+    and the check repeats until nothing changes.
+    """
+    if len(cells) == 0:
+        return cells
+    while True:
+        lmin, lmax = int(cells.level.min()), int(cells.level.max())
+        by_level = {l: cells.ijk[cells.level == l] for l in range(lmin, lmax + 1)}
+        leaf_keys = {l: np.sort(_cell_key(l, v)) for l, v in by_level.items()}
+        # nodes (leaves and their ancestors) of each level
+        nodes = {}
+        for m in range(lmin, lmax + 1):
+            parts = [by_level[l] >> (l - m) for l in range(m, lmax + 1) if len(by_level[l])]
+            nodes[m] = np.unique(_cell_key(m, np.concatenate(parts))) if parts else np.zeros(0, np.int64)
+        split_keys = []
+        for l in range(lmin + max_diff + 1, lmax + 1):
+            if not len(by_level[l]):
+                continue
+            m = l - max_diff
+            anc = np.unique(by_level[l] >> max_diff, axis=0)
+            nb = (anc[:, None, :] + _N26[None]).reshape(-1, 3)
+            nb = nb[((nb >= 0) & (nb < (1 << m))).all(axis=1)]
+            nb = np.unique(nb, axis=0)
+            missing = nb[~np.isin(_cell_key(m, nb), nodes[m])]
+            for m2 in range(m - 1, lmin - 1, -1):
+                if not len(missing):
+                    break
+                up = missing >> (m - m2)
+                hit = np.isin(_cell_key(m2, up), leaf_keys[m2])
+                if hit.any():
+                    split_keys.append(np.unique(_cell_key(m2, up[hit])))
+                missing = missing[~hit]
+        if not split_keys:
+            return cells
+        go = np.isin(_cell_key(cells.level, cells.ijk), np.unique(np.concatenate(split_keys)))
+        cells = Cells.cat([cells.take(~go), split(cells.take(go))])
+
+
 def corner_points(cells: Cells):
     """Shared grid points of a leaf set: (corner_idx [N, 8], positions [Pts, 3])."""
     n = len(cells)
@@ -319,7 +372,7 @@ SHELL_ONE = dict(base_level=4, max_level=9, centers=((0.5, 0.5, 0.5),), radii=(0
                  band=0.02, amp=0.05)
 SHELL_THREE = dict(base_level=4, max_level=11,
                    centers=((0.47, 0.5, 0.52), (0.53, 0.48, 0.5), (0.5, 0.52, 0.47)),
-                   radii=(0.25, 0.33, 0.41), band=0.01, amp=0.05)
+                   radii=(0.25, 0.33, 0.41), band=0.01, amp=0.05, max_level_diff=4)
 
 
 def shell_scene(seed: int = 0, target: int = 1 << 20, p_split: float | None = None,
@@ -368,12 +421,15 @@ def _load(path):
 
 def _shell_scene(seed, target, p_split, spec, sh_std, near_mean, near_std, far_value):
     spec = dict(SHELL_ONE if spec is None else spec)
+    max_diff = spec.pop("max_level_diff", None)
     if p_split is None:
         key = (seed, target, tuple(sorted((k, str(v)) for k, v in spec.items())))
         if key not in _SHELL_P:
             _SHELL_P[key] = calibrate_shell(target, seed, **spec)
         p_split = _SHELL_P[key]
     cells = _shell_cells(seed, p_split, **spec)
+    if max_diff is not None:
+        cells = balance_levels(cells, max_diff)
     rng = np.random.default_rng(seed)
 
     def grid_fn(pos, rng):

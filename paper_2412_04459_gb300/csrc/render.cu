@@ -54,6 +54,7 @@ namespace svr {
 
 constexpr int kWarps = 8;          // warps per CTA of the forward
 constexpr int kThreads = kWarps * 32;
+constexpr int kFwdMinBlocks = 3;   // resident CTAs per SM the forward's register budget is sized for
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
 constexpr int kBwdThreads = kBwdWarps * 32;
 constexpr int kBwdMinBlocks = 5;   // resident CTAs per SM the register budget is sized for
@@ -445,23 +446,123 @@ struct FwdState {
     int n_cand, n_hit;
 };
 
-// Walk block-list positions [p0, p1) front to back from state s.
+// Asynchronous staging of the forward.  A slot receives a voxel's 64-byte
+// record as copied (cp.async, 16 bytes per copy, no registers involved);
+// once the copy has landed, lane j turns the first part (min corner, size)
+// of its slot into the entry plane and 1 / size and writes the exit plane,
+// both from the entry's sign bits.  Slots are 80 bytes apart, which spreads
+// lanes reading different slots over the shared-memory banks.
+struct FwdSlot {
+    float4 a;    // copied: min corner relative to r_o, size; then: entry plane, 1 / size
+    float4 g0;   // raw corner densities 0..3
+    float4 g1;   // raw corner densities 4..7
+    float4 col;  // colour, clamp bits
+    float4 b;    // exit plane
+};
+
+struct FwdSmem {
+    FwdSlot slot[2][kBatch];  // double buffer: the batch being composited and the next one
+    uint2 meta[2][kBatch];    // (value, sorted index) of each staged entry
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Lane j starts the copy of its entry's record into buffer buf; every lane
+// commits a group (possibly empty) so that the group counts stay aligned.
+__device__ __forceinline__ void stage_async(FwdSmem &ws, int buf, const ViewData &vd, const Lookahead &la) {
+    const int lane = threadIdx.x & 31;
+    if (la.valid) {
+        const Record *r = vd.rec + (la.vi.x & 0x1FFFFFFFu);
+        FwdSlot &d = ws.slot[buf][lane];
+        cp_async16(&d.a, &r->r0);
+        cp_async16(&d.g0, &r->r1);
+        cp_async16(&d.g1, &r->r2);
+        cp_async16(&d.col, &r->r3);
+        ws.meta[buf][lane] = la.vi;
+    }
+    cp_async_commit();
+}
+
+// Entry and exit planes of lane j's staged record (copied: min corner, size)
+// from the entry's sign bits s: the near corner is min + size on the axes
+// where r_d is negative.
+__device__ __forceinline__ void slot_planes(FwdSlot &d, uint32_t s) {
+    const float4 r0 = d.a;
+    const float hx = r0.x + r0.w, hy = r0.y + r0.w, hz = r0.z + r0.w;
+    d.a = make_float4((s & 4) ? hx : r0.x, (s & 2) ? hy : r0.y, (s & 1) ? hz : r0.z, 1.0f / r0.w);
+    d.b = make_float4((s & 4) ? r0.x : hx, (s & 2) ? r0.y : hy, (s & 1) ? r0.z : hz, 0.f);
+}
+
+__device__ __forceinline__ bool slab_slot(const FwdSlot &e, const PixelRay &p, float &a, float &b) {
+    const float4 ea = e.a, eb = e.b;
+    a = fmaxf(fmaxf(ea.x * p.inv.x, ea.y * p.inv.y), ea.z * p.inv.z);
+    b = fminf(fminf(eb.x * p.inv.x, eb.y * p.inv.y), eb.z * p.inv.z);
+    return a <= b && a > 0.f;
+}
+
+// Local depth and transmittance factor of a hit on a staged slot (its sign
+// bits are the pixel's, sb = 1 where r_d is negative: the min corner is the
+// exit plane there and the entry plane elsewhere).
+template <int K>
+__device__ __forceinline__ void hit_fwd_slot(const FwdSlot &e, const PixelRay &p, const float3 &sb, float a,
+                                             float b, float &trans, float &dloc) {
+    const float inv_k = 1.0f / K;
+    const float seg = b - a;
+    const float xs = seg * p.rdn * inv_k;
+    const float step = seg * inv_k;
+    const float4 ea = e.a, eb = e.b;
+    const float inv = ea.w;
+    const float cx = (sb.x != 0.f ? eb.x : ea.x) * inv, cy = (sb.y != 0.f ? eb.y : ea.y) * inv,
+                cz = (sb.z != 0.f ? eb.z : ea.z) * inv;
+    const float4 g0 = e.g0, g1 = e.g1;
+    const float rx = p.rd.x * inv, ry = p.rd.y * inv, rz = p.rd.z * inv;
+    float t = fmaf(0.5f, step, a);
+    float P = 1.f, d = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float v = trilerp(g0, g1, fmaf(t, rx, -cx), fmaf(t, ry, -cy), fmaf(t, rz, -cz));
+        const float ek = __expf(-xs * explin(v));
+        d = fmaf(P * (1.f - ek), t, d);
+        P *= ek;
+        t += step;
+    }
+    trans = P;
+    dloc = d;
+}
+
+// Walk block-list positions [p0, p1) front to back from state s.  The list
+// entries are fetched two batches ahead and the next batch's records are
+// copied into the other staging buffer while this batch is composited.
 template <int K, bool STATS>
 __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0, int p1, const ViewData &vd,
-                                         const PixelRay &p, const WarpBlock &wb, Entry *st, float t_stop,
+                                         const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, float t_stop,
                                          FwdState &s) {
     const int lane = threadIdx.x & 31;
-    Lookahead la;
-    fetch_vi(la, list, p0 + lane, p0 + lane < p1);
-    fetch_box(la, vd);
-    for (int base = p0; base < p1; base += kBatch) {
+    const float3 sb = make_float3((p.s & 4) ? 1.f : 0.f, (p.s & 2) ? 1.f : 0.f, (p.s & 1) ? 1.f : 0.f);
+    Lookahead cur, nx, nn;
+    fetch_vi(cur, list, p0 + lane, p0 + lane < p1);
+    fetch_box(cur, vd);
+    stage_async(ws, 0, vd, cur);
+    fetch_vi(nx, list, p0 + kBatch + lane, p0 + kBatch + lane < p1);
+    int buf = 0;
+    for (int base = p0; base < p1; base += kBatch, buf ^= 1) {
         if (__all_sync(0xffffffffu, s.done)) break;
-        const Lookahead cur = la;
-        const int npos = base + kBatch + lane;
-        fetch_vi(la, list, npos, npos < p1);
+        fetch_box(nx, vd);
+        stage_async(ws, buf ^ 1, vd, nx);
+        const int npos = base + 2 * kBatch + lane;
+        fetch_vi(nn, list, npos, npos < p1);
         const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
-        stage_ahead(st, vd, cur);
-        fetch_box(la, vd);
+        cp_async_wait<1>();  // this batch's copies (the next batch's may still be in flight)
+        __syncwarp();
+        if (cur.valid) slot_planes(ws.slot[buf][lane], cur.vi.x >> 29);
+        __syncwarp();
+        const FwdSlot *st = ws.slot[buf];
         // phase A: this pixel's hits among its candidate entries
         unsigned hits = 0;
         if (!s.done) {
@@ -469,7 +570,7 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                 const int k = __ffs(c) - 1;
                 if (STATS) ++s.n_cand;
                 float a, b;
-                if (slab(st[k], p, a, b)) hits |= 1u << k;
+                if (slab_slot(st[k], p, a, b)) hits |= 1u << k;
             }
         }
         // phase B: composite them in list order, one hit per pixel per round
@@ -477,27 +578,32 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
             if (hits != 0) {
                 const int k = __ffs(hits) - 1;
                 hits &= hits - 1;
-                const Entry &e = st[k];
+                const FwdSlot &e = st[k];
                 float a, b;
-                slab(e, p, a, b);
+                slab_slot(e, p, a, b);
                 if (STATS) ++s.n_hit;
                 float P, dloc;
-                hit_fwd<K>(e, p, a, b, P, dloc);
+                hit_fwd_slot<K>(e, p, sb, a, b, P, dloc);
+                const float4 col = e.col;
                 const float w = s.T * (1.f - P);
-                s.C0 = fmaf(w, e.col.x, s.C0);
-                s.C1 = fmaf(w, e.col.y, s.C1);
-                s.C2 = fmaf(w, e.col.z, s.C2);
+                s.C0 = fmaf(w, col.x, s.C0);
+                s.C1 = fmaf(w, col.y, s.C1);
+                s.C2 = fmaf(w, col.z, s.C2);
                 s.D = fmaf(s.T, dloc, s.D);
                 s.T *= P;
                 if (s.T < t_stop) {
                     s.done = true;
-                    s.last = __float_as_int(e.c.w);
+                    s.last = (int)ws.meta[buf][k].y;
                     hits = 0;
                 }
             }
         }
         __syncwarp();
+        cur = nx;
+        nx = nn;
     }
+    cp_async_wait<0>();  // no copy may land in a buffer after the walk
+    __syncwarp();
 }
 
 // Merge the segments of a split tile's block, front to back: segment sg was
@@ -509,7 +615,7 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
 // depth sums behind it (T_final bg included).
 template <int K, bool STATS>
 __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, int blk, const ViewData &vd,
-                                          const PixelRay &p, const WarpBlock &wb, Entry *st, FwdState &m) {
+                                          const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, FwdState &m) {
     const int B = f.blocks_per_tile;
     const int nseg = (int)L.ts.x;
     for (int sg = 0; sg < nseg; ++sg) {
@@ -541,7 +647,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0};
             int p0, p1;
             seg_range(L, B, sg, p0, p1);
-            fwd_walk<K, STATS>(L.list, p0, p1, vd, p, wb, st, f.t_stop, r);
+            fwd_walk<K, STATS>(L.list, p0, p1, vd, p, wb, ws, f.t_stop, r);
             if (need) {
                 c0 = r.C0;
                 c1 = r.C1;
@@ -603,7 +709,7 @@ __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, 
 }
 
 template <int K, bool STATS>
-__device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entry *st, const FwdOut &out) {
+__device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdSmem &ws, const FwdOut &out) {
     const ItemView iv = item_view(f, it.g);
     const DevCam &cam = f.views[iv.view];
     WarpBlock wb;
@@ -613,7 +719,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
     const int lane = threadIdx.x & 31;
     FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
     if (L.ts.x <= 1) {
-        fwd_walk<K, STATS>(L.list, 0, L.n_list, iv.vd, p, wb, st, f.t_stop, s);
+        fwd_walk<K, STATS>(L.list, 0, L.n_list, iv.vd, p, wb, ws, f.t_stop, s);
         fwd_write<STATS>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
         return;
     }
@@ -621,7 +727,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
     const int B = f.blocks_per_tile;
     int p0, p1;
     seg_range(L, B, it.seg, p0, p1);
-    fwd_walk<K, STATS>(L.list, p0, p1, iv.vd, p, wb, st, f.t_stop, s);
+    fwd_walk<K, STATS>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s);
     float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
     q[0] = s.C0;
     q[32] = s.C1;
@@ -643,7 +749,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
     // the last segment of the block to finish merges them all
     __threadfence();
     FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
-    fwd_merge<K, STATS>(f, L, it.blk, iv.vd, p, wb, st, m);
+    fwd_merge<K, STATS>(f, L, it.blk, iv.vd, p, wb, ws, m);
     fwd_write<STATS>(f, cam, p, m, m.last >= 0 ? m.last : L.end - 1, out);
     if (lane == 0) *cnt = 0;  // ready for the next forward of this sort
 }
@@ -652,14 +758,14 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, Entr
 // pixel box contains it (the slab tests it must make) and the hits it
 // composited (int2 per pixel), for work accounting.
 template <int K, bool STATS>
-__global__ void __launch_bounds__(kThreads, 4) k_render_fwd(FrameDev f, FwdOut out) {
-    __shared__ Entry stage[kWarps][kBatch];
-    Entry *st = stage[threadIdx.x >> 5];
+__global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev f, FwdOut out) {
+    __shared__ FwdSmem smem[kWarps];
+    FwdSmem &ws = smem[threadIdx.x >> 5];
     const unsigned bpt = (unsigned)f.blocks_per_tile;
     const unsigned n_items = f.status->n_queue * bpt;
     Item it;
     while (next_item(&f.status->fwd_next, n_items, bpt, f.order, it)) {
-        fwd_item<K, STATS>(f, it, st, out);
+        fwd_item<K, STATS>(f, it, ws, out);
         __syncwarp();
     }
 }

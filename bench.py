@@ -39,6 +39,10 @@ OPS_CAND = 12                         # slab test of one candidate entry
 OPS_HIT = {1: 42, 2: 71, 3: 100}      # one composited segment (forward)
 OPS_HIT_BWD = {1: 98, 2: 156, 3: 214}  # one segment in the backward (recompute + gradient)
 BATCH_SIZES = ((640, 480), (1280, 840), (1920, 1080))
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_render_bwd<3> launch of
+# this workload, from the ncu capture summarised in profiles/render_bwd_shell1m.md
+# (to be retaken, or set to None, whenever that kernel changes)
+BWD_TRAFFIC_BYTES = 323_572_736
 
 
 def parse():
@@ -310,7 +314,7 @@ def run_native(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world} (one view per rank)"},
         "fwd_frames_per_s": fwd_fps, "ms_fwd": ms_fwd, "ms_per_call": per_call,
         "roofline": {"bound": "alu", "kernel": "k_render_bwd", "achieved": achieved_bwd, "peak": alu_peak,
-                     "unit": "T FP32 lane-ops/s", "frac": achieved_bwd / alu_peak, "traffic": None,
+                     "unit": "T FP32 lane-ops/s", "frac": achieved_bwd / alu_peak, "traffic": BWD_TRAFFIC_BYTES,
                      "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
                               "ops_per_hit": OPS_HIT_BWD[K]},
                      "timed": "svr_render_bwd call: k_render_bwd + k_voxel_bwd + 2 memsets",
@@ -347,7 +351,7 @@ def run_e2e(args, scene, cam, kw, dev, world):
     H, W = cam.height, cam.width
     rng = np.random.default_rng(9)
     target_host = torch.as_tensor(rng.uniform(0, 1, size=(3, H, W)).astype(np.float32)).pin_memory()
-    target = torch.empty(3, H, W, device=dev)
+    targets = [torch.empty(3, H, W, device=dev) for _ in range(2)]
     loss_host = torch.empty(1).pin_memory()
     loss = torch.empty(1, device=dev)
     g_rgb = torch.empty(3, H, W, device=dev)
@@ -357,17 +361,37 @@ def run_e2e(args, scene, cam, kw, dev, world):
     h2d = target_host.numel() * target_host.element_size()
     d2h = loss_host.numel() * loss_host.element_size()
     stream = torch.cuda.current_stream()
+    # the next step's target is uploaded on a copy stream while this step
+    # computes (two device buffers); every step still uploads its target
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(b):
+        copy_stream.wait_event(used[b])
+        with torch.cuda.stream(copy_stream):
+            targets[b].copy_(target_host, non_blocking=True)
+        copied[b].record(copy_stream)
+
+    state = {"i": 0}
 
     def step():
-        target.copy_(target_host, non_blocking=True)
+        b = state["i"] & 1
+        state["i"] += 1
+        upload(b ^ 1)                      # the next step's input
+        stream.wait_event(copied[b])
         fr.preprocess()
         fr.bin_sort(sync=False)
         fr.forward(out)
-        l2_loss(out["rgb"], target, g_rgb, loss)
+        l2_loss(out["rgb"], targets[b], g_rgb, loss)
+        used[b].record(stream)
         d_grid.zero_()
         fr.backward(g_rgb, None, None, out, d_grid, d_sh)
         loss_host.copy_(loss, non_blocking=True)
 
+    for b in range(2):
+        used[b].record(stream)
+    upload(0)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -381,7 +405,7 @@ def run_e2e(args, scene, cam, kw, dev, world):
     return {"value": whole_job_rate(world, ms), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "loss": float(loss_host[0]),
             "step": "target image H2D -> render -> MSE loss + gradient -> backward -> loss D2H; "
-                    "voxel parameters resident"}
+                    "voxel parameters resident; the next step's upload overlaps this step's compute"}
 
 
 def run_batched(args, scene, dscene, dev, kw, n_views=16, steps=10):

@@ -623,14 +623,9 @@ def frame_algorithmic_bytes(scene, P, H, W):
 
 def launches_per_step(fr):
     """Kernels of ours launched per step (fills/memsets excluded): tile masks,
-    preprocess, 3 scan kernels, emit, 3 per radix pass, ranges, tile order,
-    block lists, forward, backward, voxel backward."""
-    nt = int(fr.frame.total_tiles)
-    tb = max(0, int(np.ceil(np.log2(nt)))) if nt > 1 else 0
-    lmax = fr.scene.max_level
-    morton = 3 * (lmax + 1 if lmax < 16 else 16)
-    passes = (morton + tb + 7) // 8 + (1 if lmax == 16 else 0)
-    return 2 + 4 + 3 * passes + 3 + 1 + 2
+    preprocess, 3 tile-count scan kernels, work order, emission, chunk sort,
+    run merge, block lists, forward, backward, voxel backward."""
+    return 2 + 3 + 1 + 1 + 2 + 1 + 1 + 2
 
 
 def load_peaks():

@@ -105,65 +105,68 @@ __device__ void radix_tables_clear(RadixTables<THREADS> &tb) {
     for (int i = threadIdx.x; i < (THREADS / 32) * 256; i += THREADS) (&tb.wcnt[0][0])[i] = 0;
 }
 
-// One stable counting pass of the n words src -> dst by the 8-bit digit at
-// bit `shift`: digit histogram (one shared atomic per digit value present in
-// a warp), exclusive scan, then rounds of THREADS words in index order, each
-// word going to its digit's next position plus its rank among the earlier
-// words of the round with the same digit (warp match, per-warp counts).
+// One stable counting pass of n <= 4 * THREADS words src -> dst by the 8-bit
+// digit at bit `shift` (warp-private multisplit).  Warp w ranks its own
+// contiguous 128 words in four rounds of 32 with warp-local digit counters
+// (warp match: a word's rank is the count of its digit in the warp's earlier
+// words), so the ranking needs no CTA barrier; one scan over the (digit,
+// warp) counts in digit-major order then gives every (digit, warp) its first
+// output position, and each word goes there plus its rank.  Words of lower
+// warps and earlier rounds precede, so equal digits keep their order.
 template <int THREADS, class Src, class Dst>
 __device__ void radix_pass(Src src, Dst dst, int n, int shift, RadixTables<THREADS> &tb) {
     constexpr int W = THREADS / 32;
+    static_assert(THREADS == 256, "one counter column per digit and thread");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    if (t < 256) tb.run[t] = 0;
-    __syncthreads();
-    for (int c = 0; c < n; c += THREADS) {
-        const int i = c + t;
-        const uint32_t d = i < n ? (uint32_t)(src(i) >> shift) & 0xFFu : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&tb.run[d], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    uint32_t x = 0, inc = 0;
-    if (t < 256) {
-        x = tb.run[t];
-        inc = x;
+    uint32_t *cnt = tb.wcnt[warp];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) tb.wsum[warp] = inc;
-    }
-    __syncthreads();
-    if (t < 256) {
-        uint32_t wp = 0;
+    for (int k = 0; k < 256 / 32; ++k) cnt[lane + 32 * k] = 0;
+    __syncwarp();
+    uint64_t word[4];
+    uint32_t dig[4], rank[4];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) wp += w < warp ? tb.wsum[w] : 0u;
-        tb.run[t] = wp + inc - x;
-    }
-    __syncthreads();
-    for (int c = 0; c < n; c += THREADS) {
-        const int i = c + t;
+    for (int r = 0; r < 4; ++r) {
+        const int i = 128 * warp + 32 * r + lane;
         const bool valid = i < n;
-        const uint64_t word = valid ? src(i) : 0ull;
-        const uint32_t d = valid ? (uint32_t)(word >> shift) & 0xFFu : 256u;
+        word[r] = valid ? src(i) : 0ull;
+        const uint32_t d = valid ? (uint32_t)(word[r] >> shift) & 0xFFu : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) tb.wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (t < 256) {
-            uint32_t acc = tb.run[t];
+        const uint32_t prior = valid ? cnt[d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[d] = prior + __popc(peers);
+        __syncwarp();
+        dig[r] = d;
+        rank[r] = prior + __popc(peers & lt);
+    }
+    __syncthreads();
+    // thread t = digit t: its total over the warps, exclusive scan over the
+    // digits, then each warp's first position for the digit
+    uint32_t tot = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                tb.wpre[w][t] = acc;
-                acc += tb.wcnt[w][t];
-                tb.wcnt[w][t] = 0;
-            }
-            tb.run[t] = acc;
-        }
-        __syncthreads();
-        if (valid) dst(tb.wpre[warp][d] + rank, word, i);
+    for (int w = 0; w < W; ++w) tot += tb.wcnt[w][t];
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) tb.wsum[warp] = inc;
+    __syncthreads();
+    uint32_t pos = inc - tot;
+#pragma unroll
+    for (int w = 0; w < W; ++w) pos += w < warp ? tb.wsum[w] : 0u;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint32_t c = tb.wcnt[w][t];
+        tb.wpre[w][t] = pos;
+        pos += c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = 128 * warp + 32 * r + lane;
+        if (i < n) dst(tb.wpre[warp][dig[r]] + rank[r], word[r], i);
     }
     __syncthreads();
 }

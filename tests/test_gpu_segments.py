@@ -137,3 +137,18 @@ def test_backward_without_forward_is_flagged():
     fr.forward(out)
     fr.backward(*g, out)
     torch.cuda.synchronize()
+
+
+def test_very_long_lists_sort_and_render():
+    """A dense level-6 grid (262,144 voxels) seen whole by a 32x32 camera:
+    each of the 4 tiles lists 65K-70K pairs, past what the per-tile merge
+    holds in shared memory, so the runs are merged through global memory and
+    the walks span 64+ segments; sorted pairs bit-exact, images vs oracle."""
+    from tests.gpu_common import compare_integers
+    sc = cached("dense6_lowdensity", lambda: synth.dense_scene(6, seed=1, grid_fn=synth.normal_grid(-1.0, 1.0)))
+    cam = synth.look_at((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 40, 32, 32)
+    fr, out, ins = run_gpu(sc, cam, K=2, t_stop=1e-4)
+    lens = np.diff(ins["ranges"].astype(np.int64), axis=1).ravel()
+    assert lens.min() > 8192
+    compare_integers(sc, cam, ins)
+    compare_images(out, oracle.render(sc, cam, K=2, t_stop=1e-4))

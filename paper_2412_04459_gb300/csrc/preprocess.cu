@@ -70,7 +70,7 @@ __device__ __forceinline__ void mark_invalid(Status *st, int64_t v) {
 }
 
 // grid.y = view
-__global__ void __launch_bounds__(256) k_preprocess(FrameDev f) {
+__global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= f.n_vox) return;
     const int view = blockIdx.y;
@@ -366,8 +366,8 @@ cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s) {
 
 cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s) {
     if (f.n_vox == 0) return cudaSuccess;
-    const dim3 grid((unsigned)((f.n_vox + 255) / 256), (unsigned)f.n_views);
-    k_preprocess<<<grid, 256, 0, s>>>(f);
+    const dim3 grid((unsigned)((f.n_vox + 127) / 128), (unsigned)f.n_views);
+    k_preprocess<<<grid, 128, 0, s>>>(f);
     return cudaGetLastError();
 }
 

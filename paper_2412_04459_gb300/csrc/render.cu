@@ -465,14 +465,6 @@ struct FwdSmem {
     uint2 meta[2][kBatch];    // (value, sorted index) of each staged entry
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Lane j starts the copy of its entry's record into buffer buf; every lane
 // commits a group (possibly empty) so that the group counts stay aligned.
 __device__ __forceinline__ void stage_async(FwdSmem &ws, int buf, const ViewData &vd, const Lookahead &la) {

@@ -18,7 +18,7 @@ constexpr int kMaxLevel = 16;
 constexpr int kMaxViews = SVR_MAX_VIEWS;
 constexpr float kNear = 1e-3f;             // corners at camera depth <= kNear are "behind"
 constexpr uint64_t kTripleOnes = 0x249249249249ull;  // bit 0 of each of the 16 triples
-constexpr int kScanTile = 4096;            // entries per block of the count scan
+constexpr int kScanTile = 256;             // entries per block of the count scan
 // Tile lists longer than kSegLen entries are rendered as segments of kSegLen
 // consecutive entries (the last one shorter), each by its own warps, and
 // merged afterwards; kSegFields floats per pixel and segment carry the
@@ -70,6 +70,16 @@ struct Status {
 //   r1 = corner densities 0..3     (raw, gathered from the grid)
 //   r2 = corner densities 4..7
 //   r3 = colour rgb, bit c of the w word set if channel c was > 0 before the clamp
+// Asynchronous 16-byte global -> shared copy (cp.async, L2 only), its
+// commit and the wait for all but the N most recent groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 struct Record {
     float4 r0, r1, r2, r3;
 };

@@ -61,7 +61,7 @@ Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles, int 
     };
     const size_t N = (size_t)n_vox, VN = (size_t)n_vox * (size_t)n_views, C = (size_t)cap;
     take(kStatus, sizeof(svr::Status));
-    take(kTileMask, (size_t)ntiles);
+    take(kTileMask, (size_t)ntiles * (1 + (size_t)tile * tile / 32));  // tile masks, block sign masks
     take(kOctpath, 8 * N);
     take(kRect, 8 * VN);
     take(kCount, 4 * VN);
@@ -161,6 +161,7 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     const uint64_t *o = f->offsets;
     d.status = (svr::Status *)(ws + o[kStatus]);
     d.tile_mask = (uint8_t *)(ws + o[kTileMask]);
+    d.block_sign = d.tile_mask + f->total_tiles;
     d.octpath = (uint64_t *)(ws + o[kOctpath]);
     d.rect = (short4 *)(ws + o[kRect]);
     d.count = (uint32_t *)(ws + o[kCount]);

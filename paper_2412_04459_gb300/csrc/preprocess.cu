@@ -1,6 +1,7 @@
 // Per-view preprocessing, count scan and pair emission (sm_103a).
 //
-//   k_tile_mask   per tile: OR of 1 << signbits(r_d) over its in-image pixels
+//   k_tile_mask   per 8x4 pixel block and per tile: OR of 1 << signbits(r_d)
+//                 over the in-image pixels
 //                 (ray sign bits of Sec. B.2; duplication per sign pattern,
 //                 Sec. B.1)
 //   k_preprocess  per (view, voxel): lattice index, Morton code (Sec. A.1),
@@ -29,25 +30,29 @@ namespace svr {
 
 // --------------------------------------------------------------- tile masks
 
+// One warp per 8x4 pixel block (the render's warp blocks, tile / 8 per block
+// row): the block's sign-bit mask goes to block_sign, their OR to tile_mask.
 __global__ void k_tile_mask(FrameDev f) {
     const int g = blockIdx.x;
     const DevCam &cam = f.views[view_of_tile(f, g)];
     const int tile = g - cam.tile_base;
-    const int tx = tile % cam.ntx, ty = tile / cam.ntx;
+    const int T = cam.tile, bpr = T >> 3, B = f.blocks_per_tile;
+    const int x0 = (tile % cam.ntx) * T, y0 = (tile / cam.ntx) * T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     unsigned m = 0;
-    const int npx = cam.tile * cam.tile;
-    for (int p = threadIdx.x; p < npx; p += blockDim.x) {
-        int x = tx * cam.tile + p % cam.tile;
-        int y = ty * cam.tile + p / cam.tile;
-        if (x < cam.W && y < cam.H) m |= 1u << sign_bits(pixel_dir(cam, x, y));
+    for (int b = warp; b < B; b += nw) {
+        const int x = x0 + (b % bpr) * 8 + (lane & 7), y = y0 + (b / bpr) * 4 + (lane >> 3);
+        const unsigned bit = (x < cam.W && y < cam.H) ? 1u << sign_bits(pixel_dir(cam, x, y)) : 0u;
+        const unsigned bm = __reduce_or_sync(0xffffffffu, bit);
+        if (lane == 0) f.block_sign[(size_t)g * B + b] = (uint8_t)bm;
+        m |= bm;
     }
-    m = __reduce_or_sync(0xffffffffu, m);
     __shared__ unsigned wm[32];
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    if (lane == 0) wm[warp] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned r = 0;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) r |= wm[w];
+        for (int w = 0; w < nw; ++w) r |= wm[w];
         f.tile_mask[g] = (uint8_t)r;
     }
 }
@@ -321,6 +326,8 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ 
 
 // --------------------------------------------------------------------- emit
 
+constexpr int kEmitBatch = 8;
+
 // grid.y = view
 __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -335,12 +342,30 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
     const int drop = 48 - f.key_shift;
     uint64_t *keys = f.keys[0];
     uint32_t *vals = f.vals[0];
-    for (int ty = rc.z; ty <= rc.w; ++ty) {
-        for (int tx = rc.x; tx <= rc.y; ++tx) {
-            const int g = cam.tile_base + ty * cam.ntx + tx;
-            unsigned m = f.tile_mask[g];
-            if (!m) continue;
-            uint32_t o = atomicAdd(f.cursor + (size_t)(v & (kTileSub - 1)) * f.total_tiles + g, (uint32_t)__popc(m));
+    uint32_t *cur = f.cursor + (size_t)(v & (kTileSub - 1)) * f.total_tiles;
+    // the rectangle's tiles in row-major batches of kEmitBatch: a batch's
+    // cursor atomics are issued together, so a voxel over many tiles waits
+    // for one atomic round trip per batch rather than per tile
+    int tx = rc.x, ty = rc.z;
+    while (ty <= rc.w) {
+        int gb[kEmitBatch];
+        unsigned mb[kEmitBatch];
+#pragma unroll
+        for (int i = 0; i < kEmitBatch; ++i) {
+            gb[i] = cam.tile_base + ty * cam.ntx + tx;
+            mb[i] = ty <= rc.w ? (unsigned)f.tile_mask[gb[i]] : 0u;
+            if (++tx > rc.y) {
+                tx = rc.x;
+                ++ty;
+            }
+        }
+        uint32_t ob[kEmitBatch];
+#pragma unroll
+        for (int i = 0; i < kEmitBatch; ++i) ob[i] = mb[i] ? atomicAdd(cur + gb[i], (uint32_t)__popc(mb[i])) : 0u;
+#pragma unroll
+        for (int i = 0; i < kEmitBatch; ++i) {
+            unsigned m = mb[i];
+            uint32_t o = ob[i];
             if ((int64_t)o + __popc(m) > f.capacity) {  // counts and emission disagree: never expected
                 atomicOr(&f.status->flags, SVR_FLAG_CAPACITY);
                 return;
@@ -348,7 +373,7 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
             while (m) {
                 const unsigned s = __ffs(m) - 1;
                 m &= m - 1;
-                keys[o] = ((uint64_t)g << f.key_shift) | ((code ^ ((uint64_t)s * kTripleOnes)) >> drop);
+                keys[o] = ((uint64_t)gb[i] << f.key_shift) | ((code ^ ((uint64_t)s * kTripleOnes)) >> drop);
                 vals[o] = (s << 29) | (uint32_t)v;
                 ++o;
             }
@@ -359,7 +384,7 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s) {
-    const int threads = f.views[0].tile * f.views[0].tile >= 256 ? 256 : 64;
+    const int threads = 32 * (f.blocks_per_tile < 8 ? f.blocks_per_tile : 8);
     k_tile_mask<<<f.total_tiles, threads, 0, s>>>(f);
     return cudaGetLastError();
 }

@@ -188,22 +188,24 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 // whose pixel box meets the block and whose sign pattern a pixel of the block
 // has.  k_block_lists extracts them once per frame, one CTA per entry of the
 // render work order (a tile, or one kSegLen-entry segment of a split tile):
-// it loads the segment's list entries (value and box, four independent loads
-// per thread) into shared memory, then warp w keeps the entries of blocks w,
-// w + 8, ... by ballot, which preserves list order, and writes (value, sorted
-// index) pairs.  Block b of a tile whose list is [beg, end) owns the region
-// B beg + b (end - beg) of the block lists, so the lists need no allocation
-// scan; segment s of a split tile writes from offset s kSegLen of that region
-// (it keeps at most kSegLen entries) and records its count per block.  The
-// CTA of segment 0 also clears the tile's merge counters for the next
-// forward.
+// thread t loads entries t, t + 256, ... of the segment (value and box) and
+// writes each one's mask of such blocks to shared memory (the box's block
+// rectangle AND the blocks holding a pixel with its sign bits, from the
+// per-block sign masks of k_tile_mask); then warp w keeps the entries of
+// blocks w, w + 8, ... by ballot, which preserves list order, and writes
+// (value, sorted index) pairs.  Block b of a tile whose list is [beg, end)
+// owns the region B beg + b (end - beg) of the block lists, so the lists need
+// no allocation scan; segment s of a split tile writes from offset s kSegLen
+// of that region (it keeps at most kSegLen entries) and records its count per
+// block.  The CTA of segment 0 also clears the tile's merge counters for the
+// next forward.
 
 constexpr int kMaxBlocksPerWarp = 4;  // tile 32: 32 blocks over 8 warps
 constexpr int kListChunk = kSegLen;
 
-__global__ void __launch_bounds__(256, 4) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
+__global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
     __shared__ uint32_t sval[kListChunk];
-    __shared__ ushort4 sbox[kListChunk];
+    __shared__ uint32_t smsk[kListChunk];
     if (blockIdx.x >= f.status->n_queue) return;
     const uint2 gs = f.order[blockIdx.x];
     const int g = (int)gs.x, sg = (int)gs.y;
@@ -219,27 +221,23 @@ __global__ void __launch_bounds__(256, 4) k_block_lists(FrameDev f, const uint32
     const uint2 ts = f.tile_seg[g];
     const bool split = ts.x > 1;
     if (sg == 0 && threadIdx.x < B) f.merge_cnt[(size_t)g * B + threadIdx.x] = 0;
-    int bid[kMaxBlocksPerWarp], bx0[kMaxBlocksPerWarp], by0[kMaxBlocksPerWarp];
-    unsigned bmask[kMaxBlocksPerWarp], cnt[kMaxBlocksPerWarp];
+    // lane s < 8: mask of the tile's blocks with an in-image pixel of sign bits s
+    const unsigned bsign = lane < B ? f.block_sign[(size_t)g * B + lane] : 0u;
+    unsigned sblk = 0;
 #pragma unroll
-    for (int k = 0; k < kMaxBlocksPerWarp; ++k) {
-        const int b = warp + 8 * k;
-        bid[k] = b;
-        cnt[k] = 0;
-        bmask[k] = 0;
-        bx0[k] = by0[k] = 0;
-        if (b < B) {
-            WarpBlock wb;
-            pixel_ray(cam, tile, b, wb);
-            bx0[k] = wb.x0;
-            by0[k] = wb.y0;
-            bmask[k] = wb.smask;
-        }
+    for (int t = 0; t < 8; ++t) {
+        const unsigned m = __ballot_sync(0xffffffffu, (bsign >> t) & 1u);
+        if (lane == t) sblk = m;
     }
+    const int T = cam.tile, bpr = T >> 3;
+    const int tx0 = (tile % cam.ntx) * T, ty0 = (tile / cam.ntx) * T;
+    // bit r bpr for each block row r: replicates a row's column bits over the rows
+    const unsigned rep = bpr == 1 ? 0x3u : (bpr == 2 ? 0x55u : 0x11111111u);
     // a split tile's segment is one chunk; an unsplit list is walked whole
     const int first = beg + sg * kListChunk;
     const int stop = split ? min(end, first + kListChunk) : end;
     uint2 *out = f.blist + (size_t)B * beg + (split ? (size_t)sg * kListChunk : 0);
+    unsigned cnt[kMaxBlocksPerWarp] = {0u, 0u, 0u, 0u};
     for (int c0 = first; c0 < stop; c0 += kListChunk) {
         const int n = min(kListChunk, stop - c0);
         uint32_t v4[kListChunk / 256];
@@ -251,27 +249,34 @@ __global__ void __launch_bounds__(256, 4) k_block_lists(FrameDev f, const uint32
 #pragma unroll
         for (int r = 0; r < kListChunk / 256; ++r) {
             const int t = threadIdx.x + 256 * r;
+            unsigned m = 0;
+            if (t < n) {
+                const ushort4 bx = __ldg(boxes + (v4[r] & 0x1FFFFFFFu));
+                const int cx0 = max((int)bx.x - tx0, 0), cx1 = min((int)bx.y - tx0, T - 1);
+                const int cy0 = max((int)bx.z - ty0, 0), cy1 = min((int)bx.w - ty0, T - 1);
+                if (cx0 <= cx1 && cy0 <= cy1) {
+                    const unsigned cols = (2u << (cx1 >> 3)) - (1u << (cx0 >> 3));
+                    const uint64_t rows = ((1ull << (((cy1 >> 2) + 1) * bpr)) - 1ull) &
+                                          ~((1ull << ((cy0 >> 2) * bpr)) - 1ull);
+                    m = cols * rep & (unsigned)rows;
+                }
+            }
+            m &= __shfl_sync(0xffffffffu, sblk, (int)(v4[r] >> 29));
             if (t < n) {
                 sval[t] = v4[r];
-                sbox[t] = __ldg(boxes + (v4[r] & 0x1FFFFFFFu));
+                smsk[t] = m;
             }
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kMaxBlocksPerWarp; ++k) {
-            if (bid[k] >= B) continue;
+            const int b = warp + 8 * k;
+            if (b >= B) continue;
             for (int sub = 0; sub < n; sub += 32) {
                 const int j = sub + lane;
-                bool keep = false;
-                uint32_t v = 0;
-                if (j < n) {
-                    v = sval[j];
-                    const ushort4 bx = sbox[j];
-                    keep = ((bmask[k] >> (v >> 29)) & 1u) && bx.x <= bx0[k] + 7 && bx.y >= bx0[k] &&
-                           bx.z <= by0[k] + 3 && bx.w >= by0[k];
-                }
+                const bool keep = j < n && ((smsk[j] >> b) & 1u);
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (keep) out[(size_t)bid[k] * L + cnt[k] + __popc(bal & lt)] = make_uint2(v, (unsigned)(c0 + j));
+                if (keep) out[(size_t)b * L + cnt[k] + __popc(bal & lt)] = make_uint2(sval[j], (unsigned)(c0 + j));
                 cnt[k] += __popc(bal);
             }
         }
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(256, 4) k_block_lists(FrameDev f, const uint32
         uint32_t *len = split ? f.seg_len + (size_t)(ts.y + sg) * B : f.blen + (size_t)g * B;
 #pragma unroll
         for (int k = 0; k < kMaxBlocksPerWarp; ++k)
-            if (bid[k] < B) len[bid[k]] = cnt[k];
+            if (warp + 8 * k < B) len[warp + 8 * k] = cnt[k];
     }
 }
 

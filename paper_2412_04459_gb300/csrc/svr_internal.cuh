@@ -141,6 +141,7 @@ struct FrameDev {
     int key_shift;           // Morton bits kept in the key; the tile id sits above them
     Status *status;
     uint8_t *tile_mask;      // [total_tiles]
+    uint8_t *block_sign;     // [total_tiles][B]: sign-bit mask of each 8x4 block's in-image pixels
     uint64_t *octpath;       // [N]
     short4 *rect;            // [V * N] tile rectangle tx0, tx1, ty0, ty1
     uint32_t *count;         // [V * N] pairs of each (view, voxel)

@@ -327,6 +327,9 @@ def run_native(args, rank, world, local_rank):
         "frame_hbm": {"algorithmic_bytes": frame_bytes, "achieved_gbs": frame_bytes / (ms_step * 1e-3) / 1e9,
                       "peak_gbs": hbm, "frac": frame_bytes / (ms_step * 1e-3) / 1e9 / hbm,
                       "peak_from": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"},
+        # the whole step against the larger of its two algorithmic times:
+        # minimal HBM bytes at the measured copy bandwidth, render FP32 work at the ALU peak
+        "frame_roofline": frame_roofline(frame_bytes, hbm, ops + ops_bwd, alu_peak, ms_step),
         "gpu_launches": n_launch * args.steps,
         "clocks": clocks,
         "e2e": e2e,
@@ -334,6 +337,14 @@ def run_native(args, rank, world, local_rank):
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(args, scene, cam, kw)
     print(json.dumps(line), flush=True)
+
+
+def frame_roofline(frame_bytes, hbm_gbs, lane_ops, alu_peak_t, ms_step):
+    """max(bytes / bandwidth, FP32 lane-ops / ALU peak) over the measured step time."""
+    ms_bytes = frame_bytes / (hbm_gbs * 1e9) * 1e3
+    ms_ops = lane_ops / (alu_peak_t * 1e12) * 1e3
+    return {"ms_bytes": ms_bytes, "ms_ops": ms_ops, "bound": "alu" if ms_ops >= ms_bytes else "hbm",
+            "frac": max(ms_bytes, ms_ops) / ms_step}
 
 
 def run_e2e(args, scene, cam, kw, dev, world):

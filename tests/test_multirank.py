@@ -57,6 +57,17 @@ def test_single_rank_is_identity():
     assert bench.whole_job_rate(1, 2.0) == 500.0
 
 
+def test_frame_roofline_takes_the_larger_time():
+    sys.path.insert(0, ROOT)
+    import bench
+    # 6.8 GB at 6800 GB/s = 1 ms; 20 T lane-ops at 40 T/s = 0.5 s
+    r = bench.frame_roofline(6.8e9, 6800.0, 20e12, 40.0, 1000.0)
+    assert abs(r["ms_bytes"] - 1.0) < 1e-12 and abs(r["ms_ops"] - 500.0) < 1e-9
+    assert r["bound"] == "alu" and abs(r["frac"] - 0.5) < 1e-12
+    r = bench.frame_roofline(6.8e9, 6800.0, 0.0, 40.0, 4.0)
+    assert r["bound"] == "hbm" and abs(r["frac"] - 0.25) < 1e-12
+
+
 def test_reference_arm_silent_on_other_ranks():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",

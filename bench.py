@@ -634,9 +634,9 @@ def frame_algorithmic_bytes(scene, P, H, W):
 
 def launches_per_step(fr):
     """Kernels of ours launched per step (fills/memsets excluded): tile masks,
-    preprocess, 3 tile-count scan kernels, work order, emission, chunk sort,
+    preprocess, 2 tile-count scan kernels, work order, emission, chunk sort,
     run merge, block lists, forward, backward, voxel backward."""
-    return 2 + 3 + 1 + 1 + 2 + 1 + 1 + 2
+    return 2 + 2 + 1 + 1 + 2 + 1 + 1 + 2
 
 
 def load_peaks():

@@ -9,7 +9,8 @@
 //                 count, conservative pixel box, view-dependent colour
 //                 (Eq. vox_color), gathered densities
 //                 and, per tile, the pairs it will hold (atomics)
-//   k_scan_*      exclusive scan of the tiles' pair counts (three phases;
+//   k_scan_*      exclusive scan of the tiles' pair counts (block sums, then
+//                 each block scans its part after summing the earlier blocks;
 //                 kTileSub sub-buckets per tile, adjacent): each sub-bucket's
 //                 start, each tile's end, the total, the capacity check
 //   k_emit        writes each (voxel, tile, sign pattern s) pair into its
@@ -30,31 +31,28 @@ namespace svr {
 
 // --------------------------------------------------------------- tile masks
 
-// One warp per 8x4 pixel block (the render's warp blocks, tile / 8 per block
-// row): the block's sign-bit mask goes to block_sign, their OR to tile_mask.
-__global__ void k_tile_mask(FrameDev f) {
-    const int g = blockIdx.x;
+// One warp per tile, looping over its 8x4 pixel blocks (the render's warp
+// blocks, tile / 8 per block row): each block's sign-bit mask goes to
+// block_sign, their OR to tile_mask.
+constexpr int kMaskWarps = 8;
+
+__global__ void __launch_bounds__(32 * kMaskWarps) k_tile_mask(FrameDev f) {
+    const int g = blockIdx.x * kMaskWarps + (threadIdx.x >> 5);
+    if (g >= f.total_tiles) return;
     const DevCam &cam = f.views[view_of_tile(f, g)];
     const int tile = g - cam.tile_base;
     const int T = cam.tile, bpr = T >> 3, B = f.blocks_per_tile;
     const int x0 = (tile % cam.ntx) * T, y0 = (tile / cam.ntx) * T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
     unsigned m = 0;
-    for (int b = warp; b < B; b += nw) {
+    for (int b = 0; b < B; ++b) {
         const int x = x0 + (b % bpr) * 8 + (lane & 7), y = y0 + (b / bpr) * 4 + (lane >> 3);
         const unsigned bit = (x < cam.W && y < cam.H) ? 1u << sign_bits(pixel_dir(cam, x, y)) : 0u;
         const unsigned bm = __reduce_or_sync(0xffffffffu, bit);
-        if (lane == 0) f.block_sign[(size_t)g * B + b] = (uint8_t)bm;
+        if (lane == b) f.block_sign[(size_t)g * B + b] = (uint8_t)bm;
         m |= bm;
     }
-    __shared__ unsigned wm[32];
-    if (lane == 0) wm[warp] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned r = 0;
-        for (int w = 0; w < nw; ++w) r |= wm[w];
-        f.tile_mask[g] = (uint8_t)r;
-    }
+    if (lane == 0) f.tile_mask[g] = (uint8_t)m;
 }
 
 // --------------------------------------------------------------- preprocess
@@ -266,61 +264,47 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict_
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ block_sums, int nb,
-                                                   Status *st, int64_t capacity) {
-    __shared__ unsigned long long carry;
-    __shared__ unsigned long long wsum[32];
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < nb; base += 1024) {
-        const int i = base + threadIdx.x;
-        unsigned long long x = i < nb ? block_sums[i] : 0ull;
-        unsigned long long inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        unsigned long long wpre = 0, tot = 0;
-        for (int w = 0; w < 32; ++w) {
-            wpre += (w < warp) ? wsum[w] : 0ull;
-            tot += wsum[w];
-        }
-        const unsigned long long excl = carry + wpre + inc - x;
-        if (i < nb) block_sums[i] = (uint32_t)tmin<unsigned long long>(excl, 0xFFFFFFFFull);
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        st->n_pairs_lo = (unsigned)(carry & 0xFFFFFFFFull);
-        st->n_pairs_hi = (unsigned)(carry >> 32);
-        if (carry > (unsigned long long)capacity) atomicOr(&st->flags, SVR_FLAG_CAPACITY);
-    }
-}
-
-// Sub-bucket starts (the emission cursors) and tile ends from the scanned
-// counts; k_tile_order turns them into the tiles' ranges.
+// Sub-bucket starts (the emission cursors) and tile ends from the counts;
+// k_tile_order turns them into the tiles' ranges.  Each CTA first sums the
+// block sums of all earlier CTAs (64-bit), so no separate top-level scan is
+// launched; the last CTA records the total and checks it against the
+// capacity.  A start beyond 2^32 saturates; the capacity flag covers it.
 __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ count, int64_t ntiles,
-                                                   const uint32_t *__restrict__ block_off,
-                                                   uint32_t *__restrict__ cursor, uint32_t *__restrict__ tile_end) {
+                                                   const uint32_t *__restrict__ block_sums, int nb,
+                                                   uint32_t *__restrict__ cursor, uint32_t *__restrict__ tile_end,
+                                                   Status *st, int64_t capacity) {
     __shared__ uint32_t ws[8];
+    __shared__ unsigned long long wpre[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long pre = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += 256) pre += block_sums[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    if (lane == 0) wpre[warp] = pre;
+    __syncthreads();
+    pre = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) pre += wpre[w];
     const int64_t n = ntiles * kTileSub;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    uint32_t carry = block_off[blockIdx.x];
+    unsigned long long carry = pre;
     for (int r = 0; r < kScanTile / 256; ++r) {
         const int64_t i = base + r * 256 + threadIdx.x;
         const uint32_t x = i < n ? count[sub_index(i, ntiles)] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(x, ws, tot);
         if (i < n) {
-            cursor[sub_index(i, ntiles)] = carry + ex;
-            if (i % kTileSub == kTileSub - 1) tile_end[i / kTileSub] = carry + ex + x;
+            const uint32_t c = (uint32_t)tmin<unsigned long long>(carry + ex, 0xFFFFFFFFull);
+            cursor[sub_index(i, ntiles)] = c;
+            if (i % kTileSub == kTileSub - 1)
+                tile_end[i / kTileSub] = (uint32_t)tmin<unsigned long long>(carry + ex + x, 0xFFFFFFFFull);
         }
         carry += tot;
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) {
+        st->n_pairs_lo = (unsigned)(carry & 0xFFFFFFFFull);
+        st->n_pairs_hi = (unsigned)(carry >> 32);
+        if (carry > (unsigned long long)capacity) atomicOr(&st->flags, SVR_FLAG_CAPACITY);
     }
 }
 
@@ -384,8 +368,7 @@ __global__ void __launch_bounds__(256) k_emit(FrameDev f) {
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s) {
-    const int threads = 32 * (f.blocks_per_tile < 8 ? f.blocks_per_tile : 8);
-    k_tile_mask<<<f.total_tiles, threads, 0, s>>>(f);
+    k_tile_mask<<<(unsigned)((f.total_tiles + kMaskWarps - 1) / kMaskWarps), 32 * kMaskWarps, 0, s>>>(f);
     return cudaGetLastError();
 }
 
@@ -400,8 +383,7 @@ cudaError_t launch_scan(const FrameDev &f, cudaStream_t s) {
     const int64_t T = f.total_tiles;
     const int nb = (int)((T * kTileSub + kScanTile - 1) / kScanTile);
     k_scan_reduce<<<nb, 256, 0, s>>>(f.tile_cnt, T, f.scan_blocks);
-    k_scan_top<<<1, 1024, 0, s>>>(f.scan_blocks, nb, f.status, f.capacity);
-    k_scan_down<<<nb, 256, 0, s>>>(f.tile_cnt, T, f.scan_blocks, f.cursor, f.tile_end);
+    k_scan_down<<<nb, 256, 0, s>>>(f.tile_cnt, T, f.scan_blocks, nb, f.cursor, f.tile_end, f.status, f.capacity);
     return cudaGetLastError();
 }
 

@@ -35,33 +35,45 @@ __device__ __forceinline__ int order_bucket(unsigned len, unsigned nseg) {
     return len ? 32 - __clz(len) + (nseg > 1 ? 1 : 0) : 0;
 }
 
+constexpr int kOrderUnroll = 8;  // tiles per thread whose loads are issued together
+
 __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
     __shared__ unsigned cnt[34];
     __shared__ unsigned start[34];
     __shared__ unsigned slot_next;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, nt = blockDim.x;
     const int ntiles = f.total_tiles;
-    // ranges: a tile starts at its first sub-bucket; empty tiles, and all
-    // tiles when the pairs exceed the capacity, get (0, 0)
     const bool over = (f.status->flags & SVR_FLAG_CAPACITY) != 0;
-    for (int i = t; i < ntiles; i += blockDim.x) {
-        const uint32_t b = f.cursor[i], e = f.tile_end[i];
-        f.ranges[i] = over || e == b ? make_uint2(0u, 0u) : make_uint2(b, e);
-    }
     if (t < 34) cnt[t] = 0;
     if (t == 0) slot_next = 0;
     __syncthreads();
-    for (int i = t; i < ntiles; i += blockDim.x) {
-        const uint2 r = f.ranges[i];
-        const unsigned len = r.y - r.x;
-        unsigned nseg = len > (unsigned)kSegLen ? (len + kSegLen - 1) / kSegLen : 1u;
-        unsigned base = 0;
-        if (nseg > 1) {
-            base = atomicAdd(&slot_next, nseg);
-            if ((int64_t)base + nseg > f.seg_slots) nseg = 1, base = 0;  // only past the pair capacity
+    // ranges: a tile starts at its first sub-bucket; empty tiles, and all
+    // tiles when the pairs exceed the capacity, get (0, 0); then each tile's
+    // segments and its group's count
+    for (int i0 = t; i0 < ntiles; i0 += nt * kOrderUnroll) {
+        uint32_t b[kOrderUnroll], e[kOrderUnroll];
+#pragma unroll
+        for (int u = 0; u < kOrderUnroll; ++u) {
+            const int i = i0 + u * nt;
+            b[u] = i < ntiles ? f.cursor[i] : 0u;
+            e[u] = i < ntiles ? f.tile_end[i] : 0u;
         }
-        atomicAdd(&cnt[order_bucket(len, nseg)], nseg);
-        f.tile_seg[i] = make_uint2(nseg, base);
+#pragma unroll
+        for (int u = 0; u < kOrderUnroll; ++u) {
+            const int i = i0 + u * nt;
+            if (i >= ntiles) break;
+            const uint2 r = over || e[u] == b[u] ? make_uint2(0u, 0u) : make_uint2(b[u], e[u]);
+            f.ranges[i] = r;
+            const unsigned len = r.y - r.x;
+            unsigned nseg = len > (unsigned)kSegLen ? (len + kSegLen - 1) / kSegLen : 1u;
+            unsigned base = 0;
+            if (nseg > 1) {
+                base = atomicAdd(&slot_next, nseg);
+                if ((int64_t)base + nseg > f.seg_slots) nseg = 1, base = 0;  // only past the pair capacity
+            }
+            atomicAdd(&cnt[order_bucket(len, nseg)], nseg);
+            f.tile_seg[i] = make_uint2(nseg, base);
+        }
     }
     __syncthreads();
     if (t == 0) {
@@ -76,12 +88,22 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
         f.status->sort_next = 0;
     }
     __syncthreads();
-    for (int i = t; i < ntiles; i += blockDim.x) {
-        const uint2 r = f.ranges[i];
-        const uint2 ts = f.tile_seg[i];
-        const unsigned len = r.y - r.x;
-        const unsigned pos = atomicAdd(&start[order_bucket(len, ts.x)], ts.x);
-        for (unsigned sg = 0; sg < ts.x; ++sg) f.order[pos + sg] = make_uint2((unsigned)i, sg);
+    // each thread reads back its own tiles' ranges and segments
+    for (int i0 = t; i0 < ntiles; i0 += nt * kOrderUnroll) {
+        uint2 r[kOrderUnroll], ts[kOrderUnroll];
+#pragma unroll
+        for (int u = 0; u < kOrderUnroll; ++u) {
+            const int i = i0 + u * nt;
+            r[u] = i < ntiles ? f.ranges[i] : make_uint2(0u, 0u);
+            ts[u] = i < ntiles ? f.tile_seg[i] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kOrderUnroll; ++u) {
+            const int i = i0 + u * nt;
+            if (i >= ntiles) break;
+            const unsigned pos = atomicAdd(&start[order_bucket(r[u].y - r[u].x, ts[u].x)], ts[u].x);
+            for (unsigned sg = 0; sg < ts[u].x; ++sg) f.order[pos + sg] = make_uint2((unsigned)i, sg);
+        }
     }
 }
 

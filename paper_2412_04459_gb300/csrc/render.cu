@@ -69,7 +69,7 @@ struct Entry {
     float4 g0;   // raw corner densities 0..3
     float4 g1;   // raw corner densities 4..7
     float4 col;  // colour, voxel id (int)
-    float4 pad;
+    float4 pad;  // x: clamp bits of the colour channels (uint); y, z, w unused
 };
 
 __device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, const Record *__restrict__ rec) {
@@ -87,6 +87,7 @@ __device__ __forceinline__ void stage_entry(Entry &e, uint32_t val, int idx, con
     e.g1 = __ldg(&r->r2);
     const float4 c3 = __ldg(&r->r3);
     e.col = make_float4(c3.x, c3.y, c3.z, __int_as_float((int)vid));
+    e.pad.x = c3.w;
 }
 
 // Trilinear interpolation of Eq. interp; corner bits (x, y, z), x most significant.
@@ -917,9 +918,11 @@ __device__ __forceinline__ int rec_run_end(int k_lo, int end, int base) {
     return 32 - __clz(fit);
 }
 
-// Adds an entry's summed record to the global gradients of voxel vid.
-__device__ __forceinline__ void add_row(const float row[kRecStride], int vid, const int32_t *__restrict__ corner_idx,
-                                        float *__restrict__ d_grid, float *__restrict__ acc_col) {
+// Adds an entry's summed record to the global gradients of voxel vid; a
+// colour channel that the clamp cut (bit clear) has no gradient.
+__device__ __forceinline__ void add_row(const float row[kRecStride], int vid, unsigned bits,
+                                        const int32_t *__restrict__ corner_idx, float *__restrict__ d_grid,
+                                        float *__restrict__ acc_col) {
     const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
     const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
     atomicAdd(d_grid + i0.x, row[0]);
@@ -930,9 +933,9 @@ __device__ __forceinline__ void add_row(const float row[kRecStride], int vid, co
     atomicAdd(d_grid + i1.y, row[5]);
     atomicAdd(d_grid + i1.z, row[6]);
     atomicAdd(d_grid + i1.w, row[7]);
-    atomicAdd(acc_col + 3 * (size_t)vid + 0, row[8]);
-    atomicAdd(acc_col + 3 * (size_t)vid + 1, row[9]);
-    atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
+    if (bits & 1u) atomicAdd(acc_col + 3 * (size_t)vid + 0, row[8]);
+    if (bits & 2u) atomicAdd(acc_col + 3 * (size_t)vid + 1, row[9]);
+    if (bits & 4u) atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
 }
 
 // Lane j in [k_lo, k_hi) sums entry j's records and adds the sums to the
@@ -947,7 +950,7 @@ __device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, in
 #pragma unroll
         for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
         for (int r = off - base; r < end - base; ++r) rec_add(row, rs.rec + r * (kRecStride / 4));
-        add_row(row, __float_as_int(st[lane].col.w), corner_idx, d_grid, acc_col);
+        add_row(row, __float_as_int(st[lane].col.w), __float_as_uint(st[lane].pad.x), corner_idx, d_grid, acc_col);
     }
     __syncwarp();
 }
@@ -1167,28 +1170,27 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(Frame
 }
 
 // Per voxel: dL/dsh[n][c] = sum over views of Y_n(d_v) * dL/dc_{v,c}, over
-// the views where the voxel is in view and channel c was > 0 before the
-// clamp (Eq. vox_color); zero for a voxel in no view.  Each thread builds its
-// voxel's 48 values in shared memory; the block then writes its rows with
-// consecutive threads on consecutive words.
+// the views where the voxel is in view (dL/dc_{v,c} holds only the channels
+// that were > 0 before the clamp, Eq. vox_color); zero for a voxel in no view.  Each thread sums its
+// voxel's 48 values in registers and stores them to a shared row (rows 52
+// floats apart: float4 stores of a quarter warp fall in distinct banks); the
+// block then writes its rows as consecutive float4s.
 constexpr int kVoxBwdThreads = 128;
+constexpr int kShRow = 52;
 
 __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float *__restrict__ d_sh) {
-    __shared__ float rows[kVoxBwdThreads][49];
+    __shared__ __align__(16) float rows[kVoxBwdThreads * kShRow];
     const int64_t v0 = (int64_t)blockIdx.x * kVoxBwdThreads;
     const int64_t v = v0 + threadIdx.x;
     if (v < f.n_vox) {
-        float *o = rows[threadIdx.x];
+        float o[48];
 #pragma unroll
         for (int i = 0; i < 48; ++i) o[i] = 0.f;
         for (int view = 0; view < f.n_views; ++view) {
             const int64_t iv = (int64_t)view * f.n_vox + v;
             if (f.count[iv] == 0) continue;
             const DevCam &cam = f.views[view];
-            const unsigned bits = __float_as_uint(f.rec[iv].r3.w);
-            const float g0 = (bits & 1u) ? f.dcol[3 * iv + 0] : 0.f;
-            const float g1 = (bits & 2u) ? f.dcol[3 * iv + 1] : 0.f;
-            const float g2 = (bits & 4u) ? f.dcol[3 * iv + 2] : 0.f;
+            const float g0 = f.dcol[3 * iv + 0], g1 = f.dcol[3 * iv + 1], g2 = f.dcol[3 * iv + 2];
             float dx = f.centre[3 * v + 0] - cam.ro[0];
             float dy = f.centre[3 * v + 1] - cam.ro[1];
             float dz = f.centre[3 * v + 2] - cam.ro[2];
@@ -1202,11 +1204,18 @@ __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float 
                 o[3 * n + 2] = fmaf(Y[n], g2, o[3 * n + 2]);
             }
         }
+        float4 *row = reinterpret_cast<float4 *>(rows + threadIdx.x * kShRow);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) row[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
     }
     __syncthreads();
     const int nv = (int)tmin<int64_t>(kVoxBwdThreads, f.n_vox - v0);
-    float *out = d_sh + 48 * v0;
-    for (int i = threadIdx.x; i < nv * 48; i += kVoxBwdThreads) out[i] = rows[i / 48][i % 48];
+    float4 *out = reinterpret_cast<float4 *>(d_sh + 48 * v0);
+    const float4 *src = reinterpret_cast<const float4 *>(rows);
+    for (int i = threadIdx.x; i < nv * 12; i += kVoxBwdThreads) {
+        const int r = i / 12;
+        out[i] = src[r * (kShRow / 4) + (i - 12 * r)];
+    }
 }
 
 // ---------------------------------------------------------------- launchers

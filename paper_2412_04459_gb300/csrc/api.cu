@@ -386,7 +386,7 @@ SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, flo
     if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
     if (!rgb || !depth || !alpha || !T_final || !last) return fail(SVR_ERR_INVALID, "null output");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_fwd(d, frame->sorted_alt, rgb, depth, alpha, T_final, last, nullptr,
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_fwd");
     return SVR_OK;
@@ -399,7 +399,7 @@ SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, f
     if (!rgb || !depth || !alpha || !T_final || !last || !counts) return fail(SVR_ERR_INVALID, "null output");
     if (((uintptr_t)counts) & 7u) return fail(SVR_ERR_INVALID, "counts not 8-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_fwd(d, frame->sorted_alt, rgb, depth, alpha, T_final, last, (int2 *)counts,
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, (int2 *)counts,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_stats");
     return SVR_OK;
@@ -414,7 +414,7 @@ SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const flo
     if (frame->scene.n_vox > 0 && (!d_grid || !d_sh)) return fail(SVR_ERR_INVALID, "null gradient output");
     if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_bwd(d, frame->sorted_alt, d_rgb, d_depth, d_alpha, T_final, last, d_grid,
+    cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid,
                                            d_sh, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
     return SVR_OK;

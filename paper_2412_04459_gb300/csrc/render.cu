@@ -1262,9 +1262,8 @@ static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth, float *alpha,
+cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float *alpha,
                               float *T_final, int32_t *last, int2 *stats, cudaStream_t s) {
-    (void)sorted_alt;  // the block lists carry the sorted values
     const FwdOut out = {rgb, depth, alpha, T_final, last, stats};
     cudaError_t e = cudaMemsetAsync(&f.status->fwd_next, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -1282,10 +1281,9 @@ cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, flo
     return cudaMemsetAsync(&f.status->fwd_done, 1, 1, s);
 }
 
-cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_rgb, const float *d_depth,
+cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float *d_depth,
                               const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
                               float *d_sh, cudaStream_t s) {
-    (void)sorted_alt;
     cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
     if (e == cudaSuccess && f.n_vox > 0)
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);

@@ -198,9 +198,9 @@ cudaError_t launch_order(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_emit(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties, cudaStream_t s);
 cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s);
-cudaError_t launch_render_fwd(const FrameDev &f, int sorted_alt, float *rgb, float *depth,
+cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth,
                               float *alpha, float *T_final, int32_t *last, int2 *stats, cudaStream_t s);
-cudaError_t launch_render_bwd(const FrameDev &f, int sorted_alt, const float *d_rgb,
+cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb,
                               const float *d_depth, const float *d_alpha, const float *T_final,
                               const int32_t *last, float *d_grid, float *d_sh, cudaStream_t s);
 

@@ -328,19 +328,23 @@ __device__ __forceinline__ void stage_ahead(Entry *st, const ViewData &vd, const
     __syncwarp();
 }
 
-// Number of entries of block-list positions [lo, hi) (sorted by index) whose
-// index is below key, plus lo: the first position at or past key.
+// First block-list position in [lo, hi) (entries sorted by index) whose
+// index is at least key, found by the whole warp: each round the lanes probe
+// the last entry of 32 equal chunks and keep the chunk holding the boundary,
+// then one probe per position; a list up to 1024 entries long costs two
+// dependent loads.
 __device__ __forceinline__ int lower_pos(const uint2 *__restrict__ list, int lo, int hi, int key) {
-    int up = hi;
-    if ((threadIdx.x & 31) == 0) {
-        if (lo < up && (int)__ldg(&list[up - 1].y) < key) lo = up;  // the usual case: no pixel stopped
-        while (lo < up) {
-            const int mid = (lo + up) >> 1;
-            if ((int)__ldg(&list[mid].y) < key) lo = mid + 1;
-            else up = mid;
-        }
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int s = (hi - lo + 31) >> 5;       // chunk length
+        const int pos = lo + (lane + 1) * s - 1;  // last position of chunk `lane`
+        const bool below = pos < hi && (int)__ldg(&list[pos].y) < key;
+        lo += s * __popc(__ballot_sync(0xffffffffu, below));  // chunks wholly below key
+        hi = min(hi, lo + s);
     }
-    return __shfl_sync(0xffffffffu, lo, 0);
+    const int pos = lo + lane;
+    const bool below = pos < hi && (int)__ldg(&list[pos].y) < key;
+    return lo + __popc(__ballot_sync(0xffffffffu, below));
 }
 
 // Work item of a render warp: segment `seg` of global tile g, 8x4 block blk.

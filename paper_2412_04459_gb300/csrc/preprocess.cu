@@ -311,9 +311,10 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ 
 // --------------------------------------------------------------------- emit
 
 constexpr int kEmitBatch = 8;
+constexpr int kEmitThreads = 256;
 
 // grid.y = view
-__global__ void __launch_bounds__(256) k_emit(FrameDev f) {
+__global__ void __launch_bounds__(kEmitThreads) k_emit(FrameDev f) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= f.n_vox) return;
     if (f.status->flags & SVR_FLAG_CAPACITY) return;
@@ -389,8 +390,8 @@ cudaError_t launch_scan(const FrameDev &f, cudaStream_t s) {
 
 cudaError_t launch_emit(const FrameDev &f, cudaStream_t s) {
     if (f.n_vox > 0) {
-        const dim3 grid((unsigned)((f.n_vox + 255) / 256), (unsigned)f.n_views);
-        k_emit<<<grid, 256, 0, s>>>(f);
+        const dim3 grid((unsigned)((f.n_vox + kEmitThreads - 1) / kEmitThreads), (unsigned)f.n_views);
+        k_emit<<<grid, kEmitThreads, 0, s>>>(f);
     }
     return cudaGetLastError();
 }

@@ -189,11 +189,11 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 // whose pixel box meets the block and whose sign pattern a pixel of the block
 // has.  k_block_lists extracts them once per frame, one CTA per entry of the
 // render work order (a tile, or one kSegLen-entry segment of a split tile):
-// thread t loads entries t, t + 256, ... of the segment (value and box) and
+// thread t loads entries t, t + kListThreads, ... of the segment (value and box) and
 // writes each one's mask of such blocks to shared memory (the box's block
 // rectangle AND the blocks holding a pixel with its sign bits, from the
 // per-block sign masks of k_tile_mask); then warp w keeps the entries of
-// blocks w, w + 8, ... by ballot, which preserves list order, and writes
+// blocks w, w + kListWarps, ... by ballot, which preserves list order, and writes
 // (value, sorted index) pairs.  Block b of a tile whose list is [beg, end)
 // owns the region B beg + b (end - beg) of the block lists, so the lists need
 // no allocation scan; segment s of a split tile writes from offset s kSegLen
@@ -201,10 +201,12 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 // block.  The CTA of segment 0 also clears the tile's merge counters for the
 // next forward.
 
-constexpr int kMaxBlocksPerWarp = 4;  // tile 32: 32 blocks over 8 warps
+constexpr int kListThreads = 128;
+constexpr int kListWarps = kListThreads / 32;
+constexpr int kMaxBlocksPerWarp = 32 / kListWarps;  // tile 32: 32 blocks over the warps
 constexpr int kListChunk = kSegLen;
 
-__global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
+__global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
     __shared__ uint32_t sval[kListChunk];
     __shared__ uint32_t smsk[kListChunk];
     if (blockIdx.x >= f.status->n_queue) return;
@@ -238,18 +240,20 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
     const int first = beg + sg * kListChunk;
     const int stop = split ? min(end, first + kListChunk) : end;
     uint2 *out = f.blist + (size_t)B * beg + (split ? (size_t)sg * kListChunk : 0);
-    unsigned cnt[kMaxBlocksPerWarp] = {0u, 0u, 0u, 0u};
+    unsigned cnt[kMaxBlocksPerWarp];
+#pragma unroll
+    for (int k = 0; k < kMaxBlocksPerWarp; ++k) cnt[k] = 0u;
     for (int c0 = first; c0 < stop; c0 += kListChunk) {
         const int n = min(kListChunk, stop - c0);
-        uint32_t v4[kListChunk / 256];
+        uint32_t v4[kListChunk / kListThreads];
 #pragma unroll
-        for (int r = 0; r < kListChunk / 256; ++r) {
-            const int t = threadIdx.x + 256 * r;
+        for (int r = 0; r < kListChunk / kListThreads; ++r) {
+            const int t = threadIdx.x + kListThreads * r;
             v4[r] = t < n ? __ldg(vals + c0 + t) : 0u;
         }
 #pragma unroll
-        for (int r = 0; r < kListChunk / 256; ++r) {
-            const int t = threadIdx.x + 256 * r;
+        for (int r = 0; r < kListChunk / kListThreads; ++r) {
+            const int t = threadIdx.x + kListThreads * r;
             unsigned m = 0;
             if (t < n) {
                 const ushort4 bx = __ldg(boxes + (v4[r] & 0x1FFFFFFFu));
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kMaxBlocksPerWarp; ++k) {
-            const int b = warp + 8 * k;
+            const int b = warp + kListWarps * k;
             if (b >= B) continue;
             for (int sub = 0; sub < n; sub += 32) {
                 const int j = sub + lane;
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(256) k_block_lists(FrameDev f, const uint32_t 
         uint32_t *len = split ? f.seg_len + (size_t)(ts.y + sg) * B : f.blen + (size_t)g * B;
 #pragma unroll
         for (int k = 0; k < kMaxBlocksPerWarp; ++k)
-            if (warp + 8 * k < B) len[warp + 8 * k] = cnt[k];
+            if (warp + kListWarps * k < B) len[warp + kListWarps * k] = cnt[k];
     }
 }
 
@@ -1228,7 +1232,7 @@ cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s
     if (f.total_tiles == 0) return cudaSuccess;
     // one CTA per entry of the work order; CTAs past the device-side count exit
     const int64_t grid = (int64_t)f.total_tiles + f.seg_slots;
-    k_block_lists<<<(unsigned)grid, 256, 0, s>>>(f, f.vals[sorted_alt]);
+    k_block_lists<<<(unsigned)grid, kListThreads, 0, s>>>(f, f.vals[sorted_alt]);
     return cudaGetLastError();
 }
 

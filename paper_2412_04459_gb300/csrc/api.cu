@@ -270,11 +270,8 @@ int preprocess(svr_frame *frame, const svr_scene *scene, const svr_camera *cams,
     for (int i = 0; i < kNumSlots; ++i) frame->offsets[i] = L.off[i];
     const svr::FrameDev d = frame_dev(frame);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(svr::Status), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&d.status->bad_voxel, 0xFF, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.tile_cnt, 0, sizeof(uint32_t) * svr::kTileSub * (size_t)ntiles, s);
-    if (e != cudaSuccess) return cuda_fail(e, "status reset");
-    e = svr::launch_tile_mask(d, s);
+    // the tile-mask kernel also clears the status block and the tile counters
+    cudaError_t e = svr::launch_tile_mask(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "tile mask");
     e = svr::launch_preprocess(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "preprocess");

@@ -37,8 +37,14 @@ namespace svr {
 constexpr int kMaskWarps = 8;
 
 __global__ void __launch_bounds__(32 * kMaskWarps) k_tile_mask(FrameDev f) {
+    // also starts the frame: status cleared (no smallest invalid voxel yet)
+    // and the tiles' pair counters zeroed, before k_preprocess counts
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(Status) / 4)
+        reinterpret_cast<unsigned *>(f.status)[threadIdx.x] =
+            threadIdx.x == offsetof(Status, bad_voxel) / 4 ? 0xFFFFFFFFu : 0u;
     const int g = blockIdx.x * kMaskWarps + (threadIdx.x >> 5);
     if (g >= f.total_tiles) return;
+    if ((threadIdx.x & 31) < kTileSub) f.tile_cnt[(size_t)(threadIdx.x & 31) * f.total_tiles + g] = 0u;
     const DevCam &cam = f.views[view_of_tile(f, g)];
     const int tile = g - cam.tile_base;
     const int T = cam.tile, bpr = T >> 3, B = f.blocks_per_tile;

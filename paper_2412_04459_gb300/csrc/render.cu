@@ -774,6 +774,16 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
         fwd_item<K, STATS>(f, it, ws, out);
         __syncwarp();
     }
+    // the launch's last warp to run out of work resets the work counter for
+    // the next launch and marks the segment sums as this sort's
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        if (atomicAdd(&f.status->fwd_exit, 1u) == gridDim.x * (blockDim.x >> 5) - 1) {
+            f.status->fwd_next = 0;
+            f.status->fwd_exit = 0;
+            f.status->fwd_done = 1;
+        }
+    }
 }
 
 // ----------------------------------------------------------------- backward
@@ -1273,8 +1283,9 @@ static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
 cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float *alpha,
                               float *T_final, int32_t *last, int2 *stats, cudaStream_t s) {
     const FwdOut out = {rgb, depth, alpha, T_final, last, stats};
-    cudaError_t e = cudaMemsetAsync(&f.status->fwd_next, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
+    // the work counter is zero here: cleared with the status block, then by
+    // the last warp of every launch
+    cudaError_t e;
     switch (f.K * 2 + (stats ? 1 : 0)) {
         case 2: e = fwd_k<1, false>(f, out, s); break;
         case 3: e = fwd_k<1, true>(f, out, s); break;
@@ -1284,9 +1295,7 @@ cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float
         case 7: e = fwd_k<3, true>(f, out, s); break;
         default: return cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess) return e;
-    // the segment sums in the workspace now belong to this sort (low byte: 1)
-    return cudaMemsetAsync(&f.status->fwd_done, 1, 1, s);
+    return e;
 }
 
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float *d_depth,

@@ -55,14 +55,15 @@ struct Status {
     unsigned flags;       // SVR_FLAG_*
     unsigned n_pairs_lo;  // total pair count (64-bit, split)
     unsigned n_pairs_hi;
-    int bad_voxel;        // smallest invalid voxel id, or INT_MAX
-    unsigned fwd_next;    // next work item of the forward render (reset before each launch)
-    unsigned bwd_next;    // next work item of the backward render
+    int bad_voxel;        // smallest invalid voxel id (all bits set: none)
+    unsigned fwd_next;    // next work item of the forward render (the last warp of a launch resets it)
+    unsigned bwd_next;    // next work item of the backward render (reset before each launch)
     unsigned n_queue;     // (tile, segment) entries of the render work order
     unsigned slots_used;  // segment slots taken by the split tiles
     unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort
     unsigned sort_next;   // next work-order entry of the long-list sort
-    unsigned pad[6];
+    unsigned fwd_exit;    // warps of the running forward launch that ran out of work
+    unsigned pad[5];
 };
 
 // Per-voxel record of one view (64 bytes):

@@ -42,7 +42,7 @@ BATCH_SIZES = ((640, 480), (1280, 840), (1920, 1080))
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_render_bwd<3> launch of
 # this workload, from the ncu capture summarised in profiles/render_bwd_shell1m.md
 # (to be retaken, or set to None, whenever that kernel changes)
-BWD_TRAFFIC_BYTES = 329_576_960
+BWD_TRAFFIC_BYTES = 321_802_496
 
 
 def parse():

@@ -985,6 +985,94 @@ struct BwdIn {
     float *d_grid;
 };
 
+// Front-to-back gradients for the pixels of an item whose transmittance
+// behind their part of the list underflowed (the back-to-front recovery
+// T_i = T_(i+1) / (1 - alpha_i) would lose precision): sweep 1 sums the
+// part's colour and depth from the transmittance in front of it, sweep 2
+// takes the gradients with the sums behind each voxel as total minus prefix.
+template <int K>
+__device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList L, int p0, int p1, int idx0,
+                                               int last, bool fallback, float T_before, float SC0, float SC1, float SC2,
+                                               float SD, const ViewData vd, const WarpBlock wb, const PixelRay p,
+                                               const PixelGrad g, Entry *st, RecSmem &rs, const BwdIn &in,
+                                               float *dcol) {
+    const int lane = threadIdx.x & 31;
+    const int n_fb = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : idx0));
+    // sweep 1: this part's own sums, from the transmittance in front of it
+    float T = T_before, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
+    for (int base = p0; base < n_fb; base += kBatch) {
+        Lookahead cur;
+        fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
+        fetch_box(cur, vd);
+        const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
+        stage_ahead(st, vd, cur);
+        if (fallback) {
+            for (unsigned c = cand; c; c &= c - 1u) {
+                const Entry &e = st[__ffs(c) - 1];
+                float a, b;
+                if (__float_as_int(e.c.w) > last || !slab(e, p, a, b)) continue;
+                float trans, dloc;
+                hit_fwd<K>(e, p, a, b, trans, dloc);
+                const float w = T * (1.f - trans);
+                Ct0 = fmaf(w, e.col.x, Ct0);
+                Ct1 = fmaf(w, e.col.y, Ct1);
+                Ct2 = fmaf(w, e.col.z, Ct2);
+                Dt = fmaf(T, dloc, Dt);
+                T *= trans;
+            }
+        }
+        __syncwarp();
+    }
+    Ct0 += SC0;
+    Ct1 += SC1;
+    Ct2 += SC2;
+    Dt += SD;
+    // sweep 2: gradients with the sums behind = total - prefix
+    float Tf = T_before, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
+    for (int base = p0; base < n_fb; base += kBatch) {
+        Lookahead cur;
+        fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
+        fetch_box(cur, vd);
+        const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
+        stage_ahead(st, vd, cur);
+        unsigned hits = 0;
+        if (fallback) {
+            for (unsigned c = cand; c; c &= c - 1u) {
+                const int k = __ffs(c) - 1;
+                const Entry &e = st[k];
+                float a, b;
+                if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
+            }
+        }
+        int off, end;
+        const int total = rec_layout(rs, hits, off, end);
+        for (int k_lo = 0, rb = 0; rb < total; rb = __shfl_sync(0xffffffffu, off, k_lo)) {
+            const int k_hi = rec_run_end(k_lo, end, rb);
+            unsigned h = hits & range_mask(k_lo, k_hi);
+            while (h != 0) {
+                const int k = __ffs(h) - 1;   // staged in increasing list order
+                h &= h - 1;
+                const Entry &e = st[k];
+                float a, b;
+                slab(e, p, a, b);
+                float T_i, Ta, w, dloc, dgeo[8], dc[3];
+                hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo, dc,
+                                   T_i, Ta, w, dloc);
+                PC0 = fmaf(w, e.col.x, PC0);
+                PC1 = fmaf(w, e.col.y, PC1);
+                PC2 = fmaf(w, e.col.z, PC2);
+                PD = fmaf(T_i, dloc, PD);
+                Tf = Ta;
+                rec_write(rs, rec_slot(rs, k, rb), dgeo, dc);
+            }
+            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol);
+            k_lo = k_hi;
+            if (k_lo >= 32) break;
+        }
+        __syncwarp();
+    }
+}
+
 template <int K>
 __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entry *st, RecSmem &rs,
                                          const BwdIn &in) {
@@ -1093,83 +1181,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         }
     }
 
-    // ---- front to back for pixels whose transmittance underflowed
-    if (__any_sync(0xffffffffu, fallback)) {
-        const int n_fb = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : idx0));
-        // sweep 1: this part's own sums, from the transmittance in front of it
-        float T = T_before, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
-        for (int base = p0; base < n_fb; base += kBatch) {
-            Lookahead cur;
-            fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
-            fetch_box(cur, vd);
-            const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
-            stage_ahead(st, vd, cur);
-            if (fallback) {
-                for (unsigned c = cand; c; c &= c - 1u) {
-                    const Entry &e = st[__ffs(c) - 1];
-                    float a, b;
-                    if (__float_as_int(e.c.w) > last || !slab(e, p, a, b)) continue;
-                    float trans, dloc;
-                    hit_fwd<K>(e, p, a, b, trans, dloc);
-                    const float w = T * (1.f - trans);
-                    Ct0 = fmaf(w, e.col.x, Ct0);
-                    Ct1 = fmaf(w, e.col.y, Ct1);
-                    Ct2 = fmaf(w, e.col.z, Ct2);
-                    Dt = fmaf(T, dloc, Dt);
-                    T *= trans;
-                }
-            }
-            __syncwarp();
-        }
-        Ct0 += SC0;
-        Ct1 += SC1;
-        Ct2 += SC2;
-        Dt += SD;
-        // sweep 2: gradients with the sums behind = total - prefix
-        float Tf = T_before, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
-        for (int base = p0; base < n_fb; base += kBatch) {
-            Lookahead cur;
-            fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
-            fetch_box(cur, vd);
-            const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
-            stage_ahead(st, vd, cur);
-            unsigned hits = 0;
-            if (fallback) {
-                for (unsigned c = cand; c; c &= c - 1u) {
-                    const int k = __ffs(c) - 1;
-                    const Entry &e = st[k];
-                    float a, b;
-                    if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
-                }
-            }
-            int off, end;
-            const int total = rec_layout(rs, hits, off, end);
-            for (int k_lo = 0, rb = 0; rb < total; rb = __shfl_sync(0xffffffffu, off, k_lo)) {
-                const int k_hi = rec_run_end(k_lo, end, rb);
-                unsigned h = hits & range_mask(k_lo, k_hi);
-                while (h != 0) {
-                    const int k = __ffs(h) - 1;   // staged in increasing list order
-                    h &= h - 1;
-                    const Entry &e = st[k];
-                    float a, b;
-                    slab(e, p, a, b);
-                    float T_i, Ta, w, dloc, dgeo[8], dc[3];
-                    hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo, dc,
-                                       T_i, Ta, w, dloc);
-                    PC0 = fmaf(w, e.col.x, PC0);
-                    PC1 = fmaf(w, e.col.y, PC1);
-                    PC2 = fmaf(w, e.col.z, PC2);
-                    PD = fmaf(T_i, dloc, PD);
-                    Tf = Ta;
-                    rec_write(rs, rec_slot(rs, k, rb), dgeo, dc);
-                }
-                rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol);
-                k_lo = k_hi;
-                if (k_lo >= 32) break;
-            }
-            __syncwarp();
-        }
-    }
+    // ---- front to back for pixels whose transmittance underflowed (rare:
+    // kept out of line so that it does not weigh on the main path's registers)
+    if (__any_sync(0xffffffffu, fallback))
+        bwd_front_to_back<K>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, vd, wb, p, g, st, rs, in,
+                             dcol);
 }
 
 template <int K>

@@ -47,7 +47,8 @@
 // instead, with SC_i, SD_i from totals recomputed in a first sweep.  The
 // per-voxel gradients (8 corner densities, 3 colour channels) of all the
 // warp's pixels are summed per staged entry in shared memory, and each entry
-// that was hit is added to the global accumulators once per warp.
+// that was hit is added to the global accumulators once per warp (a colour
+// channel that the clamp of Eq. vox_color cut gets no gradient).
 #include "svr_internal.cuh"
 
 namespace svr {

@@ -120,3 +120,12 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     assert lib.svr_render_fwd(N.ref(fr), None, None, None, None, None, None) == N.SVR_ERR_INVALID
     assert lib.svr_render_bwd(N.ref(fr), None, None, None, None, None, None, None, None) == N.SVR_ERR_INVALID
     assert lib.svr_frame_buffers(N.ref(fr), None) == N.SVR_ERR_INVALID
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libsvr.so the binding raises: there is no CPU fallback."""
+    from paper_2412_04459_gb300 import _native
+    monkeypatch.setattr(_native, "_LIB", None)
+    monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "libsvr.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _native.lib()

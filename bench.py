@@ -34,7 +34,11 @@ if ROOT not in sys.path:
 METRIC = "fwd frames/s & fwd+bwd steps/s, 1M voxels 1280x840; % HBM roofline"
 L2_FLUSH_BYTES = 256 << 20           # > 129 MB L2
 FP32_LANES_PER_SM = 128
-# FP32 operations of the path, per unit of counted work:
+# FP32 operations of the path per unit of counted work (an FMA counts once): a
+# candidate's slab test is 6 multiplies, 4 min/max and 2 compares; a composited
+# segment is its setup plus, per sample, the trilinear interpolation, explin,
+# the exponential and the depth and transmittance updates; the backward adds,
+# per sample, the chain through explin and the 8 trilinear weights.
 OPS_CAND = 12                         # slab test of one candidate entry
 OPS_HIT = {1: 42, 2: 71, 3: 100}      # one composited segment (forward)
 OPS_HIT_BWD = {1: 98, 2: 156, 3: 214}  # one segment in the backward (recompute + gradient)

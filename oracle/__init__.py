@@ -29,6 +29,13 @@ from . import build as _build
 
 _LIB = None
 
+# Relative band |T / t_stop - 1| around the stop threshold inside which a
+# pixel's termination decision is rounding-sensitive for an FP32 renderer
+# (its transmittance after ~30 composited voxels carries a relative error of
+# a few 1e-6): such pixels are reported as near_stop and left out of
+# elementwise image and gradient comparisons, and counted.
+NEAR_STOP_REL = 1e-5
+
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 
 
@@ -63,7 +70,7 @@ def lib():
                                 ctypes.c_int64, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.oc_render_grad.restype = ctypes.c_int
         L.oc_render_grad.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P,
-                                     ctypes.c_int64, P, P, P, P, P, P, ctypes.c_int]
+                                     ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.oc_ray_hits.restype = ctypes.c_int64
         L.oc_ray_hits.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, ctypes.c_int64,
                                   P, P, P]
@@ -125,37 +132,55 @@ def _pixels(cam, pixels):
 
 
 def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, threads=None,
-           grid=None, sh=None):
+           grid=None, sh=None, near_stop_rel=None):
     """Brute-force FP64 render.  pixels: int [n, 2] of (x, y), or None for the
     whole image (outputs then reshaped to [H, W]).  grid / sh: optional FP64
-    overrides of the scene's parameters (finite differences)."""
+    overrides of the scene's parameters (finite differences).
+
+    Besides the images, per pixel: n_comp (voxels composited), term_vox (the
+    voxel that stopped the walk, -1 if none), stop_margin (smallest
+    |T / t_stop - 1| after a composited voxel: how close the walk came to a
+    different termination decision) and near_stop = stop_margin <
+    near_stop_rel (default NEAR_STOP_REL), the pixels whose termination an
+    FP32 renderer may legitimately decide the other way."""
     centre, level, corner, g, s = _scene_arrays(scene, grid, sh)
     n, px = _pixels(cam, pixels)
     out = dict(rgb=np.zeros((n, 3)), depth=np.zeros(n), alpha=np.zeros(n), t_final=np.zeros(n),
                n_comp=np.zeros(n, np.int32), term_vox=np.zeros(n, np.int64),
-               near_stop=np.zeros(n, np.uint8))
+               stop_margin=np.zeros(n))
     c = camera_struct(cam)
     p = params_struct(K, t_stop, bg)
     rc = lib().oc_render(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre), _ptr(level),
                          _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c), ctypes.byref(p), n,
                          _ptr(px), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]),
                          _ptr(out["t_final"]), _ptr(out["n_comp"]), _ptr(out["term_vox"]),
-                         _ptr(out["near_stop"]), _threads(threads))
+                         _ptr(out["stop_margin"]), _threads(threads))
     if rc != 0:
         raise RuntimeError(f"oc_render failed ({rc})")
+    band = NEAR_STOP_REL if near_stop_rel is None else float(near_stop_rel)
+    out["near_stop"] = (out["stop_margin"] < band).astype(np.uint8)
     if pixels is None:
         H, W = cam.height, cam.width
         out["rgb"] = out["rgb"].reshape(H, W, 3).transpose(2, 0, 1).copy()
-        for k in ("depth", "alpha", "t_final", "n_comp", "term_vox", "near_stop"):
+        for k in ("depth", "alpha", "t_final", "n_comp", "term_vox", "stop_margin", "near_stop"):
             out[k] = out[k].reshape(H, W)
     return out
 
 
 def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0),
-                pixels=None, threads=None, grid=None, sh=None):
+                pixels=None, threads=None, grid=None, sh=None, magnitudes=None):
     """Analytic FP64 gradient of sum(g_rgb*C + g_depth*D + g_alpha*A).
     Full image: g_rgb [3, H, W], g_depth/g_alpha [H, W]; pixel list: g_rgb
-    [n, 3], g_depth/g_alpha [n].  Returns (d_grid [Pts], d_sh [N, 48])."""
+    [n, 3], g_depth/g_alpha [n].  Returns (d_grid [Pts], d_sh [N, 48]).
+    magnitudes: a dict that, if given, receives "grid" and "sh", the sums of
+    the absolute values of the terms each gradient element adds up (per
+    pixel, voxel hit and sample), and "grid_seg" and "sh_seg", the same sums
+    with every term weighted by the condition number of its hit's segment
+    length b - a with respect to relative perturbations of the entry and exit
+    plane coordinates, the ray origin and the direction components:
+    ((|P_i| + |o_i|) / |d_i| + |a| + (|Q_j| + |o_j|) / |d_j| + |b|) / (b - a),
+    i and j the axes of the entry plane P and the exit plane Q (large for a
+    ray that grazes the voxel)."""
     centre, level, corner, g, s = _scene_arrays(scene, grid, sh)
     n, px = _pixels(cam, pixels)
     if pixels is None:
@@ -165,14 +190,20 @@ def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 
     ga = np.ascontiguousarray(g_alpha, np.float64).reshape(n)
     d_grid = np.zeros(len(g))
     d_sh = np.zeros((scene.n_vox, 48))
+    want = magnitudes is not None
+    a_grid, a_sh = (np.zeros(len(g)), np.zeros((scene.n_vox, 48))) if want else (None, None)
+    k_grid, k_sh = (np.zeros(len(g)), np.zeros((scene.n_vox, 48))) if want else (None, None)
     c = camera_struct(cam)
     p = params_struct(K, t_stop, bg)
     rc = lib().oc_render_grad(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre),
                               _ptr(level), _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c),
                               ctypes.byref(p), n, _ptr(px), _ptr(gr), _ptr(gd), _ptr(ga),
-                              _ptr(d_grid), _ptr(d_sh), _threads(threads))
+                              _ptr(d_grid), _ptr(d_sh), _ptr(a_grid), _ptr(a_sh), _ptr(k_grid), _ptr(k_sh),
+                              _threads(threads))
     if rc != 0:
         raise RuntimeError(f"oc_render_grad failed ({rc})")
+    if magnitudes is not None:
+        magnitudes.update(grid=a_grid, sh=a_sh, grid_seg=k_grid, sh_seg=k_sh)
     return d_grid, d_sh
 
 

@@ -154,6 +154,38 @@ int oc_ray_aabb(const double c[3], double s, const double ro[3], const double rd
     return (amax <= bmin) && (amax > 0.0);
 }
 
+/* Condition number of the segment length b - a of a valid hit with respect
+ * to relative perturbations of the numbers that define it: a = (P - r_o)_i /
+ * r_d,i on the entry plane's axis i and b = (Q - r_o)_j / r_d,j on the exit
+ * plane's axis j move by (|P_i| + |r_o,i|) / |r_d,i| + |a| (and likewise b) per
+ * unit relative change of the plane coordinate, the origin and the direction
+ * component; their sum over the length.  Large for a ray that grazes the
+ * voxel, or crosses a plane nearly parallel to it. */
+static double segment_condition(const double c[3], double s, const double ro[3], const double rd[3],
+                                double a, double b) {
+    int ia = -1, ib = -1;
+    double amax = -INFINITY, bmin = INFINITY, pa = 0.0, pb = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double lo = c[i] - 0.5 * s, hi = c[i] + 0.5 * s;
+        double c0 = (lo - ro[i]) / rd[i], c1 = (hi - ro[i]) / rd[i];
+        double near = fmin(c0, c1), far = fmax(c0, c1);
+        if (near > amax) {
+            amax = near;
+            ia = i;
+            pa = c0 < c1 ? lo : hi;
+        }
+        if (far < bmin) {
+            bmin = far;
+            ib = i;
+            pb = c0 < c1 ? hi : lo;
+        }
+    }
+    if (ia < 0 || ib < 0 || !(b > a)) return 0.0;
+    double da = (fabs(pa) + fabs(ro[ia])) / fabs(rd[ia]) + fabs(a);
+    double db = (fabs(pb) + fabs(ro[ib])) / fabs(rd[ib]) + fabs(b);
+    return (da + db) / (b - a);
+}
+
 /* Trilinear weights of Eq. (interp) for local coordinate q, corner order
  * V_000, V_001, ..., V_111 (subscript = x, y, z bits, x most significant). */
 static void trilinear_weights(const double q[3], double w[8]) {
@@ -287,7 +319,7 @@ typedef struct {
     double rgb[3], depth, alpha, t_final;
     int32_t n_comp;
     int64_t term_vox;  /* voxel whose compositing stopped the ray, or -1 */
-    uint8_t near_stop; /* some T after a voxel lies within 1e-3 relative of t_stop */
+    double stop_margin; /* min over composited voxels of |T after it / t_stop - 1| (HUGE_VAL: none) */
 } oc_pixel_out;
 
 #define OC_KMAX 8
@@ -300,7 +332,7 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
     double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
     int32_t n = 0;
     o->term_vox = -1;
-    o->near_stop = 0;
+    o->stop_margin = HUGE_VAL;
     if (scratch_comp(s, n_hits > 0 ? n_hits : 1)) return -1;
     for (int64_t i = 0; i < n_hits; ++i) {
         int64_t v = s->hits[i].v;
@@ -332,7 +364,10 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
         }
         ++n;
         T = T * (1.0 - alpha);
-        if (P->t_stop > 0.0 && fabs(T / P->t_stop - 1.0) < 1e-3) o->near_stop = 1;
+        if (P->t_stop > 0.0) {
+            double m = fabs(T / P->t_stop - 1.0);
+            if (m < o->stop_margin) o->stop_margin = m;
+        }
         if (T < P->t_stop) {
             o->term_vox = v;
             break;
@@ -359,10 +394,20 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
  *     (the K <= 3 cases are the closed forms of Sec. A.4),
  *   dalpha_ik/dv_ik = (1 - alpha_ik) (l/K) explin'(v_ik),
  *   dv_ik/dV_c = trilinear weight of corner c,
- *   dc/dsh[n][ch] = Y_n(dir) if the pre-clamp channel is > 0, else 0. */
+ *   dc/dsh[n][ch] = Y_n(dir) if the pre-clamp channel is > 0, else 0.
+ * d_grid_abs / d_sh_abs (may be NULL) accumulate the absolute value of every
+ * term added to d_grid / d_sh: the magnitude of an element's contributions,
+ * which bounds how much of it the rounding of a lower-precision sum can
+ * change when the contributions cancel.  d_grid_seg / d_sh_seg (may be NULL)
+ * accumulate each term's absolute value times the condition number of the
+ * hit's segment length l = (b - a)|r_d| (segment_condition): every term of a
+ * hit is proportional to l for a grazing hit, so a renderer that rounds the
+ * planes, the origin and the direction to precision u has a relative error of
+ * order u times this factor in those terms. */
 static void pixel_backward(const oc_scene *S, const oc_params *P, const double ro[3], const double rd[3],
                            const oc_scratch *s, const oc_pixel_out *o, const double g_rgb[3],
-                           double g_depth, double g_alpha, double *d_grid, double *d_sh) {
+                           double g_depth, double g_alpha, double *d_grid, double *d_sh,
+                           double *d_grid_abs, double *d_sh_abs, double *d_grid_seg, double *d_sh_seg) {
     const int K = P->K;
     int32_t n = o->n_comp;
     double RC[3] = {P->bg[0], P->bg[1], P->bg[2]};
@@ -373,6 +418,7 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
         double Ti = s->T[i], al = s->alpha[i], ell = s->ell[i];
         const double *c = s->col + 3 * i;
         const double *pre = s->pre + 3 * i;
+        double kappa = segment_condition(S->centre + 3 * v, ldexp(S->world_size, -(int)S->level[v]), ro, rd, a, b);
         double g = 0.0;
         for (int ch = 0; ch < 3; ++ch) g += g_rgb[ch] * Ti * (c[ch] - RC[ch]);
         g += g_depth * (-Ti * RD);
@@ -401,6 +447,14 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
                 double add = gv * w[k][j];
 #pragma omp atomic
                 d_grid[ci[j]] += add;
+                if (d_grid_abs) {
+#pragma omp atomic
+                    d_grid_abs[ci[j]] += fabs(add);
+                }
+                if (d_grid_seg) {
+#pragma omp atomic
+                    d_grid_seg[ci[j]] += fabs(add) * kappa;
+                }
             }
         }
         /* colour */
@@ -416,6 +470,14 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
                     double add = Y[m] * dc;
 #pragma omp atomic
                     d_sh[48 * v + 3 * m + ch] += add;
+                    if (d_sh_abs) {
+#pragma omp atomic
+                        d_sh_abs[48 * v + 3 * m + ch] += fabs(add);
+                    }
+                    if (d_sh_seg) {
+#pragma omp atomic
+                        d_sh_seg[48 * v + 3 * m + ch] += fabs(add) * kappa;
+                    }
                 }
             }
         }
@@ -441,13 +503,16 @@ static void pixel_xy(const oc_camera *cam, int64_t n_px, const int32_t *px_xy, i
 
 /* Forward render of n_px pixels (px_xy = NULL: every pixel, row-major).
  * Per pixel: rgb[3], depth, alpha, t_final, number of composited hits, the
- * terminating voxel (-1 if none) and the near-threshold flag.  Returns 0, or
+ * terminating voxel (-1 if none) and the stop margin: the smallest relative
+ * distance |T / t_stop - 1| of the transmittance after a composited voxel from
+ * the stop threshold (HUGE_VAL if t_stop = 0 or nothing was composited), which
+ * says how close the pixel came to another termination decision.  Returns 0, or
  * -1 on allocation failure. */
 int oc_render(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
               const int32_t *corner_idx, const double *grid, const double *sh,
               const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
               double *rgb, double *depth, double *alpha, double *t_final, int32_t *n_comp,
-              int64_t *term_vox, uint8_t *near_stop, int n_threads) {
+              int64_t *term_vox, double *stop_margin, int n_threads) {
     oc_scene S = {world_size, n_vox, centre, level, corner_idx, grid, sh};
     if (P->K < 1 || P->K > OC_KMAX) return -2;
     int err = 0;
@@ -479,7 +544,7 @@ int oc_render(double world_size, int64_t n_vox, const double *centre, const uint
             t_final[p] = o.t_final;
             if (n_comp) n_comp[p] = o.n_comp;
             if (term_vox) term_vox[p] = o.term_vox;
-            if (near_stop) near_stop[p] = o.near_stop;
+            if (stop_margin) stop_margin[p] = o.stop_margin;
         }
         scratch_free(&s);
     }
@@ -493,7 +558,8 @@ int oc_render_grad(double world_size, int64_t n_vox, const double *centre, const
                    const int32_t *corner_idx, const double *grid, const double *sh,
                    const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
                    const double *g_rgb, const double *g_depth, const double *g_alpha,
-                   double *d_grid, double *d_sh, int n_threads) {
+                   double *d_grid, double *d_sh, double *d_grid_abs, double *d_sh_abs,
+                   double *d_grid_seg, double *d_sh_seg, int n_threads) {
     oc_scene S = {world_size, n_vox, centre, level, corner_idx, grid, sh};
     if (P->K < 1 || P->K > OC_KMAX) return -2;
     int err = 0;
@@ -519,7 +585,8 @@ int oc_render_grad(double world_size, int64_t n_vox, const double *centre, const
                 err = -1;
                 continue;
             }
-            pixel_backward(&S, P, ro, rd, &s, &o, g_rgb + 3 * p, g_depth[p], g_alpha[p], d_grid, d_sh);
+            pixel_backward(&S, P, ro, rd, &s, &o, g_rgb + 3 * p, g_depth[p], g_alpha[p], d_grid, d_sh,
+                           d_grid_abs, d_sh_abs, d_grid_seg, d_sh_seg);
         }
         scratch_free(&s);
     }

@@ -479,3 +479,59 @@ def test_colour_uses_direction_to_voxel_centre():
     ratio = out["rgb"][0][seen] / out["alpha"][seen]
     assert np.allclose(ratio, c, rtol=1e-6)
     assert (out["rgb"][1] == 0).all() and (out["rgb"][2] == 0).all()
+
+
+def test_gradient_magnitudes():
+    """The oracle's contribution magnitudes (sum of |term| per gradient
+    element): never below |gradient|; equal to it where an element has one
+    term (one pixel through one voxel, K = 1); unchanged when every upstream
+    gradient flips sign (the gradient flips); doubled when they double."""
+    sc = _single_voxel_scene(2, (1, 2, 1), 1.5, sh_dc=0.7)
+    sc.grid[:] = np.linspace(0.5, 2.5, sc.n_pts).astype(np.float32)
+    cam = synth.look_at((-1.2, 0.8, -1.5), (0.375, 0.625, 0.375), (0, 1, 0), 25.0, 16, 16)
+    ref = oracle.render(sc, cam, K=1, t_stop=0.0)
+    y, x = np.unravel_index(np.argmax(ref["alpha"]), ref["alpha"].shape)
+    assert ref["n_comp"][y, x] == 1
+    px = np.array([[x, y]])
+    up = (np.array([[0.3, -1.2, 0.8]]), np.array([0.5]), np.array([-0.7]))
+    mag = {}
+    g, s = oracle.render_grad(sc, cam, *up, K=1, t_stop=0.0, pixels=px, magnitudes=mag)
+    assert np.allclose(mag["grid"], np.abs(g), rtol=1e-12, atol=0)
+    assert np.allclose(mag["sh"], np.abs(s), rtol=1e-12, atol=0)
+    # the segment-weighted magnitudes carry the condition number of the hit's
+    # length b - a: perturbing the voxel's planes, the origin and the
+    # direction by relative 1e-9 moves b - a by at most 1e-9 kappa (first
+    # order), and some perturbation comes within a factor 4 of it
+    ro, rd = oracle.pixel_ray(cam, x, y)
+    vs = float(sc.world_size) / 4
+    c0 = sc.centre[0].astype(np.float64)
+    a, b, ok = oracle.ray_aabb(c0, vs, ro, rd)
+    assert ok and b > a
+    kappa = mag["grid_seg"][mag["grid"] > 0] / mag["grid"][mag["grid"] > 0]
+    assert np.allclose(kappa, kappa[0], rtol=1e-12) and np.allclose(mag["sh_seg"][mag["sh"] > 0] /
+                                                                    mag["sh"][mag["sh"] > 0], kappa[0], rtol=1e-12)
+    kappa = kappa[0]
+    eps, worst = 1e-9, 0.0
+    rng = np.random.default_rng(0)
+    for _ in range(2000):
+        sgn = rng.choice([-1.0, 1.0], size=(4, 3))
+        lo = (c0 - vs / 2) * (1 + eps * sgn[0])
+        hi = (c0 + vs / 2) * (1 + eps * sgn[1])
+        o = ro * (1 + eps * sgn[2])
+        d = rd * (1 + eps * sgn[3])
+        t0, t1 = (lo - o) / d, (hi - o) / d
+        aa, bb = np.minimum(t0, t1).max(), np.maximum(t0, t1).min()
+        worst = max(worst, abs((bb - aa) - (b - a)) / (b - a) / eps)
+    assert worst <= kappa * 1.01 and worst >= kappa / 4, (worst, kappa)
+    # a whole image: many terms per element
+    G = synth.upstream_grads(3, cam.height, cam.width)
+    m1 = {}
+    g1, s1 = oracle.render_grad(sc, cam, G[0].astype(np.float64), G[1], G[2], K=2, t_stop=0.0, magnitudes=m1)
+    assert (m1["grid"] >= np.abs(g1) - 1e-15).all() and (m1["sh"] >= np.abs(s1) - 1e-15).all()
+    assert (m1["grid"] > 1.5 * np.abs(g1)).any()           # some elements cancel
+    m2 = {}
+    g2, s2 = oracle.render_grad(sc, cam, -G[0].astype(np.float64), -G[1], -G[2], K=2, t_stop=0.0, magnitudes=m2)
+    assert np.allclose(g2, -g1, rtol=1e-12, atol=1e-300) and np.allclose(m2["grid"], m1["grid"], rtol=1e-12)
+    m3 = {}
+    oracle.render_grad(sc, cam, 2 * G[0].astype(np.float64), 2 * G[1], 2 * G[2], K=2, t_stop=0.0, magnitudes=m3)
+    assert np.allclose(m3["grid"], 2 * m1["grid"], rtol=1e-12) and np.allclose(m3["sh"], 2 * m1["sh"], rtol=1e-12)

@@ -102,6 +102,17 @@ __device__ __forceinline__ float trilerp(const float4 &g0, const float4 &g1, flo
     return fmaf(qx, c1 - c0, c0);
 }
 
+// alpha = 1 - exp(-X) of a segment with optical depth X = sum_k (l/K) sigma_k
+// (Eq. supp_alpha_comp), given P = prod_k exp(-(l/K) sigma_k).  1 - P loses
+// its relative precision as X -> 0 (P rounds to within 2^-24 of 1); below
+// X = 1/32 the series X - X^2/2 + X^3/6 - X^4/24 is used instead, whose first
+// omitted term is below 1e-8 of alpha there, so alpha (and every weight and
+// gradient proportional to it) keeps its relative precision for faint voxels.
+__device__ __forceinline__ float seg_alpha(float X, float P) {
+    const float s = X * fmaf(-0.5f * X, fmaf(-0.333333333f * X, fmaf(-0.25f, X, 1.f), 1.f), 1.f);
+    return X < 0.03125f ? s : 1.f - P;
+}
+
 struct PixelRay {
     float3 rd, inv;
     float rdn;
@@ -423,10 +434,10 @@ __device__ __forceinline__ float *seg_fields(const FrameDev &f, unsigned slot, i
 
 // ------------------------------------------------------------------ forward
 
-// Local depth and transmittance factor of a hit.
+// Local depth, transmittance factor and alpha of a hit.
 template <int K>
 __device__ __forceinline__ void hit_fwd(const Entry &e, const PixelRay &p, float a, float b, float &trans,
-                                        float &dloc) {
+                                        float &dloc, float &alpha) {
     const float inv_k = 1.0f / K;
     const float seg = b - a;
     const float xs = seg * p.rdn * inv_k;
@@ -434,17 +445,20 @@ __device__ __forceinline__ void hit_fwd(const Entry &e, const PixelRay &p, float
     const float inv_size = e.b.w;
     const float rx = p.rd.x * inv_size, ry = p.rd.y * inv_size, rz = p.rd.z * inv_size;
     float t = fmaf(0.5f, step, a);
-    float P = 1.f, d = 0.f;
+    float P = 1.f, d = 0.f, X = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float v = trilerp(e.g0, e.g1, fmaf(t, rx, -e.c.x), fmaf(t, ry, -e.c.y), fmaf(t, rz, -e.c.z));
-        const float ek = __expf(-xs * explin(v));
+        const float xk = xs * explin(v);
+        const float ek = __expf(-xk);
         d = fmaf(P * (1.f - ek), t, d);
         P *= ek;
+        X += xk;
         t += step;
     }
     trans = P;
     dloc = d;
+    alpha = seg_alpha(X, P);
 }
 
 struct FwdOut {
@@ -518,7 +532,7 @@ __device__ __forceinline__ bool slab_slot(const FwdSlot &e, const PixelRay &p, f
 // exit plane there and the entry plane elsewhere).
 template <int K>
 __device__ __forceinline__ void hit_fwd_slot(const FwdSlot &e, const PixelRay &p, const float3 &sb, float a,
-                                             float b, float &trans, float &dloc) {
+                                             float b, float &trans, float &dloc, float &alpha) {
     const float inv_k = 1.0f / K;
     const float seg = b - a;
     const float xs = seg * p.rdn * inv_k;
@@ -530,17 +544,20 @@ __device__ __forceinline__ void hit_fwd_slot(const FwdSlot &e, const PixelRay &p
     const float4 g0 = e.g0, g1 = e.g1;
     const float rx = p.rd.x * inv, ry = p.rd.y * inv, rz = p.rd.z * inv;
     float t = fmaf(0.5f, step, a);
-    float P = 1.f, d = 0.f;
+    float P = 1.f, d = 0.f, X = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float v = trilerp(g0, g1, fmaf(t, rx, -cx), fmaf(t, ry, -cy), fmaf(t, rz, -cz));
-        const float ek = __expf(-xs * explin(v));
+        const float xk = xs * explin(v);
+        const float ek = __expf(-xk);
         d = fmaf(P * (1.f - ek), t, d);
         P *= ek;
+        X += xk;
         t += step;
     }
     trans = P;
     dloc = d;
+    alpha = seg_alpha(X, P);
 }
 
 // Walk block-list positions [p0, p1) front to back from state s.  The list
@@ -589,10 +606,10 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                 float a, b;
                 slab_slot(e, p, a, b);
                 if (STATS) ++s.n_hit;
-                float P, dloc;
-                hit_fwd_slot<K>(e, p, sb, a, b, P, dloc);
+                float P, dloc, al;
+                hit_fwd_slot<K>(e, p, sb, a, b, P, dloc, al);
                 const float4 col = e.col;
-                const float w = s.T * (1.f - P);
+                const float w = s.T * al;
                 s.C0 = fmaf(w, col.x, s.C0);
                 s.C1 = fmaf(w, col.y, s.C1);
                 s.C2 = fmaf(w, col.z, s.C2);
@@ -813,7 +830,7 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     const float rx = p.rd.x * inv_size, ry = p.rd.y * inv_size, rz = p.rd.z * inv_size;
     float tk[K], ek[K], qx[K], qy[K], qz[K], dsig[K];
     float t = fmaf(0.5f, step, a);
-    float trans = 1.f, d = 0.f;
+    float trans = 1.f, d = 0.f, X = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         qx[k] = fmaf(t, rx, -e.c.x);
@@ -822,7 +839,9 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
         const float v = trilerp(e.g0, e.g1, qx[k], qy[k], qz[k]);
         const float sig = explin(v);
         dsig[k] = v > 1.1f ? 1.f : sig * 0.909090909f;
-        ek[k] = __expf(-xs * sig);
+        const float xk = xs * sig;
+        ek[k] = __expf(-xk);
+        X += xk;
         tk[k] = t;
         d = fmaf(trans * (1.f - ek[k]), t, d);
         trans *= ek[k];
@@ -835,7 +854,7 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
         T_i = T_known;
         T_after = T_known * trans;
     }
-    w = T_i * (1.f - trans);
+    w = T_i * seg_alpha(X, trans);
     dloc = d;
     if (!B2F) {
         SC0 -= w * e.col.x;
@@ -1012,9 +1031,9 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 const Entry &e = st[__ffs(c) - 1];
                 float a, b;
                 if (__float_as_int(e.c.w) > last || !slab(e, p, a, b)) continue;
-                float trans, dloc;
-                hit_fwd<K>(e, p, a, b, trans, dloc);
-                const float w = T * (1.f - trans);
+                float trans, dloc, al;
+                hit_fwd<K>(e, p, a, b, trans, dloc, al);
+                const float w = T * al;
                 Ct0 = fmaf(w, e.col.x, Ct0);
                 Ct1 = fmaf(w, e.col.y, Ct1);
                 Ct2 = fmaf(w, e.col.z, Ct2);
@@ -1279,8 +1298,8 @@ static unsigned persistent_grid(Kern kernel, int threads) {
 // one segment); the kernels read the exact count from the device.
 template <int K, bool ST>
 static cudaError_t fwd_k(const FrameDev &f, const FwdOut &out, cudaStream_t s) {
-    static unsigned grid = 0;
-    if (grid == 0) grid = persistent_grid(k_render_fwd<K, ST>, kThreads);
+    static DeviceCache cache;
+    const unsigned grid = device_cached(cache, [] { return persistent_grid(k_render_fwd<K, ST>, kThreads); });
     const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kWarps - 1) / kWarps);
     k_render_fwd<K, ST><<<g, kThreads, 0, s>>>(f, out);
@@ -1289,8 +1308,8 @@ static cudaError_t fwd_k(const FrameDev &f, const FwdOut &out, cudaStream_t s) {
 
 template <int K>
 static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
-    static unsigned grid = 0;
-    if (grid == 0) grid = persistent_grid(k_render_bwd<K>, kBwdThreads);
+    static DeviceCache cache;
+    const unsigned grid = device_cached(cache, [] { return persistent_grid(k_render_bwd<K>, kBwdThreads); });
     const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kBwdWarps - 1) / kBwdWarps);
     k_render_bwd<K><<<g, kBwdThreads, 0, s>>>(f, in);

@@ -369,15 +369,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_runs(FrameDev f) {
     }
 }
 
-static int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+static unsigned sm_count() {
+    static DeviceCache cache;
+    return device_cached(cache, [] {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
+        return (unsigned)(n > 0 ? n : 1);
+    });
 }
 
 cudaError_t launch_order(const FrameDev &f, cudaStream_t s) {
@@ -391,16 +390,14 @@ cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties
     const unsigned grid = (unsigned)((int64_t)f.total_tiles + f.seg_slots);
     k_sort_small<<<grid, kSmallThreads, 0, s>>>(f, lo_bit, nbits, ties);
     // the shared-memory opt-in is a per-device function attribute
-    static unsigned long long attr_set = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
-        cudaError_t e = cudaFuncSetAttribute(k_merge_runs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMergeSmemBytes);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set |= 1ull << dev;
-    }
-    k_merge_runs<<<tmin(grid, (unsigned)sm_count()), kMergeThreads, kMergeSmemBytes, s>>>(f);
+    static DeviceCache attr_set;
+    cudaError_t e = cudaSuccess;
+    device_cached(attr_set, [&e] {
+        e = cudaFuncSetAttribute(k_merge_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMergeSmemBytes);
+        return e == cudaSuccess ? 1u : 0u;
+    });
+    if (e != cudaSuccess) return e;
+    k_merge_runs<<<tmin(grid, sm_count()), kMergeThreads, kMergeSmemBytes, s>>>(f);
     return cudaGetLastError();
 }
 

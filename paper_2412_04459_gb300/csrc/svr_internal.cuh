@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/svr.h"
 
 namespace svr {
@@ -187,6 +189,27 @@ __device__ __forceinline__ int view_of_tile(const FrameDev &f, int g) {
     int v = 0;
     while (v + 1 < f.n_views && g >= f.views[v + 1].tile_base) ++v;
     return v;
+}
+
+// A launch constant (a persistent grid size, an SM count) kept per device,
+// so that a process driving several GPUs in turn launches each with its
+// own; 0 means not computed yet.  Concurrent first calls may both compute
+// it and store the same value.
+constexpr int kMaxDevices = 64;
+struct DeviceCache {
+    std::atomic<unsigned> v[kMaxDevices];
+};
+
+template <class F>
+unsigned device_cached(DeviceCache &c, F compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute();
+    unsigned x = c.v[dev].load(std::memory_order_relaxed);
+    if (x == 0) {
+        x = compute();
+        c.v[dev].store(x, std::memory_order_relaxed);
+    }
+    return x;
 }
 
 // Records a printf-style message for svr_last_error() and returns code.

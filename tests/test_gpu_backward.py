@@ -7,7 +7,7 @@ import pytest
 import oracle
 import synth
 from tests.conftest import cached
-from tests.gpu_common import compare_grads, require_gpu, run_gpu, to_np
+from tests.gpu_common import compare_grads, oracle_grads, require_gpu, run_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +29,9 @@ def _grads(scene, cam, K, t_stop, bg, seed, ref_stop=None):
         g_alpha = g_alpha * keep
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     d_grid, d_sh = fr.backward(t(g_rgb), t(g_depth), t(g_alpha), out)
-    og, osh = oracle.render_grad(scene, cam, g_rgb.astype(np.float64), g_depth, g_alpha, K=K,
-                                 t_stop=t_stop, bg=bg)
-    return d_grid.cpu().numpy(), d_sh.cpu().numpy(), og, osh
+    og, osh, mag = oracle_grads(scene, cam, g_rgb.astype(np.float64), g_depth, g_alpha, K=K,
+                                t_stop=t_stop, bg=bg)
+    return d_grid.cpu().numpy(), d_sh.cpu().numpy(), og, osh, mag
 
 
 @pytest.mark.parametrize("K", [1, 2, 3])
@@ -42,9 +42,9 @@ def test_tiny_gradients(K, seed):
     cam = synth.orbit_camera(seed + 3, 48, 40, distance=1.7)
     bg = (0.1, 0.2, 0.3) if seed else (0.0, 0.0, 0.0)
     ref = oracle.render(sc, cam, K=K, t_stop=1e-4, bg=bg)
-    dg, ds, og, osh = _grads(sc, cam, K, 1e-4, bg, seed, ref["near_stop"])
-    compare_grads(dg, og, name="grid")
-    compare_grads(ds, osh, name="sh")
+    dg, ds, og, osh, mag = _grads(sc, cam, K, 1e-4, bg, seed, ref["near_stop"])
+    compare_grads(dg, og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds, osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
 
 
 @pytest.mark.parametrize("K", [1, 3])
@@ -52,9 +52,9 @@ def test_dense_level5_gradients(K):
     sc = cached("dense5", lambda: synth.dense_scene(5, seed=0))
     cam = synth.dense_view_camera()
     ref = cached(("dense5_ref", K), lambda: oracle.render(sc, cam, K=K, t_stop=1e-4))
-    dg, ds, og, osh = _grads(sc, cam, K, 1e-4, (0.0, 0.0, 0.0), 5, ref["near_stop"])
-    compare_grads(dg, og, name="grid")
-    compare_grads(ds, osh, name="sh")
+    dg, ds, og, osh, mag = _grads(sc, cam, K, 1e-4, (0.0, 0.0, 0.0), 5, ref["near_stop"])
+    compare_grads(dg, og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds, osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
 
 
 def test_terminated_pixels_gradients():
@@ -64,9 +64,9 @@ def test_terminated_pixels_gradients():
     cam = synth.orbit_camera(6, 40, 40, distance=1.6)
     ref = oracle.render(sc, cam, K=3, t_stop=1e-3)
     assert (ref["term_vox"] >= 0).mean() > 0.2
-    dg, ds, og, osh = _grads(sc, cam, 3, 1e-3, (0.0, 0.0, 0.0), 2, ref["near_stop"])
-    compare_grads(dg, og, name="grid")
-    compare_grads(ds, osh, name="sh")
+    dg, ds, og, osh, mag = _grads(sc, cam, 3, 1e-3, (0.0, 0.0, 0.0), 2, ref["near_stop"])
+    compare_grads(dg, og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds, osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
 
 
 def test_underflowing_transmittance_takes_front_to_back_phase():
@@ -81,10 +81,10 @@ def test_underflowing_transmittance_takes_front_to_back_phase():
     fr, out, _ = run_gpu(sc, cam, K=2, t_stop=0.0, inspect=False)
     T = to_np(out)["T_final"]
     assert (T < 1e-30).mean() > 0.05
-    dg, ds, og, osh = _grads(sc, cam, 2, 0.0, (0.2, 0.2, 0.2), 4)
+    dg, ds, og, osh, mag = _grads(sc, cam, 2, 0.0, (0.2, 0.2, 0.2), 4)
     assert np.isfinite(dg).all() and np.isfinite(ds).all()
-    compare_grads(dg, og, name="grid")
-    compare_grads(ds, osh, name="sh")
+    compare_grads(dg, og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds, osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
 
 
 def test_l2_loss_kernel():
@@ -106,7 +106,9 @@ def test_l2_loss_kernel():
 
 def test_autograd_matches_frame_backward_and_l2_loss():
     """rasterize() under autograd: an L2 loss against a target rendered from
-    perturbed densities; gradients equal the oracle's for the same loss."""
+    perturbed densities.  The gradients equal the oracle's for the upstream
+    gradient this loss hands the backward (2 (C - C*) / n of the rendered
+    images), and, through the oracle's own images, for the whole loss."""
     import torch
     from paper_2412_04459_gb300 import DeviceScene, rasterize
     sc = synth.random_octree_scene(51, max_level=4, p_split=0.5, max_cells=64,
@@ -122,12 +124,49 @@ def test_autograd_matches_frame_backward_and_l2_loss():
     rgb, depth, alpha = rasterize(grid, sh, dev, cam, K=3)
     loss = ((rgb - target) ** 2).mean()
     loss.backward()
-    # same loss through the oracle: dL/dC = 2 (C - C*) / (3 H W)
+    zeros = np.zeros((cam.height, cam.width))
+    # the backward for the upstream gradient the loss produced
+    g_up = (2.0 * (rgb.detach() - target) / rgb.numel()).cpu().numpy().astype(np.float64)
+    og, osh, mag = oracle_grads(sc, cam, g_up, zeros, zeros, K=3)
+    compare_grads(grid.grad.cpu().numpy(), og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(sh.grad.cpu().numpy(), osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
+    # the whole loss through the oracle: dL/dC = 2 (C - C*) / (3 H W)
     ref = oracle.render(sc, cam, K=3)
     tgt = oracle.render(sc, cam, K=3, grid=target_grid.cpu().numpy().astype(np.float64))
+    assert not ref["near_stop"].any() and not tgt["near_stop"].any()
     g_rgb = 2.0 * (ref["rgb"] - tgt["rgb"]) / ref["rgb"].size
-    zeros = np.zeros((cam.height, cam.width))
-    og, osh = oracle.render_grad(sc, cam, g_rgb, zeros, zeros, K=3)
-    compare_grads(grid.grad.cpu().numpy(), og, rel=2e-3, name="grid")
-    compare_grads(sh.grad.cpu().numpy(), osh, rel=2e-3, name="sh")
+    og, osh, mag = oracle_grads(sc, cam, g_rgb, zeros, zeros, K=3)
+    compare_grads(grid.grad.cpu().numpy(), og, name="grid (oracle images)", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(sh.grad.cpu().numpy(), osh, name="sh (oracle images)", mag=(mag["sh"], mag["sh_seg"]))
     assert abs(loss.item() - float(((ref["rgb"] - tgt["rgb"]) ** 2).mean())) < 1e-6
+
+
+def test_autograd_with_expanded_upstream_gradients():
+    """rgb.sum() + depth.sum() + alpha.sum() hands the backward expanded
+    (stride-0) gradients for all three images, which the front end copies to
+    contiguous buffers; the result equals the backward of the same loss given
+    contiguous ones-tensors."""
+    import torch
+    from paper_2412_04459_gb300 import DeviceScene, Frame, rasterize
+    sc = synth.random_octree_scene(53, max_level=4, p_split=0.5, max_cells=64,
+                                   grid_fn=synth.normal_grid(1.5, 1.0))
+    cam = synth.orbit_camera(12, 48, 40, distance=1.7)
+    dev = DeviceScene.from_host(sc)
+    grid = dev.grid.clone().requires_grad_(True)
+    sh = dev.sh.clone().requires_grad_(True)
+    for _ in range(2):              # the second pass reuses the allocator's freed blocks
+        grid.grad = None
+        sh.grad = None
+        rgb, depth, alpha = rasterize(grid, sh, dev, cam, K=2)
+        (rgb.sum() + depth.sum() + alpha.sum()).backward()
+    fr = Frame(dev, cam, K=2)
+    out = fr.render()
+    ones = lambda *s: torch.ones(*s, device="cuda")
+    dg, ds = fr.backward(ones(3, cam.height, cam.width), ones(cam.height, cam.width),
+                         ones(cam.height, cam.width), out)
+    assert torch.allclose(grid.grad, dg, rtol=1e-5, atol=1e-6 * float(dg.abs().max()))
+    assert torch.allclose(sh.grad, ds, rtol=1e-5, atol=1e-6 * float(ds.abs().max()))
+    g = np.ones((3, cam.height, cam.width))
+    og, osh, mag = oracle_grads(sc, cam, g, g[0], g[0], K=2)
+    compare_grads(dg.cpu().numpy(), og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds.cpu().numpy(), osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))

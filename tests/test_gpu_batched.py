@@ -10,7 +10,7 @@ import oracle
 import synth
 from oracle import binning
 from tests.conftest import cached
-from tests.gpu_common import compare_images, compare_integers, require_gpu, run_gpu, to_np
+from tests.gpu_common import compare_images, compare_integers, compare_reordered, require_gpu, run_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -90,9 +90,10 @@ def test_batched_backward_sums_single_views():
         dg, ds = single.backward(t(grads[v][0]), t(grads[v][1]), t(grads[v][2]), o1)
         dg_s += dg
         ds_s += ds
-    for a, b in ((dg_b, dg_s), (ds_b, ds_s)):
+    for a, b, name in ((dg_b, dg_s, "grid"), (ds_b, ds_s, "sh")):
         a, b = a.cpu().numpy(), b.cpu().numpy()
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+        compare_reordered(a, b, name)
 
 
 def test_batched_beyond_single_view_tile_limit():
@@ -163,6 +164,8 @@ def test_graph_replay_of_batched_step():
         assert torch.equal(got[k], ref[k]), k
     assert torch.linalg.norm(got_dg - dg2) <= 1e-5 * torch.linalg.norm(dg2)
     assert torch.linalg.norm(got_ds - ds2) <= 1e-5 * torch.linalg.norm(ds2)
+    compare_reordered(got_dg.cpu().numpy(), dg2.cpu().numpy(), "grid")
+    compare_reordered(got_ds.cpu().numpy(), ds2.cpu().numpy(), "sh")
     flags, _ = fr.status()
     assert flags == 0
 
@@ -199,6 +202,8 @@ def test_batched_renderer_partitions_equal_views(partitions, tmp_path, monkeypat
         g1, s1 = fr.backward(r.grads[0][3 * a:3 * b], r.grads[1][a:b], r.grads[2][a:b], o)
         dg += g1
         ds += s1
-    # sums over views in another order: compare as relative L2 error
+    # sums over views in another order
     assert torch.linalg.norm(r.d_grid - dg) <= 1e-5 * torch.linalg.norm(dg)
     assert torch.linalg.norm(r.d_sh - ds) <= 1e-5 * torch.linalg.norm(ds)
+    compare_reordered(r.d_grid.cpu().numpy(), dg.cpu().numpy(), "grid")
+    compare_reordered(r.d_sh.cpu().numpy(), ds.cpu().numpy(), "sh")

@@ -9,7 +9,8 @@ import pytest
 import oracle
 import synth
 from tests.conftest import cached
-from tests.gpu_common import compare_grads, compare_images, compare_integers, require_gpu, run_gpu, to_np
+from tests.gpu_common import (compare_grads, compare_images, compare_integers, oracle_grads, require_gpu,
+                              run_gpu, to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +70,7 @@ def test_gradients_full_size_sampled(shell):
     g_a[rnd[:, 1], rnd[:, 0]] = vals[:, 4]
     t = lambda a: torch.as_tensor(a, device="cuda")
     d_grid, d_sh = fr.backward(t(g_rgb), t(g_d), t(g_a), out)
-    og, osh = oracle.render_grad(scene, cam, vals[:, :3].astype(np.float64), vals[:, 3], vals[:, 4],
-                                 K=3, t_stop=1e-4, pixels=rnd)
-    compare_grads(d_grid.cpu().numpy(), og, name="grid")
-    compare_grads(d_sh.cpu().numpy(), osh, name="sh")
+    og, osh, mag = oracle_grads(scene, cam, vals[:, :3].astype(np.float64), vals[:, 3], vals[:, 4],
+                                K=3, t_stop=1e-4, pixels=rnd)
+    compare_grads(d_grid.cpu().numpy(), og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(d_sh.cpu().numpy(), osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))

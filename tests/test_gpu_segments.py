@@ -8,7 +8,7 @@ import pytest
 import oracle
 import synth
 from tests.conftest import cached
-from tests.gpu_common import compare_grads, compare_images, require_gpu, run_gpu, to_np
+from tests.gpu_common import compare_grads, compare_images, oracle_grads, require_gpu, run_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -61,9 +61,9 @@ def test_stop_inside_later_segments(K):
     g_rgb, g_d, g_a = g_rgb * keep[None], g_d * keep, g_a * keep
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     dg, ds = fr.backward(t(g_rgb), t(g_d), t(g_a), out)
-    og, osh = oracle.render_grad(sc, cam, g_rgb.astype(np.float64), g_d, g_a, K=K, t_stop=1e-3)
-    compare_grads(dg.cpu().numpy(), og, name="grid")
-    compare_grads(ds.cpu().numpy(), osh, name="sh")
+    og, osh, mag = oracle_grads(sc, cam, g_rgb.astype(np.float64), g_d, g_a, K=K, t_stop=1e-3)
+    compare_grads(dg.cpu().numpy(), og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds.cpu().numpy(), osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
 
 
 def test_underflow_inside_later_segments():
@@ -83,9 +83,9 @@ def test_underflow_inside_later_segments():
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     dg, ds = fr.backward(t(g_rgb), t(g_d), t(g_a), out)
     assert np.isfinite(dg.cpu().numpy()).all() and np.isfinite(ds.cpu().numpy()).all()
-    og, osh = oracle.render_grad(sc, cam, g_rgb.astype(np.float64), g_d, g_a, K=2, t_stop=0.0)
-    compare_grads(dg.cpu().numpy(), og, name="grid")
-    compare_grads(ds.cpu().numpy(), osh, name="sh")
+    og, osh, mag = oracle_grads(sc, cam, g_rgb.astype(np.float64), g_d, g_a, K=2, t_stop=0.0)
+    compare_grads(dg.cpu().numpy(), og, name="grid", mag=(mag["grid"], mag["grid_seg"]))
+    compare_grads(ds.cpu().numpy(), osh, name="sh", mag=(mag["sh"], mag["sh_seg"]))
 
 
 def test_work_counts_across_segments():

@@ -15,7 +15,8 @@ from tests.gpu_common import IMG_TOL, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _static_render(scene_dev, cam, K, t_stop, bg):
+def _static_call(scene_dev, cam, K, t_stop, bg, tile=16):
+    """(return code, outputs as numpy, pair count) of one call."""
     import torch
     from paper_2412_04459_gb300 import _native as N
     from paper_2412_04459_gb300.raster import camera_struct, params_struct
@@ -25,15 +26,21 @@ def _static_render(scene_dev, cam, K, t_stop, bg):
                last=torch.empty(H, W, dtype=torch.int32, device="cuda"))
     sc = scene_dev.struct()
     c = camera_struct(cam)
-    p = params_struct(K, t_stop, 16, bg)
+    p = params_struct(K, t_stop, tile, bg)
     n = ctypes.c_int64(-1)
     ptr = lambda t: ctypes.c_void_p(t.data_ptr())
     rc = N.lib().svr_render_fwd_static(N.ref(sc), N.ref(c), N.ref(p), ptr(out["rgb"]), ptr(out["depth"]),
                                         ptr(out["alpha"]), ptr(out["T_final"]), ptr(out["last"]), N.ref(n),
                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    N.check(rc, "svr_render_fwd_static")
     torch.cuda.synchronize()
-    return {k: v.cpu().numpy() for k, v in out.items()}, n.value
+    return rc, {k: v.cpu().numpy() for k, v in out.items()}, n.value
+
+
+def _static_render(scene_dev, cam, K, t_stop, bg):
+    from paper_2412_04459_gb300 import _native as N
+    rc, out, n = _static_call(scene_dev, cam, K, t_stop, bg)
+    N.check(rc, "svr_render_fwd_static")
+    return out, n
 
 
 def _regular_render(scene_dev, cam, K, t_stop, bg):
@@ -70,3 +77,36 @@ def test_static_workspace_rejects_oversized_scenes():
         _static_render(dev, synth.dense_view_camera(), 1, 1e-4, (0.0, 0.0, 0.0))
     assert e.value.code == N.SVR_ERR_LIMIT
     assert "65536" in str(e.value)
+
+
+def test_static_workspace_reports_pair_overflow():
+    """32,768 voxels (within the voxel limit) filling a 1280x840 view make
+    more pairs than fit in the array: the call returns SVR_ERR_CAPACITY,
+    skips the render, and reports the true pair count, which equals the
+    regular path's."""
+    require_gpu()
+    from paper_2412_04459_gb300 import DeviceScene, _native as N
+    scene = synth.dense_scene(5, seed=1)
+    cam = synth.orbit_camera(3, 1280, 840, distance=1.2)
+    dev = DeviceScene.from_host(scene)
+    rc, _, n_static = _static_call(dev, cam, 1, 1e-4, (0.0, 0.0, 0.0))
+    assert rc == N.SVR_ERR_CAPACITY
+    _, n_regular = _regular_render(dev, cam, 1, 1e-4, (0.0, 0.0, 0.0))
+    assert n_static == n_regular > 0
+    # the array still serves a call that fits, right after the overflow
+    small = synth.dense_view_camera(96, 80)
+    got, _ = _static_render(dev, small, 1, 1e-4, (0.0, 0.0, 0.0))
+    ref, _ = _regular_render(dev, small, 1, 1e-4, (0.0, 0.0, 0.0))
+    assert np.abs(got["rgb"] - ref["rgb"]).max() <= IMG_TOL
+
+
+def test_static_workspace_rejects_too_many_tiles():
+    """An image of more than 2^16 tiles is reported as the tile limit."""
+    require_gpu()
+    from paper_2412_04459_gb300 import DeviceScene, _native as N
+    dev = DeviceScene.from_host(synth.dense_scene(2, seed=0))
+    cam = synth.orbit_camera(0, 4200, 4200)          # 263 x 263 tiles of 16 pixels
+    with pytest.raises(N.SvrError) as e:
+        _static_render(dev, cam, 1, 1e-4, (0.0, 0.0, 0.0))
+    assert e.value.code == N.SVR_ERR_LIMIT
+    assert "tiles" in str(e.value)

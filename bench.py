@@ -43,10 +43,12 @@ OPS_CAND = 12                         # slab test of one candidate entry
 OPS_HIT = {1: 42, 2: 71, 3: 100}      # one composited segment (forward)
 OPS_HIT_BWD = {1: 98, 2: 156, 3: 214}  # one segment in the backward (recompute + gradient)
 BATCH_SIZES = ((640, 480), (1280, 840), (1920, 1080))
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_render_bwd<3> launch of
-# this workload, from the ncu capture summarised in profiles/render_bwd_shell1m.md
-# (to be retaken, or set to None, whenever that kernel changes)
-BWD_TRAFFIC_BYTES = 321_802_496
+# The DRAM traffic of the dominant kernel comes from an ncu capture recorded
+# in its profile summary as one line
+#   traffic: kernel=<name> bytes_per_launch=<n> source_sha1=<sha1 of the kernel's sources>
+# and is reported only while the kernel's sources still hash to that value.
+KERNEL_SOURCES = ("paper_2412_04459_gb300/csrc/render.cu", "paper_2412_04459_gb300/csrc/svr_internal.cuh")
+TRAFFIC_RECORD = "profiles/render_bwd_shell1m.md"
 
 
 def parse():
@@ -309,6 +311,7 @@ def run_native(args, rank, world, local_rank):
     hbm = (peaks or {}).get("hbm_gbs", 6800.0)
     frame_bytes = frame_algorithmic_bytes(scene, P, H, W)
     n_launch = launches_per_step(fr)
+    traffic, traffic_from = recorded_traffic(f"k_render_bwd<{K}>")
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -318,7 +321,8 @@ def run_native(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world} (one view per rank)"},
         "fwd_frames_per_s": fwd_fps, "ms_fwd": ms_fwd, "ms_per_call": per_call,
         "roofline": {"bound": "alu", "kernel": "k_render_bwd", "achieved": achieved_bwd, "peak": alu_peak,
-                     "unit": "T FP32 lane-ops/s", "frac": achieved_bwd / alu_peak, "traffic": BWD_TRAFFIC_BYTES,
+                     "unit": "T FP32 lane-ops/s", "frac": achieved_bwd / alu_peak, "traffic": traffic,
+                     "traffic_from": traffic_from,
                      "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
                               "ops_per_hit": OPS_HIT_BWD[K]},
                      "timed": "svr_render_bwd call: k_render_bwd + k_voxel_bwd + 2 memsets",
@@ -641,6 +645,34 @@ def launches_per_step(fr):
     preprocess, 2 tile-count scan kernels, work order, emission, chunk sort,
     run merge, block lists, forward, backward, voxel backward."""
     return 2 + 2 + 1 + 1 + 2 + 1 + 1 + 2
+
+
+def sources_sha1(paths=KERNEL_SOURCES):
+    import hashlib
+    h = hashlib.sha1()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, record=TRAFFIC_RECORD):
+    """(bytes per launch, note) of `kernel` from its profile summary's traffic
+    line, or (None, why) if there is none or the sources changed since."""
+    path = os.path.join(ROOT, record)
+    if not os.path.exists(path):
+        return None, "no ncu record"
+    for line in open(path):
+        line = line.strip()
+        if not line.startswith("traffic:"):
+            continue
+        kv = dict(x.split("=", 1) for x in line[len("traffic:"):].split())
+        if kv.get("kernel") != kernel:
+            continue
+        if kv.get("source_sha1") != sources_sha1():
+            return None, "kernel sources changed since the ncu capture"
+        return int(kv["bytes_per_launch"]), f"ncu capture recorded in {record}"
+    return None, "no ncu record for this kernel"
 
 
 def load_peaks():

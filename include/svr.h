@@ -290,15 +290,19 @@ SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, f
  * (with a pair count) + svr_render_fwd, but the scratch memory is one 16 MiB
  * array compiled into the library, which every GPU that loads the library
  * keeps until the process exits.
- * Limits: at most 65536 voxels, and as many pairs as fit in the array next to
- * the voxel buffers; beyond them the call returns SVR_ERR_LIMIT (voxels or
- * image) or SVR_ERR_CAPACITY (pairs; *n_pairs_out then holds the count).
+ * Limits: at most 65536 voxels, at most 2^16 tiles, and as many pairs as fit
+ * in the array next to the voxel buffers; beyond them the call returns
+ * SVR_ERR_LIMIT (voxels, tiles or image) or SVR_ERR_CAPACITY (pairs; the
+ * render is skipped and *n_pairs_out holds the true count).
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  The call synchronises the stream (to read the pair count).  All
- * calls share the array and each leaves its contents behind (everything that
- * must start at zero is cleared by the call); calls whose GPU work overlaps
- * race on the array.  Outputs as for svr_render_fwd; n_pairs_out may be NULL.
+ * device, with that device current) and keeps it for the life of the
+ * process: do not use the library across a cudaDeviceReset.  Every call
+ * synchronises the stream (it reads the pair count back, like svr_bin_sort
+ * with a count), so it cannot be called while the stream is being captured
+ * into a CUDA graph.  All calls share the array and each leaves its contents
+ * behind (everything that must start at zero is cleared by the call); calls
+ * whose GPU work overlaps race on the array.  Outputs as for svr_render_fwd;
+ * n_pairs_out may be NULL.
  */
 SVR_API int svr_render_fwd_static(const svr_scene *scene, const svr_camera *cam,
                                   const svr_params *params, float *rgb, float *depth,

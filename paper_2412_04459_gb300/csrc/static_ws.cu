@@ -34,7 +34,9 @@ void *g_static_ptr[kMaxDevices] = {};
 
 // Device address of g_static_ws on the current device.  The host-side name
 // of the array is only a stand-in: it must not be passed to a kernel.  The
-// address is looked up once per device, with that device current.
+// address is looked up once per device, with that device current, and kept
+// for the life of the process (a device reset would invalidate it: the
+// library is not to be used across cudaDeviceReset).
 int static_workspace(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -62,6 +64,17 @@ SVR_API int svr_render_fwd_static(const svr_scene *scene, const svr_camera *cam,
     if (scene->n_vox < 0 || scene->n_vox > kStaticMaxVoxels)
         return svr::set_error(SVR_ERR_LIMIT, "static workspace: %lld voxels, at most %lld",
                               (long long)scene->n_vox, (long long)kStaticMaxVoxels);
+    // the image's tile count first, so that an oversized image is reported as
+    // the limit it breaks (svr_workspace_size returns 0 for it)
+    if (params->tile == 8 || params->tile == 16 || params->tile == 32) {
+        if (cam->width > 0 && cam->height > 0) {
+            const int64_t tiles = (int64_t)((cam->width + params->tile - 1) / params->tile) *
+                                  ((cam->height + params->tile - 1) / params->tile);
+            if (tiles > 65536)
+                return svr::set_error(SVR_ERR_LIMIT, "static workspace: %lld tiles > 2^16 (the key's 16-bit tile id)",
+                                      (long long)tiles);
+        }
+    }
     const size_t base = svr_workspace_size(scene->n_vox, 0, cam, params);
     if (base == 0) return svr::set_error(SVR_ERR_INVALID, "invalid camera or params");
     if (base > kStaticWorkspaceBytes)

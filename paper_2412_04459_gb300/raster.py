@@ -232,10 +232,14 @@ class Frame:
             d_grid = torch.zeros(self.grid.shape[0], device=dev)
         if d_sh is None:
             d_sh = torch.empty(self.scene.n_vox, 48, device=dev)
-        c = lambda t: None if t is None else t.contiguous()
-        N.check(N.lib().svr_render_bwd(N.ref(self.frame), _ptr(c(g_rgb)), _ptr(c(g_depth)),
-                                       _ptr(c(g_alpha)), _ptr(out["T_final"]), _ptr(out["last"]),
-                                       _ptr(d_grid), _ptr(d_sh), _stream(stream)), "svr_render_bwd")
+        # contiguous copies (of expanded or strided gradients) are held by
+        # these names until the call has been enqueued on the stream, so the
+        # caching allocator cannot hand one copy's block to the next
+        gr, gd, ga = (None if t is None else t.contiguous() for t in (g_rgb, g_depth, g_alpha))
+        N.check(N.lib().svr_render_bwd(N.ref(self.frame), _ptr(gr), _ptr(gd), _ptr(ga), _ptr(out["T_final"]),
+                                       _ptr(out["last"]), _ptr(d_grid), _ptr(d_sh), _stream(stream)),
+                "svr_render_bwd")
+        del gr, gd, ga
         return d_grid, d_sh
 
     def render_batched(self, out, grads=None, d_grid=None, d_sh=None, stream=None):

@@ -6,7 +6,9 @@ CUDA library and never imports it; the two meet only through the seeded
 inputs of the ``synth`` package.
 
 * ``oracle.render`` / ``oracle.render_grad``: brute-force renderer and its
-  analytic gradient (plain C in svr_oracle.c, FP64, OpenMP over pixels).
+  analytic gradient (plain C in svr_oracle.c, FP64, OpenMP over pixels),
+  with the optional normal modality (Eq. vox_normal) and the pruning and
+  subdivision statistics (Sec. 3.2.2).
 * ``oracle.morton``: Morton codes and the direction-dependent order (Sec. B).
 * ``oracle.binning``: pixel rays, tile sign masks, tile rectangles, the
   sorting keys/values, their sort order and the per-tile ranges (Sec. 3.1.2,
@@ -71,6 +73,16 @@ def lib():
         L.oc_render_grad.restype = ctypes.c_int
         L.oc_render_grad.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P,
                                      ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+        L.oc_render_ex.restype = ctypes.c_int
+        L.oc_render_ex.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P,
+                                   ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+        L.oc_render_grad_ex.restype = ctypes.c_int
+        L.oc_render_grad_ex.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P,
+                                        ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+        L.oc_trilinear.restype = ctypes.c_double
+        L.oc_trilinear.argtypes = [P, P]
+        L.oc_interp_grad_centre.restype = None
+        L.oc_interp_grad_centre.argtypes = [P, P]
         L.oc_ray_hits.restype = ctypes.c_int64
         L.oc_ray_hits.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, ctypes.c_int64,
                                   P, P, P]
@@ -132,7 +144,7 @@ def _pixels(cam, pixels):
 
 
 def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, threads=None,
-           grid=None, sh=None, near_stop_rel=None):
+           grid=None, sh=None, near_stop_rel=None, normals=False, max_weight=None):
     """Brute-force FP64 render.  pixels: int [n, 2] of (x, y), or None for the
     whole image (outputs then reshaped to [H, W]).  grid / sh: optional FP64
     overrides of the scene's parameters (finite differences).
@@ -142,19 +154,30 @@ def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, thread
     |T / t_stop - 1| after a composited voxel: how close the walk came to a
     different termination decision) and near_stop = stop_margin <
     near_stop_rel (default NEAR_STOP_REL), the pixels whose termination an
-    FP32 renderer may legitimately decide the other way."""
+    FP32 renderer may legitimately decide the other way.
+
+    normals=True adds "normal" ([3, H, W] or [n, 3]): the composited voxel
+    normals of Eq. (vox_normal).  max_weight: an FP64 array [N] that is raised
+    to each voxel's largest blending weight T_i alpha_i over these pixels
+    (pruning statistic, Sec. 3.2.2)."""
     centre, level, corner, g, s = _scene_arrays(scene, grid, sh)
     n, px = _pixels(cam, pixels)
     out = dict(rgb=np.zeros((n, 3)), depth=np.zeros(n), alpha=np.zeros(n), t_final=np.zeros(n),
                n_comp=np.zeros(n, np.int32), term_vox=np.zeros(n, np.int64),
                stop_margin=np.zeros(n))
+    if normals:
+        out["normal"] = np.zeros((n, 3))
+    if max_weight is not None:
+        assert max_weight.dtype == np.float64 and max_weight.shape == (scene.n_vox,)
+        assert max_weight.flags.c_contiguous
     c = camera_struct(cam)
     p = params_struct(K, t_stop, bg)
-    rc = lib().oc_render(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre), _ptr(level),
-                         _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c), ctypes.byref(p), n,
-                         _ptr(px), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]),
-                         _ptr(out["t_final"]), _ptr(out["n_comp"]), _ptr(out["term_vox"]),
-                         _ptr(out["stop_margin"]), _threads(threads))
+    rc = lib().oc_render_ex(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre), _ptr(level),
+                            _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c), ctypes.byref(p), n,
+                            _ptr(px), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]),
+                            _ptr(out["t_final"]), _ptr(out["n_comp"]), _ptr(out["term_vox"]),
+                            _ptr(out["stop_margin"]), _ptr(out.get("normal")), _ptr(max_weight),
+                            _threads(threads))
     if rc != 0:
         raise RuntimeError(f"oc_render failed ({rc})")
     band = NEAR_STOP_REL if near_stop_rel is None else float(near_stop_rel)
@@ -162,13 +185,16 @@ def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, thread
     if pixels is None:
         H, W = cam.height, cam.width
         out["rgb"] = out["rgb"].reshape(H, W, 3).transpose(2, 0, 1).copy()
+        if normals:
+            out["normal"] = out["normal"].reshape(H, W, 3).transpose(2, 0, 1).copy()
         for k in ("depth", "alpha", "t_final", "n_comp", "term_vox", "stop_margin", "near_stop"):
             out[k] = out[k].reshape(H, W)
     return out
 
 
 def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0),
-                pixels=None, threads=None, grid=None, sh=None, magnitudes=None):
+                pixels=None, threads=None, grid=None, sh=None, magnitudes=None, g_normal=None,
+                priority=None):
     """Analytic FP64 gradient of sum(g_rgb*C + g_depth*D + g_alpha*A).
     Full image: g_rgb [3, H, W], g_depth/g_alpha [H, W]; pixel list: g_rgb
     [n, 3], g_depth/g_alpha [n].  Returns (d_grid [Pts], d_sh [N, 48]).
@@ -180,11 +206,25 @@ def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 
     plane coordinates, the ray origin and the direction components:
     ((|P_i| + |o_i|) / |d_i| + |a| + (|Q_j| + |o_j|) / |d_j| + |b|) / (b - a),
     i and j the axes of the entry plane P and the exit plane Q (large for a
-    ray that grazes the voxel)."""
+    ray that grazes the voxel).
+
+    g_normal ([3, H, W] or [n, 3]) adds g_normal . N to the objective (the
+    normal image of Eq. vox_normal).  priority: an FP64 array [N] to which
+    each voxel's subdivision priority sum |alpha_i dL/dalpha_i| over these
+    pixels is added (Eq. priority, Sec. 3.2.2)."""
     centre, level, corner, g, s = _scene_arrays(scene, grid, sh)
     n, px = _pixels(cam, pixels)
     if pixels is None:
         g_rgb = np.asarray(g_rgb, np.float64).reshape(3, -1).T
+    gn = None
+    if g_normal is not None:
+        gn = np.asarray(g_normal, np.float64)
+        if pixels is None:
+            gn = gn.reshape(3, -1).T
+        gn = np.ascontiguousarray(gn, np.float64).reshape(n, 3)
+    if priority is not None:
+        assert priority.dtype == np.float64 and priority.shape == (scene.n_vox,)
+        assert priority.flags.c_contiguous
     gr = np.ascontiguousarray(g_rgb, np.float64).reshape(n, 3)
     gd = np.ascontiguousarray(g_depth, np.float64).reshape(n)
     ga = np.ascontiguousarray(g_alpha, np.float64).reshape(n)
@@ -195,16 +235,28 @@ def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 
     k_grid, k_sh = (np.zeros(len(g)), np.zeros((scene.n_vox, 48))) if want else (None, None)
     c = camera_struct(cam)
     p = params_struct(K, t_stop, bg)
-    rc = lib().oc_render_grad(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre),
-                              _ptr(level), _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c),
-                              ctypes.byref(p), n, _ptr(px), _ptr(gr), _ptr(gd), _ptr(ga),
-                              _ptr(d_grid), _ptr(d_sh), _ptr(a_grid), _ptr(a_sh), _ptr(k_grid), _ptr(k_sh),
-                              _threads(threads))
+    rc = lib().oc_render_grad_ex(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre),
+                                 _ptr(level), _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c),
+                                 ctypes.byref(p), n, _ptr(px), _ptr(gr), _ptr(gd), _ptr(ga), _ptr(gn),
+                                 _ptr(d_grid), _ptr(d_sh), _ptr(a_grid), _ptr(a_sh), _ptr(k_grid), _ptr(k_sh),
+                                 _ptr(priority), _threads(threads))
     if rc != 0:
         raise RuntimeError(f"oc_render_grad failed ({rc})")
     if magnitudes is not None:
         magnitudes.update(grid=a_grid, sh=a_sh, grid_seg=k_grid, sh_seg=k_sh)
     return d_grid, d_sh
+
+
+def trilinear(V, q) -> float:
+    """Trilinear interpolation of Eq. (interp) of 8 corner values at q."""
+    return lib().oc_trilinear(_ptr(np.ascontiguousarray(V, np.float64)), _ptr(np.ascontiguousarray(q, np.float64)))
+
+
+def interp_grad_centre(V) -> np.ndarray:
+    """Gradient of the trilinear field at the voxel centre, Eq. (interp_grad)."""
+    g = np.zeros(3)
+    lib().oc_interp_grad_centre(_ptr(np.ascontiguousarray(V, np.float64)), _ptr(g))
+    return g
 
 
 def explin(x: float) -> float:

@@ -23,7 +23,14 @@
  *   - the analytic gradient of sum(g_rgb * C + g_depth * D + g_alpha * A)
  *     with respect to the raw grid-point densities and the SH coefficients
  *     (Sec. A.2 alpha gradient, Sec. A.4 depth gradient), written in the
- *     alpha form with suffix sums.
+ *     alpha form with suffix sums;
+ *   - on request (the _ex entry points): the normal image N = sum_i T_i
+ *     alpha_i n_i with the voxel normal n of Eq. (vox_normal), the
+ *     normalised gradient of the trilinear density field at the voxel
+ *     centre in the closed form of Eq. (interp_grad), and its gradient
+ *     (Eq. interp_grad_grad through the normalisation); per voxel the
+ *     maximum blending weight max T_i alpha_i (pruning, Sec. 3.2.2) and the
+ *     subdivision priority sum |alpha_i dL/dalpha_i| (Eq. priority).
  *
  * Voxel geometry: size v_s = w_s 2^-l (Eq. vox_coord); the centre is the
  * caller's value (the lattice check lives in the Python part of the oracle).
@@ -197,6 +204,52 @@ static void trilinear_weights(const double q[3], double w[8]) {
     }
 }
 
+/* Trilinear interpolation of Eq. (interp) of 8 corner values at q. */
+double oc_trilinear(const double V[8], const double q[3]) {
+    double w[8], acc = 0.0;
+    trilinear_weights(q, w);
+    for (int c = 0; c < 8; ++c) acc += w[c] * V[c];
+    return acc;
+}
+
+/* Gradient of the trilinear field with respect to the local coordinate at
+ * the voxel centre q = (0.5, 0.5, 0.5), Eq. (interp_grad): along each axis a
+ * quarter of (sum of the four corners on the far face) - (sum of the four on
+ * the near face); corner c has bit 2 = x, bit 1 = y, bit 0 = z. */
+void oc_interp_grad_centre(const double V[8], double g[3]) {
+    for (int ax = 0; ax < 3; ++ax) {
+        const int bit = 2 - ax;
+        double far = 0.0, near = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            if ((c >> bit) & 1) far += V[c];
+            else near += V[c];
+        }
+        g[ax] = 0.25 * (far - near);
+    }
+}
+
+/* Voxel normal of Eq. (vox_normal): normalize(gradient at the centre); the
+ * zero vector where the gradient vanishes.  Also returns the gradient. */
+static void voxel_normal(const oc_scene *S, int64_t v, double n[3], double g[3]) {
+    const int32_t *ci = S->corner_idx + 8 * v;
+    double V[8];
+    for (int c = 0; c < 8; ++c) V[c] = S->grid[ci[c]];
+    oc_interp_grad_centre(V, g);
+    double len = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    for (int ax = 0; ax < 3; ++ax) n[ax] = len > 0.0 ? g[ax] / len : 0.0;
+}
+
+/* max(*p, x) stored atomically, for x >= 0 (non-negative doubles order like
+ * their bit patterns). */
+static void atomic_max_nonneg(double *p, double x) {
+    int64_t *q = (int64_t *)p;
+    int64_t want;
+    memcpy(&want, &x, sizeof(want));
+    int64_t cur = __atomic_load_n(q, __ATOMIC_RELAXED);
+    while (cur < want && !__atomic_compare_exchange_n(q, &cur, want, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+    }
+}
+
 /* -------------------------------------------------------------- per pixel */
 
 typedef struct {
@@ -218,11 +271,14 @@ typedef struct {
     int64_t cap;
     /* per composited hit */
     double *alpha, *T, *d, *col, *pre, *ell;
+    double *nrm;   /* [3] voxel normal n of each hit, when normals are rendered */
+    double *gvec;  /* [3] unnormalised gradient of Eq. (interp_grad) of each hit */
     int64_t pcap;
 } oc_scratch;
 
 static void scratch_free(oc_scratch *s) {
     free(s->hits); free(s->alpha); free(s->T); free(s->d); free(s->col); free(s->pre); free(s->ell);
+    free(s->nrm); free(s->gvec);
     memset(s, 0, sizeof(*s));
 }
 
@@ -253,6 +309,12 @@ static int scratch_comp(oc_scratch *s, int64_t n) {
     p = (double *)realloc(s->pre, (size_t)c * 3 * sizeof(double));
     if (!p) return -1;
     s->pre = p;
+    p = (double *)realloc(s->nrm, (size_t)c * 3 * sizeof(double));
+    if (!p) return -1;
+    s->nrm = p;
+    p = (double *)realloc(s->gvec, (size_t)c * 3 * sizeof(double));
+    if (!p) return -1;
+    s->gvec = p;
     s->pcap = c;
     return 0;
 }
@@ -317,6 +379,7 @@ static void voxel_colour(const oc_scene *S, int64_t v, const double ro[3], doubl
 
 typedef struct {
     double rgb[3], depth, alpha, t_final;
+    double normal[3];  /* N = sum_i T_i alpha_i n_i (when normals are rendered) */
     int32_t n_comp;
     int64_t term_vox;  /* voxel whose compositing stopped the ray, or -1 */
     double stop_margin; /* min over composited voxels of |T after it / t_stop - 1| (HUGE_VAL: none) */
@@ -324,12 +387,14 @@ typedef struct {
 
 #define OC_KMAX 8
 
-/* Front-to-back compositing of one pixel; fills the per-hit arrays of s. */
+/* Front-to-back compositing of one pixel; fills the per-hit arrays of s.
+ * with_normals: also composite the voxel normals; max_weight (may be NULL):
+ * per voxel, the largest blending weight T_i alpha_i seen. */
 static int composite(const oc_scene *S, const oc_params *P, const double ro[3], const double rd[3],
-                     oc_scratch *s, int64_t n_hits, oc_pixel_out *o) {
+                     oc_scratch *s, int64_t n_hits, oc_pixel_out *o, int with_normals, double *max_weight) {
     const int K = P->K;
     double rdn = sqrt(rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2]);
-    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, Nrm[3] = {0, 0, 0};
     int32_t n = 0;
     o->term_vox = -1;
     o->stop_margin = HUGE_VAL;
@@ -354,6 +419,11 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
         voxel_colour(S, v, ro, pre, col);
         for (int ch = 0; ch < 3; ++ch) C[ch] += T * alpha * col[ch];
         D += T * d;
+        if (with_normals) {
+            voxel_normal(S, v, s->nrm + 3 * n, s->gvec + 3 * n);
+            for (int ax = 0; ax < 3; ++ax) Nrm[ax] += T * alpha * s->nrm[3 * n + ax];
+        }
+        if (max_weight) atomic_max_nonneg(max_weight + v, T * alpha);
         s->alpha[n] = alpha;
         s->T[n] = T;
         s->d[n] = d;
@@ -374,6 +444,7 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
         }
     }
     for (int ch = 0; ch < 3; ++ch) o->rgb[ch] = C[ch] + T * P->bg[ch];
+    for (int ax = 0; ax < 3; ++ax) o->normal[ax] = Nrm[ax];
     o->depth = D;
     o->alpha = 1.0 - T;
     o->t_final = T;
@@ -404,13 +475,35 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
  * hit is proportional to l for a grazing hit, so a renderer that rounds the
  * planes, the origin and the direction to precision u has a relative error of
  * order u times this factor in those terms. */
+static void add_term(double *acc, double *acc_abs, double *acc_seg, int64_t i, double add, double kappa) {
+#pragma omp atomic
+    acc[i] += add;
+    if (acc_abs) {
+#pragma omp atomic
+        acc_abs[i] += fabs(add);
+    }
+    if (acc_seg) {
+#pragma omp atomic
+        acc_seg[i] += fabs(add) * kappa;
+    }
+}
+
+/* With normals (g_normal != NULL, the normals composited by the forward):
+ * dN/dalpha_i = T_i (n_i - RN_i) with RN_i = alpha_{i+1} n_{i+1} + (1 -
+ * alpha_{i+1}) RN_{i+1}, RN_last = 0, joins dL/dalpha_i; dL/dn_i = T_i
+ * alpha_i g_normal passes the normalisation, dL/dgrad = (dL/dn - n (n .
+ * dL/dn)) / |grad|, and reaches corner c through Eq. (interp_grad_grad):
+ * dgrad/dV_c = 0.25 (2 x_c - 1, 2 y_c - 1, 2 z_c - 1).  priority (may be
+ * NULL) accumulates |alpha_i dL/dalpha_i| per voxel (Eq. priority). */
 static void pixel_backward(const oc_scene *S, const oc_params *P, const double ro[3], const double rd[3],
                            const oc_scratch *s, const oc_pixel_out *o, const double g_rgb[3],
-                           double g_depth, double g_alpha, double *d_grid, double *d_sh,
-                           double *d_grid_abs, double *d_sh_abs, double *d_grid_seg, double *d_sh_seg) {
+                           double g_depth, double g_alpha, const double *g_normal, double *d_grid, double *d_sh,
+                           double *d_grid_abs, double *d_sh_abs, double *d_grid_seg, double *d_sh_seg,
+                           double *priority) {
     const int K = P->K;
     int32_t n = o->n_comp;
     double RC[3] = {P->bg[0], P->bg[1], P->bg[2]};
+    double RN[3] = {0.0, 0.0, 0.0};
     double RD = 0.0, Sfx = 1.0;
     for (int32_t i = n - 1; i >= 0; --i) {
         int64_t v = s->hits[i].v;
@@ -423,6 +516,13 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
         for (int ch = 0; ch < 3; ++ch) g += g_rgb[ch] * Ti * (c[ch] - RC[ch]);
         g += g_depth * (-Ti * RD);
         g += g_alpha * Ti * Sfx;
+        const double *nv = g_normal ? s->nrm + 3 * i : NULL;
+        if (g_normal)
+            for (int ax = 0; ax < 3; ++ax) g += g_normal[ax] * Ti * (nv[ax] - RN[ax]);
+        if (priority) {
+#pragma omp atomic
+            priority[v] += fabs(al * g);
+        }
 
         double t[OC_KMAX], val[OC_KMAX], w[OC_KMAX][8], ak[OC_KMAX];
         segment_samples(S, v, K, a, b, ro, rd, t, val, w);
@@ -443,17 +543,24 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
             double gk = g * da_dak + g_depth * Ti * dd_dak;
             double gv = gk * (1.0 - ak[k]) * (ell / K) * oc_explin_grad(val[k]);
             const int32_t *ci = S->corner_idx + 8 * v;
-            for (int j = 0; j < 8; ++j) {
-                double add = gv * w[k][j];
-#pragma omp atomic
-                d_grid[ci[j]] += add;
-                if (d_grid_abs) {
-#pragma omp atomic
-                    d_grid_abs[ci[j]] += fabs(add);
+            for (int j = 0; j < 8; ++j) add_term(d_grid, d_grid_abs, d_grid_seg, ci[j], gv * w[k][j], kappa);
+        }
+        /* normal */
+        if (g_normal) {
+            const double *gv = s->gvec + 3 * i;
+            double len = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+            if (len > 0.0) {
+                double dn[3], dot = 0.0, dg[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    dn[ax] = g_normal[ax] * Ti * al;
+                    dot += dn[ax] * nv[ax];
                 }
-                if (d_grid_seg) {
-#pragma omp atomic
-                    d_grid_seg[ci[j]] += fabs(add) * kappa;
+                for (int ax = 0; ax < 3; ++ax) dg[ax] = (dn[ax] - nv[ax] * dot) / len;
+                const int32_t *ci = S->corner_idx + 8 * v;
+                for (int c = 0; c < 8; ++c) {
+                    double add = 0.0;
+                    for (int ax = 0; ax < 3; ++ax) add += dg[ax] * 0.25 * (2.0 * ((c >> (2 - ax)) & 1) - 1.0);
+                    add_term(d_grid, d_grid_abs, d_grid_seg, ci[c], add, kappa);
                 }
             }
         }
@@ -466,23 +573,13 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
             for (int ch = 0; ch < 3; ++ch) {
                 if (!(pre[ch] > 0.0)) continue;
                 double dc = g_rgb[ch] * Ti * al;
-                for (int m = 0; m < 16; ++m) {
-                    double add = Y[m] * dc;
-#pragma omp atomic
-                    d_sh[48 * v + 3 * m + ch] += add;
-                    if (d_sh_abs) {
-#pragma omp atomic
-                        d_sh_abs[48 * v + 3 * m + ch] += fabs(add);
-                    }
-                    if (d_sh_seg) {
-#pragma omp atomic
-                        d_sh_seg[48 * v + 3 * m + ch] += fabs(add) * kappa;
-                    }
-                }
+                for (int m = 0; m < 16; ++m) add_term(d_sh, d_sh_abs, d_sh_seg, 48 * v + 3 * m + ch, Y[m] * dc, kappa);
             }
         }
         /* suffix sums for the next (nearer) hit */
         for (int ch = 0; ch < 3; ++ch) RC[ch] = al * c[ch] + (1.0 - al) * RC[ch];
+        if (g_normal)
+            for (int ax = 0; ax < 3; ++ax) RN[ax] = al * nv[ax] + (1.0 - al) * RN[ax];
         RD = s->d[i] + (1.0 - al) * RD;
         Sfx *= 1.0 - al;
     }
@@ -506,13 +603,15 @@ static void pixel_xy(const oc_camera *cam, int64_t n_px, const int32_t *px_xy, i
  * terminating voxel (-1 if none) and the stop margin: the smallest relative
  * distance |T / t_stop - 1| of the transmittance after a composited voxel from
  * the stop threshold (HUGE_VAL if t_stop = 0 or nothing was composited), which
- * says how close the pixel came to another termination decision.  Returns 0, or
- * -1 on allocation failure. */
-int oc_render(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
-              const int32_t *corner_idx, const double *grid, const double *sh,
-              const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
-              double *rgb, double *depth, double *alpha, double *t_final, int32_t *n_comp,
-              int64_t *term_vox, double *stop_margin, int n_threads) {
+ * says how close the pixel came to another termination decision.  normal
+ * (may be NULL): [n_px][3] composited voxel normals; max_weight (may be NULL):
+ * [N], raised to the largest T_i alpha_i of each voxel over these pixels.
+ * Returns 0, or -1 on allocation failure. */
+int oc_render_ex(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
+                 const int32_t *corner_idx, const double *grid, const double *sh,
+                 const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
+                 double *rgb, double *depth, double *alpha, double *t_final, int32_t *n_comp,
+                 int64_t *term_vox, double *stop_margin, double *normal, double *max_weight, int n_threads) {
     oc_scene S = {world_size, n_vox, centre, level, corner_idx, grid, sh};
     if (P->K < 1 || P->K > OC_KMAX) return -2;
     int err = 0;
@@ -533,7 +632,7 @@ int oc_render(double world_size, int64_t n_vox, const double *centre, const uint
             oc_pixel_ray(cam, x, y, ro, rd);
             int64_t nh = gather_hits(&S, ro, rd, &s);
             oc_pixel_out o;
-            if (nh < 0 || composite(&S, P, ro, rd, &s, nh, &o)) {
+            if (nh < 0 || composite(&S, P, ro, rd, &s, nh, &o, normal != NULL, max_weight)) {
 #pragma omp atomic write
                 err = -1;
                 continue;
@@ -545,21 +644,35 @@ int oc_render(double world_size, int64_t n_vox, const double *centre, const uint
             if (n_comp) n_comp[p] = o.n_comp;
             if (term_vox) term_vox[p] = o.term_vox;
             if (stop_margin) stop_margin[p] = o.stop_margin;
+            if (normal)
+                for (int ax = 0; ax < 3; ++ax) normal[3 * p + ax] = o.normal[ax];
         }
         scratch_free(&s);
     }
     return err;
 }
 
+int oc_render(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
+              const int32_t *corner_idx, const double *grid, const double *sh,
+              const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
+              double *rgb, double *depth, double *alpha, double *t_final, int32_t *n_comp,
+              int64_t *term_vox, double *stop_margin, int n_threads) {
+    return oc_render_ex(world_size, n_vox, centre, level, corner_idx, grid, sh, cam, P, n_px, px_xy, rgb, depth,
+                        alpha, t_final, n_comp, term_vox, stop_margin, NULL, NULL, n_threads);
+}
+
 /* Gradient of sum_p (g_rgb[p] . C_p + g_depth[p] D_p + g_alpha[p] A_p) with
  * respect to grid (accumulated into d_grid[Pts]) and sh (accumulated into
- * d_sh[N][48]).  Same pixel convention as oc_render. */
-int oc_render_grad(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
-                   const int32_t *corner_idx, const double *grid, const double *sh,
-                   const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
-                   const double *g_rgb, const double *g_depth, const double *g_alpha,
-                   double *d_grid, double *d_sh, double *d_grid_abs, double *d_sh_abs,
-                   double *d_grid_seg, double *d_sh_seg, int n_threads) {
+ * d_sh[N][48]).  Same pixel convention as oc_render.  g_normal (may be NULL):
+ * [n_px][3] upstream gradient of the normal image, which adds
+ * sum_p g_normal[p] . N_p to the objective; priority (may be NULL): [N],
+ * accumulates the subdivision priority of Eq. (priority). */
+int oc_render_grad_ex(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
+                      const int32_t *corner_idx, const double *grid, const double *sh,
+                      const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
+                      const double *g_rgb, const double *g_depth, const double *g_alpha, const double *g_normal,
+                      double *d_grid, double *d_sh, double *d_grid_abs, double *d_sh_abs,
+                      double *d_grid_seg, double *d_sh_seg, double *priority, int n_threads) {
     oc_scene S = {world_size, n_vox, centre, level, corner_idx, grid, sh};
     if (P->K < 1 || P->K > OC_KMAX) return -2;
     int err = 0;
@@ -580,17 +693,29 @@ int oc_render_grad(double world_size, int64_t n_vox, const double *centre, const
             oc_pixel_ray(cam, x, y, ro, rd);
             int64_t nh = gather_hits(&S, ro, rd, &s);
             oc_pixel_out o;
-            if (nh < 0 || composite(&S, P, ro, rd, &s, nh, &o)) {
+            if (nh < 0 || composite(&S, P, ro, rd, &s, nh, &o, g_normal != NULL, NULL)) {
 #pragma omp atomic write
                 err = -1;
                 continue;
             }
-            pixel_backward(&S, P, ro, rd, &s, &o, g_rgb + 3 * p, g_depth[p], g_alpha[p], d_grid, d_sh,
-                           d_grid_abs, d_sh_abs, d_grid_seg, d_sh_seg);
+            pixel_backward(&S, P, ro, rd, &s, &o, g_rgb + 3 * p, g_depth[p], g_alpha[p],
+                           g_normal ? g_normal + 3 * p : NULL, d_grid, d_sh, d_grid_abs, d_sh_abs, d_grid_seg,
+                           d_sh_seg, priority);
         }
         scratch_free(&s);
     }
     return err;
+}
+
+int oc_render_grad(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
+                   const int32_t *corner_idx, const double *grid, const double *sh,
+                   const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
+                   const double *g_rgb, const double *g_depth, const double *g_alpha,
+                   double *d_grid, double *d_sh, double *d_grid_abs, double *d_sh_abs,
+                   double *d_grid_seg, double *d_sh_seg, int n_threads) {
+    return oc_render_grad_ex(world_size, n_vox, centre, level, corner_idx, grid, sh, cam, P, n_px, px_xy, g_rgb,
+                             g_depth, g_alpha, NULL, d_grid, d_sh, d_grid_abs, d_sh_abs, d_grid_seg, d_sh_seg,
+                             NULL, n_threads);
 }
 
 /* Sorted hit list of an arbitrary ray (for order checks): writes up to cap

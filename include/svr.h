@@ -72,7 +72,8 @@ extern "C" {
 /* Device-side error flags (svr_frame_status). */
 #define SVR_FLAG_INVALID_VOXEL 1u
 #define SVR_FLAG_CAPACITY 2u
-#define SVR_FLAG_NO_FORWARD 4u /* svr_render_bwd ran before any svr_render_fwd of the sort */
+#define SVR_FLAG_NO_FORWARD 4u /* svr_render_bwd ran before any svr_render_fwd of the sort (or, with
+                                  d_normal, before one that rendered normals) */
 
 typedef struct svr_camera {
     float fx, fy, cx, cy;
@@ -273,6 +274,52 @@ SVR_API int svr_render_batched(svr_frame *frame, const svr_scene *scene, const s
                                const float *d_depth, const float *d_alpha, float *d_grid,
                                float *d_sh, void *stream);
 
+/*
+ * Extra outputs and inputs of svr_render_fwd_ex / svr_render_bwd_ex.  Any
+ * member may be NULL (not computed / zero).  Device pointers, caller-owned,
+ * 4-byte aligned.
+ *   normal      forward output, planar [3][H][W] like rgb (batch layout for
+ *               a batch): N = sum_i T_i alpha_i n_i, the voxel normal n =
+ *               normalize(gradient of the trilinear density field at the
+ *               voxel centre) in world axes (Eq. vox_normal, closed form of
+ *               Eq. interp_grad; the zero vector where the gradient
+ *               vanishes), composited like colour with no background term.
+ *   max_weight  forward output [N]: raised (atomic max, never lowered) to
+ *               every voxel's largest blending weight T_i alpha_i over the
+ *               rendered pixels: the pruning statistic of Sec. 3.2.2,
+ *               accumulated over views and calls until the caller zeroes it.
+ *               Tile lists longer than 1024 entries are walked a second time
+ *               from their true transmittance to get it exactly.
+ *   d_normal    backward input [3][H][W]: dL/dN.  Requires that the frame's
+ *               last forward of this sort rendered `normal` (its tile
+ *               segments carry the normal sums); otherwise split tiles are
+ *               skipped and SVR_FLAG_NO_FORWARD is raised.  The gradient
+ *               passes the normalisation and Eq. interp_grad_grad into d_grid.
+ *   priority    backward output [N]: accumulates (adds to) every voxel's
+ *               subdivision priority sum over pixels |alpha_i dL/dalpha_i|
+ *               (Eq. priority), dL/dalpha_i the derivative of the objective
+ *               (the upstream gradients of all images, normals included) with
+ *               respect to the voxel's alpha in the compositing of Eq.
+ *               alpha_blend, its colour, normal and depth held fixed.
+ */
+typedef struct svr_render_extras {
+    float *normal;
+    float *max_weight;
+    const float *d_normal;
+    float *priority;
+} svr_render_extras;
+
+/* svr_render_fwd plus the forward members of *extras (NULL: none). */
+SVR_API int svr_render_fwd_ex(const svr_frame *frame, float *rgb, float *depth, float *alpha,
+                              float *T_final, int32_t *last, const svr_render_extras *extras,
+                              void *stream);
+
+/* svr_render_bwd plus the backward members of *extras (NULL: none). */
+SVR_API int svr_render_bwd_ex(const svr_frame *frame, const float *d_rgb, const float *d_depth,
+                              const float *d_alpha, const float *T_final, const int32_t *last,
+                              float *d_grid, float *d_sh, const svr_render_extras *extras,
+                              void *stream);
+
 /* svr_render_fwd that also writes, per pixel, counts[y][x] = (list entries
  * with the pixel's sign bits that it examined, hits it composited): the
  * work the forward did, for throughput accounting.  counts: device int32
@@ -308,6 +355,27 @@ SVR_API int svr_render_fwd_static(const svr_scene *scene, const svr_camera *cam,
                                   const svr_params *params, float *rgb, float *depth,
                                   float *alpha, float *T_final, int32_t *last,
                                   int64_t *n_pairs_out, void *stream);
+
+/*
+ * Supersampling anti-aliasing (Sec. 3.1.2 "Anti-aliasing": render at h_ss
+ * times the resolution, then downsample with an anti-aliasing filter).  The
+ * caller renders the view with a camera of width_ss x height_ss pixels over
+ * the same image plane (intrinsics scaled by width_ss / width and height_ss /
+ * height; the paper uses h_ss = 1.1 .. 1.5) and downsamples every output
+ * plane with svr_downsample: target pixel (x, y) is the average of the
+ * supersampled image over its footprint [s_x x, s_x (x + 1)) x [s_y y,
+ * s_y (y + 1)), s_x = width_ss / width (area filter; the paper names no
+ * filter).  src: device float [planes][height_ss][width_ss] (rgb: 3 planes,
+ * depth, alpha: 1); dst: [planes][height][width].  Ratios must lie in [1, 4]
+ * per axis (SVR_ERR_INVALID otherwise).  Enqueues only.
+ */
+SVR_API int svr_downsample(const float *src, int64_t planes, int height_ss, int width_ss, float *dst,
+                           int height, int width, void *stream);
+
+/* Backward of svr_downsample (its transpose): d_src [planes][height_ss][width_ss]
+ * is overwritten with the gradient for the upstream d_dst [planes][height][width]. */
+SVR_API int svr_downsample_bwd(const float *d_dst, int64_t planes, int height, int width, float *d_src,
+                               int height_ss, int width_ss, void *stream);
 
 /*
  * Mean squared error of a rendered image against a target, the MSE term of

@@ -61,6 +61,10 @@ class SvrBuffers(ctypes.Structure):
                 ("offset", _P), ("record", _P), ("keys", _P), ("values", _P), ("ranges", _P)]
 
 
+class SvrRenderExtras(ctypes.Structure):
+    _fields_ = [("normal", _P), ("max_weight", _P), ("d_normal", _P), ("priority", _P)]
+
+
 class SvrError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: status {code}: {msg}")
@@ -82,8 +86,14 @@ SIGNATURES = {
     "svr_render_fwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "svr_render_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_render_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "svr_render_fwd_ex": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "svr_render_bwd_ex": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_render_fwd_static": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "svr_l2_loss": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    "svr_downsample": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                      ctypes.c_int, _P]),
+    "svr_downsample_bwd": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                          ctypes.c_int, _P]),
     "svr_frame_status": (ctypes.c_int, [_P, _P, _P, _P]),
     "svr_frame_buffers": (ctypes.c_int, [_P, _P]),
     "svr_last_error": (ctypes.c_char_p, []),

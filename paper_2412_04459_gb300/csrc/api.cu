@@ -383,9 +383,24 @@ SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, flo
     if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
     if (!rgb || !depth || !alpha || !T_final || !last) return fail(SVR_ERR_INVALID, "null output");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr,
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr, nullptr, nullptr,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_fwd");
+    return SVR_OK;
+}
+
+SVR_API int svr_render_fwd_ex(const svr_frame *frame, float *rgb, float *depth, float *alpha, float *T_final,
+                              int32_t *last, const svr_render_extras *extras, void *stream) {
+    g_err[0] = 0;
+    if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
+    if (!rgb || !depth || !alpha || !T_final || !last) return fail(SVR_ERR_INVALID, "null output");
+    float *normal = extras ? extras->normal : nullptr;
+    float *max_weight = extras ? extras->max_weight : nullptr;
+    if (max_weight && (((uintptr_t)max_weight) & 3u)) return fail(SVR_ERR_INVALID, "max_weight not 4-byte aligned");
+    const svr::FrameDev d = frame_dev(frame);
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr, normal, max_weight,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render_fwd_ex");
     return SVR_OK;
 }
 
@@ -396,7 +411,7 @@ SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, f
     if (!rgb || !depth || !alpha || !T_final || !last || !counts) return fail(SVR_ERR_INVALID, "null output");
     if (((uintptr_t)counts) & 7u) return fail(SVR_ERR_INVALID, "counts not 8-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, (int2 *)counts,
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, (int2 *)counts, nullptr, nullptr,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_stats");
     return SVR_OK;
@@ -412,8 +427,25 @@ SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const flo
     if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
     cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid,
-                                           d_sh, (cudaStream_t)stream);
+                                           d_sh, nullptr, nullptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
+    return SVR_OK;
+}
+
+SVR_API int svr_render_bwd_ex(const svr_frame *frame, const float *d_rgb, const float *d_depth,
+                              const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
+                              float *d_sh, const svr_render_extras *extras, void *stream) {
+    g_err[0] = 0;
+    if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
+    if (!T_final || !last) return fail(SVR_ERR_INVALID, "null T_final or last");
+    if (frame->scene.n_vox > 0 && (!d_grid || !d_sh)) return fail(SVR_ERR_INVALID, "null gradient output");
+    if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
+    const float *d_normal = extras ? extras->d_normal : nullptr;
+    float *priority = extras ? extras->priority : nullptr;
+    const svr::FrameDev d = frame_dev(frame);
+    cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_sh, d_normal,
+                                           priority, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render_bwd_ex");
     return SVR_OK;
 }
 

@@ -465,7 +465,13 @@ struct FwdOut {
     float *rgb, *depth, *alpha, *T;
     int32_t *last;
     int2 *stats;
+    float *normal;      // extras: [3][H][W] composited voxel normals, or NULL
+    float *max_weight;  // extras: [N] per-voxel maximum of T_i alpha_i, raised with atomicMax, or NULL
 };
+
+// Forward variants: the plain render, the work-counting one, and the one with
+// the extra outputs (normal image, maximum blending weights).
+constexpr int kModePlain = 0, kModeStats = 1, kModeExtra = 2;
 
 // Compositing state of the calling lane's pixel.
 struct FwdState {
@@ -473,7 +479,24 @@ struct FwdState {
     int last;     // sorted index of the voxel that stopped the walk, or -1
     bool done;
     int n_cand, n_hit;
+    float N0, N1, N2;  // composited normal (extras)
 };
+
+// Voxel normal of Eq. vox_normal from the 8 raw corner densities (corner c:
+// bit 2 = x, bit 1 = y, bit 0 = z; g0 = corners 0..3, g1 = 4..7): the
+// gradient of the trilinear field at the centre, Eq. interp_grad (a quarter
+// of far face minus near face per axis; the factor cancels here), normalised;
+// zero where the gradient vanishes.  Returns the gradient's length (of the
+// unscaled differences times 1/4).
+__device__ __forceinline__ float voxel_normal(const float4 &g0, const float4 &g1, float3 &n) {
+    const float gx = 0.25f * ((g1.x + g1.y + g1.z + g1.w) - (g0.x + g0.y + g0.z + g0.w));
+    const float gy = 0.25f * ((g0.z + g0.w + g1.z + g1.w) - (g0.x + g0.y + g1.x + g1.y));
+    const float gz = 0.25f * ((g0.y + g0.w + g1.y + g1.w) - (g0.x + g0.z + g1.x + g1.z));
+    const float len = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float inv = len > 0.f ? 1.0f / len : 0.f;
+    n = make_float3(gx * inv, gy * inv, gz * inv);
+    return len;
+}
 
 // Asynchronous staging of the forward.  A slot receives a voxel's 64-byte
 // record as copied (cp.async, 16 bytes per copy, no registers involved);
@@ -563,10 +586,11 @@ __device__ __forceinline__ void hit_fwd_slot(const FwdSlot &e, const PixelRay &p
 // Walk block-list positions [p0, p1) front to back from state s.  The list
 // entries are fetched two batches ahead and the next batch's records are
 // copied into the other staging buffer while this batch is composited.
-template <int K, bool STATS>
+template <int K, int MODE>
 __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0, int p1, const ViewData &vd,
                                          const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, float t_stop,
-                                         FwdState &s) {
+                                         FwdState &s, const FwdOut &out, bool true_weights) {
+    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
     const int lane = threadIdx.x & 31;
     const float3 sb = make_float3((p.s & 4) ? 1.f : 0.f, (p.s & 2) ? 1.f : 0.f, (p.s & 1) ? 1.f : 0.f);
     Lookahead cur, nx, nn;
@@ -614,6 +638,20 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                 s.C1 = fmaf(w, col.y, s.C1);
                 s.C2 = fmaf(w, col.z, s.C2);
                 s.D = fmaf(s.T, dloc, s.D);
+                if (EXTRA) {
+                    if (out.normal) {
+                        float3 n;
+                        voxel_normal(e.g0, e.g1, n);
+                        s.N0 = fmaf(w, n.x, s.N0);
+                        s.N1 = fmaf(w, n.y, s.N1);
+                        s.N2 = fmaf(w, n.z, s.N2);
+                    }
+                    // weights are exact only when the walk started from the
+                    // true transmittance (not a split segment's T = 1)
+                    if (out.max_weight && true_weights)
+                        atomicMax(reinterpret_cast<int *>(out.max_weight) + (ws.meta[buf][k].x & 0x1FFFFFFFu),
+                                  __float_as_int(w));
+                }
                 s.T *= P;
                 if (s.T < t_stop) {
                     s.done = true;
@@ -637,23 +675,36 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
 // walked again from the merged state to find it).  Leaves per segment, for
 // the backward: the transmittance after and before it and the colour and
 // depth sums behind it (T_final bg included).
-template <int K, bool STATS>
+template <int K, int MODE>
 __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, int blk, const ViewData &vd,
-                                          const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, FwdState &m) {
+                                          const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, FwdState &m,
+                                          const FwdOut &out) {
+    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
     const int B = f.blocks_per_tile;
     const int nseg = (int)L.ts.x;
+    // with maximum weights requested every later segment is walked again
+    // from its true transmittance (the segment walks started from T = 1;
+    // segment 0 recorded its weights itself)
+    const bool rewalk = EXTRA && out.max_weight != nullptr;
     for (int sg = 0; sg < nseg; ++sg) {
         float *q = seg_fields(f, L.ts.y + sg, blk);
         const float Tb = m.T;
-        float c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
         bool need = false;
         if (!m.done) {
             const float Tl = __ldcg(q + 4 * 32);
-            if (Tb * Tl >= f.t_stop || sg == 0) {
+            if (rewalk && sg > 0) {
+                need = true;
+            } else if (Tb * Tl >= f.t_stop || sg == 0) {
                 c0 = Tb * __ldcg(q);
                 c1 = Tb * __ldcg(q + 32);
                 c2 = Tb * __ldcg(q + 2 * 32);
                 dd = Tb * __ldcg(q + 3 * 32);
+                if (EXTRA) {
+                    n0 = Tb * __ldcg(q + 8 * 32);
+                    n1 = Tb * __ldcg(q + 9 * 32);
+                    n2 = Tb * __ldcg(q + 10 * 32);
+                }
                 m.T = Tb * Tl;
                 if (Tb * Tl < f.t_stop) {  // segment 0 stopped by itself
                     m.done = true;
@@ -668,15 +719,18 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             }
         }
         if (__any_sync(0xffffffffu, need)) {
-            FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0};
+            FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0, 0.f, 0.f, 0.f};
             int p0, p1;
             seg_range(L, B, sg, p0, p1);
-            fwd_walk<K, STATS>(L.list, p0, p1, vd, p, wb, ws, f.t_stop, r);
+            fwd_walk<K, MODE>(L.list, p0, p1, vd, p, wb, ws, f.t_stop, r, out, true);
             if (need) {
                 c0 = r.C0;
                 c1 = r.C1;
                 c2 = r.C2;
                 dd = r.D;
+                n0 = r.N0;
+                n1 = r.N1;
+                n2 = r.N2;
                 m.T = r.T;
                 if (r.done) {
                     m.done = true;
@@ -696,9 +750,17 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
         q[3 * 32] = dd;
         q[4 * 32] = m.T;
         q[5 * 32] = Tb;
+        if (EXTRA) {
+            m.N0 += n0;
+            m.N1 += n1;
+            m.N2 += n2;
+            q[8 * 32] = n0;
+            q[9 * 32] = n1;
+            q[10 * 32] = n2;
+        }
     }
     // sums behind each segment, back to front
-    float S0 = m.T * f.bg[0], S1 = m.T * f.bg[1], S2 = m.T * f.bg[2], SD = 0.f;
+    float S0 = m.T * f.bg[0], S1 = m.T * f.bg[1], S2 = m.T * f.bg[2], SD = 0.f, SN0 = 0.f, SN1 = 0.f, SN2 = 0.f;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         float *q = seg_fields(f, L.ts.y + sg, blk);
         const float c0 = q[0], c1 = q[32], c2 = q[2 * 32], dd = q[3 * 32];
@@ -710,12 +772,22 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
         S1 += c1;
         S2 += c2;
         SD += dd;
+        if (EXTRA) {
+            const float n0 = q[8 * 32], n1 = q[9 * 32], n2 = q[10 * 32];
+            q[8 * 32] = SN0;
+            q[9 * 32] = SN1;
+            q[10 * 32] = SN2;
+            SN0 += n0;
+            SN1 += n1;
+            SN2 += n2;
+        }
     }
 }
 
-template <bool STATS>
+template <int MODE>
 __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, const PixelRay &p,
                                           const FwdState &s, int last, const FwdOut &out) {
+    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
     if (!p.inside) return;
     // outputs of view v start at pixel pix_base (rgb: 3 * pix_base, planar)
     const size_t HW = (size_t)cam.W * cam.H;
@@ -730,10 +802,17 @@ __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, 
     out.T[o] = s.T;
     out.last[o] = last;
     if (STATS) out.stats[o] = make_int2(s.n_cand, s.n_hit);
+    if (EXTRA && out.normal) {
+        float *nrm = out.normal + 3 * (size_t)cam.pix_base + px;
+        nrm[0] = s.N0;
+        nrm[HW] = s.N1;
+        nrm[2 * HW] = s.N2;
+    }
 }
 
-template <int K, bool STATS>
+template <int K, int MODE>
 __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdSmem &ws, const FwdOut &out) {
+    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
     const ItemView iv = item_view(f, it.g);
     const DevCam &cam = f.views[iv.view];
     WarpBlock wb;
@@ -741,17 +820,17 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
     if (wb.smask == 0) return;  // the whole block lies outside the image
     const ItemList L = item_list(f, it.g, it.blk);
     const int lane = threadIdx.x & 31;
-    FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
+    FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f};
     if (L.ts.x <= 1) {
-        fwd_walk<K, STATS>(L.list, 0, L.n_list, iv.vd, p, wb, ws, f.t_stop, s);
-        fwd_write<STATS>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
+        fwd_walk<K, MODE>(L.list, 0, L.n_list, iv.vd, p, wb, ws, f.t_stop, s, out, true);
+        fwd_write<MODE>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
         return;
     }
     // one segment of a split tile, walked from T = 1
     const int B = f.blocks_per_tile;
     int p0, p1;
     seg_range(L, B, it.seg, p0, p1);
-    fwd_walk<K, STATS>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s);
+    fwd_walk<K, MODE>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s, out, it.seg == 0);
     float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
     q[0] = s.C0;
     q[32] = s.C1;
@@ -763,6 +842,11 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
         q[6 * 32] = __int_as_float(s.n_cand);
         q[7 * 32] = __int_as_float(s.n_hit);
     }
+    if (EXTRA) {
+        q[8 * 32] = s.N0;
+        q[9 * 32] = s.N1;
+        q[10 * 32] = s.N2;
+    }
     __threadfence();
     __syncwarp();
     unsigned prev = 0;
@@ -772,16 +856,18 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
     if (prev + 1 != L.ts.x) return;
     // the last segment of the block to finish merges them all
     __threadfence();
-    FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0};
-    fwd_merge<K, STATS>(f, L, it.blk, iv.vd, p, wb, ws, m);
-    fwd_write<STATS>(f, cam, p, m, m.last >= 0 ? m.last : L.end - 1, out);
+    FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f};
+    fwd_merge<K, MODE>(f, L, it.blk, iv.vd, p, wb, ws, m, out);
+    fwd_write<MODE>(f, cam, p, m, m.last >= 0 ? m.last : L.end - 1, out);
     if (lane == 0) *cnt = 0;  // ready for the next forward of this sort
 }
 
-// STATS: also count, per pixel, the list entries with its sign bits whose
-// pixel box contains it (the slab tests it must make) and the hits it
-// composited (int2 per pixel), for work accounting.
-template <int K, bool STATS>
+// MODE kModeStats: also count, per pixel, the list entries with its sign
+// bits whose pixel box contains it (the slab tests it must make) and the hits
+// it composited (int2 per pixel), for work accounting.  kModeExtra: the
+// normal image and the per-voxel maximum blending weights (whichever of
+// out.normal, out.max_weight is set).
+template <int K, int MODE>
 __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev f, FwdOut out) {
     __shared__ FwdSmem smem[kWarps];
     FwdSmem &ws = smem[threadIdx.x >> 5];
@@ -789,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
     const unsigned n_items = f.status->n_queue * bpt;
     Item it;
     while (next_item(&f.status->fwd_next, n_items, bpt, f.order, it)) {
-        fwd_item<K, STATS>(f, it, ws, out);
+        fwd_item<K, MODE>(f, it, ws, out);
         __syncwarp();
     }
     // the launch's last warp to run out of work resets the work counter for
@@ -799,7 +885,8 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
         if (atomicAdd(&f.status->fwd_exit, 1u) == gridDim.x * (blockDim.x >> 5) - 1) {
             f.status->fwd_next = 0;
             f.status->fwd_exit = 0;
-            f.status->fwd_done = 1;
+            // 2: the segment sums include the normal image
+            f.status->fwd_done = (MODE == kModeExtra && out.normal) ? 2u : 1u;
         }
     }
 }
@@ -809,6 +896,12 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
 struct PixelGrad {
     float gC0, gC1, gC2, gD, gA;
     float Tfin;
+    float gN0, gN1, gN2;  // upstream gradient of the normal image (extras)
+};
+
+// Sums of the normal image behind a voxel (extras; like SC for colour).
+struct NrmSums {
+    float x, y, z;
 };
 
 // Gradient contributions of one hit, computed from one pass over its K
@@ -818,10 +911,15 @@ struct PixelGrad {
 // prefix before it); the voxel's own share is removed here.  Returns the
 // transmittance in front of the voxel (T_i) and behind it (T_{i+1}), its
 // blending weight and local depth.
-template <int K, bool B2F>
+// EXTRA: the normal image joins the objective (SN: its sums behind the voxel,
+// like SC; nrm returns the voxel's normal) and prio returns the voxel's
+// subdivision priority term |alpha dL/dalpha| (Eq. priority), alpha dL/dalpha
+// = alpha / (1 - alpha) dL/dx with x the optical depth.
+template <int K, bool B2F, bool EXTRA>
 __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, const PixelGrad &g, float a, float b,
-                                         float T_known, float SC0, float SC1, float SC2, float SD, float dgeo[8],
-                                         float dcol[3], float &T_i, float &T_after, float &w, float &dloc) {
+                                         float T_known, float SC0, float SC1, float SC2, float SD, NrmSums SN,
+                                         float dgeo[8], float dcol[3], float &T_i, float &T_after, float &w,
+                                         float &dloc, float3 &nrm, float &prio) {
     const float inv_k = 1.0f / K;
     const float seg = b - a;
     const float xs = seg * p.rdn * inv_k;
@@ -854,20 +952,34 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
         T_i = T_known;
         T_after = T_known * trans;
     }
-    w = T_i * seg_alpha(X, trans);
+    const float al = seg_alpha(X, trans);
+    w = T_i * al;
     dloc = d;
+    float nlen = 0.f;
+    nrm = make_float3(0.f, 0.f, 0.f);
+    if (EXTRA) nlen = voxel_normal(e.g0, e.g1, nrm);
     if (!B2F) {
         SC0 -= w * e.col.x;
         SC1 -= w * e.col.y;
         SC2 -= w * e.col.z;
         SD -= T_i * d;
+        if (EXTRA) {
+            SN.x -= w * nrm.x;
+            SN.y -= w * nrm.y;
+            SN.z -= w * nrm.z;
+        }
     }
     dcol[0] = w * g.gC0;
     dcol[1] = w * g.gC1;
     dcol[2] = w * g.gC2;
     // dL/dx_i through C, A and the transmittance of later voxels in D
-    const float gx = g.gC0 * fmaf(T_after, e.col.x, -SC0) + g.gC1 * fmaf(T_after, e.col.y, -SC1) +
-                     g.gC2 * fmaf(T_after, e.col.z, -SC2) + g.gA * g.Tfin - g.gD * SD;
+    float gx = g.gC0 * fmaf(T_after, e.col.x, -SC0) + g.gC1 * fmaf(T_after, e.col.y, -SC1) +
+               g.gC2 * fmaf(T_after, e.col.z, -SC2) + g.gA * g.Tfin - g.gD * SD;
+    if (EXTRA) {
+        gx += g.gN0 * fmaf(T_after, nrm.x, -SN.x) + g.gN1 * fmaf(T_after, nrm.y, -SN.y) +
+              g.gN2 * fmaf(T_after, nrm.z, -SN.z);
+        prio = fabsf(gx * al / fmaxf(trans, 1e-30f));
+    }
     // per-sample depth term, suffix Q_k = sum_{m>k} P_m (1 - e_m) t_m
     float Pk[K + 1];
     Pk[0] = 1.f;
@@ -892,6 +1004,17 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
         dgeo[6] = fmaf(dv, w11 * uz, dgeo[6]);
         dgeo[7] = fmaf(dv, w11 * qz[k], dgeo[7]);
         Q = fmaf(Pk[k] * (1.f - ek[k]), tk[k], Q);
+    }
+    // normal: dL/dn = w g_N, through the normalisation (I - n n^T) / |grad|
+    // and Eq. interp_grad_grad: dgrad/dV_c = (2 x_c - 1, 2 y_c - 1, 2 z_c - 1) / 4
+    if (EXTRA && nlen > 0.f) {
+        const float dnx = w * g.gN0, dny = w * g.gN1, dnz = w * g.gN2;
+        const float dot = dnx * nrm.x + dny * nrm.y + dnz * nrm.z;
+        const float il = 0.25f / nlen;
+        const float gx_ = (dnx - nrm.x * dot) * il, gy_ = (dny - nrm.y * dot) * il, gz_ = (dnz - nrm.z * dot) * il;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            dgeo[c] += ((c & 4) ? gx_ : -gx_) + ((c & 2) ? gy_ : -gy_) + ((c & 1) ? gz_ : -gz_);
     }
 }
 
@@ -934,18 +1057,21 @@ __device__ __forceinline__ int rec_slot(const RecSmem &rs, int k, int base) {
     return rs.off[k] + __popc(rs.pix[k] & lt) - base;
 }
 
-__device__ __forceinline__ void rec_write(RecSmem &rs, int slot, const float dgeo[8], const float dcol[3]) {
+// Record: 8 corner-density gradients, 3 colour gradients and the
+// subdivision priority term (extras; 0 otherwise).
+__device__ __forceinline__ void rec_write(RecSmem &rs, int slot, const float dgeo[8], const float dcol[3],
+                                          float prio) {
     float4 *r = rs.rec + slot * (kRecStride / 4);
     r[0] = make_float4(dgeo[0], dgeo[1], dgeo[2], dgeo[3]);
     r[1] = make_float4(dgeo[4], dgeo[5], dgeo[6], dgeo[7]);
-    r[2] = make_float4(dcol[0], dcol[1], dcol[2], 0.f);
+    r[2] = make_float4(dcol[0], dcol[1], dcol[2], prio);
 }
 
 __device__ __forceinline__ void rec_add(float row[kRecStride], const float4 *r) {
     const float4 a = r[0], b = r[1], c = r[2];
     row[0] += a.x, row[1] += a.y, row[2] += a.z, row[3] += a.w;
     row[4] += b.x, row[5] += b.y, row[6] += b.z, row[7] += b.w;
-    row[8] += c.x, row[9] += c.y, row[10] += c.z;
+    row[8] += c.x, row[9] += c.y, row[10] += c.z, row[11] += c.w;
 }
 
 // End of the run of entries from k_lo whose records fit in kRecCap slots
@@ -960,7 +1086,7 @@ __device__ __forceinline__ int rec_run_end(int k_lo, int end, int base) {
 // colour channel that the clamp cut (bit clear) has no gradient.
 __device__ __forceinline__ void add_row(const float row[kRecStride], int vid, unsigned bits,
                                         const int32_t *__restrict__ corner_idx, float *__restrict__ d_grid,
-                                        float *__restrict__ acc_col) {
+                                        float *__restrict__ acc_col, float *__restrict__ priority) {
     const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
     const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
     atomicAdd(d_grid + i0.x, row[0]);
@@ -974,13 +1100,15 @@ __device__ __forceinline__ void add_row(const float row[kRecStride], int vid, un
     if (bits & 1u) atomicAdd(acc_col + 3 * (size_t)vid + 0, row[8]);
     if (bits & 2u) atomicAdd(acc_col + 3 * (size_t)vid + 1, row[9]);
     if (bits & 4u) atomicAdd(acc_col + 3 * (size_t)vid + 2, row[10]);
+    if (priority) atomicAdd(priority + vid, row[11]);
 }
 
 // Lane j in [k_lo, k_hi) sums entry j's records and adds the sums to the
 // global gradients of its voxel.
 __device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, int k_lo, int k_hi, int off, int end,
                                           int base, const int32_t *__restrict__ corner_idx,
-                                          float *__restrict__ d_grid, float *__restrict__ acc_col) {
+                                          float *__restrict__ d_grid, float *__restrict__ acc_col,
+                                          float *__restrict__ priority) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     if (lane >= k_lo && lane < k_hi && end > off) {
@@ -988,7 +1116,8 @@ __device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, in
 #pragma unroll
         for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
         for (int r = off - base; r < end - base; ++r) rec_add(row, rs.rec + r * (kRecStride / 4));
-        add_row(row, __float_as_int(st[lane].col.w), __float_as_uint(st[lane].pad.x), corner_idx, d_grid, acc_col);
+        add_row(row, __float_as_int(st[lane].col.w), __float_as_uint(st[lane].pad.x), corner_idx, d_grid, acc_col,
+                priority);
     }
     __syncwarp();
 }
@@ -1003,23 +1132,27 @@ struct BwdIn {
     const float *d_rgb, *d_depth, *d_alpha, *T;
     const int32_t *last;
     float *d_grid;
+    const float *d_normal;  // extras: upstream gradient of the normal image [3][H][W], or NULL
+    float *priority;        // extras: [N] subdivision priority, accumulated, or NULL
 };
 
 // Front-to-back gradients for the pixels of an item whose transmittance
 // behind their part of the list underflowed (the back-to-front recovery
 // T_i = T_(i+1) / (1 - alpha_i) would lose precision): sweep 1 sums the
-// part's colour and depth from the transmittance in front of it, sweep 2
-// takes the gradients with the sums behind each voxel as total minus prefix.
-template <int K>
+// part's colour, depth (and normal) from the transmittance in front of it,
+// sweep 2 takes the gradients with the sums behind each voxel as total minus
+// prefix.
+template <int K, bool EXTRA>
 __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList L, int p0, int p1, int idx0,
                                                int last, bool fallback, float T_before, float SC0, float SC1, float SC2,
-                                               float SD, const ViewData vd, const WarpBlock wb, const PixelRay p,
-                                               const PixelGrad g, Entry *st, RecSmem &rs, const BwdIn &in,
-                                               float *dcol) {
+                                               float SD, NrmSums SN, const ViewData vd, const WarpBlock wb,
+                                               const PixelRay p, const PixelGrad g, Entry *st, RecSmem &rs,
+                                               const BwdIn &in, float *dcol) {
     const int lane = threadIdx.x & 31;
     const int n_fb = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : idx0));
     // sweep 1: this part's own sums, from the transmittance in front of it
     float T = T_before, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
+    NrmSums Nt = {0.f, 0.f, 0.f};
     for (int base = p0; base < n_fb; base += kBatch) {
         Lookahead cur;
         fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
@@ -1038,6 +1171,13 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 Ct1 = fmaf(w, e.col.y, Ct1);
                 Ct2 = fmaf(w, e.col.z, Ct2);
                 Dt = fmaf(T, dloc, Dt);
+                if (EXTRA) {
+                    float3 n;
+                    voxel_normal(e.g0, e.g1, n);
+                    Nt.x = fmaf(w, n.x, Nt.x);
+                    Nt.y = fmaf(w, n.y, Nt.y);
+                    Nt.z = fmaf(w, n.z, Nt.z);
+                }
                 T *= trans;
             }
         }
@@ -1047,8 +1187,12 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
     Ct1 += SC1;
     Ct2 += SC2;
     Dt += SD;
+    Nt.x += SN.x;
+    Nt.y += SN.y;
+    Nt.z += SN.z;
     // sweep 2: gradients with the sums behind = total - prefix
     float Tf = T_before, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
+    NrmSums PN = {0.f, 0.f, 0.f};
     for (int base = p0; base < n_fb; base += kBatch) {
         Lookahead cur;
         fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
@@ -1075,17 +1219,24 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 const Entry &e = st[k];
                 float a, b;
                 slab(e, p, a, b);
-                float T_i, Ta, w, dloc, dgeo[8], dc[3];
-                hit_grad<K, false>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, dgeo, dc,
-                                   T_i, Ta, w, dloc);
+                float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f;
+                float3 n;
+                const NrmSums Nb = {Nt.x - PN.x, Nt.y - PN.y, Nt.z - PN.z};
+                hit_grad<K, false, EXTRA>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, Nb, dgeo,
+                                          dc, T_i, Ta, w, dloc, n, prio);
                 PC0 = fmaf(w, e.col.x, PC0);
                 PC1 = fmaf(w, e.col.y, PC1);
                 PC2 = fmaf(w, e.col.z, PC2);
                 PD = fmaf(T_i, dloc, PD);
+                if (EXTRA) {
+                    PN.x = fmaf(w, n.x, PN.x);
+                    PN.y = fmaf(w, n.y, PN.y);
+                    PN.z = fmaf(w, n.z, PN.z);
+                }
                 Tf = Ta;
-                rec_write(rs, rec_slot(rs, k, rb), dgeo, dc);
+                rec_write(rs, rec_slot(rs, k, rb), dgeo, dc, prio);
             }
-            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol);
+            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol, EXTRA ? in.priority : nullptr);
             k_lo = k_hi;
             if (k_lo >= 32) break;
         }
@@ -1093,7 +1244,7 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
     }
 }
 
-template <int K>
+template <int K, bool EXTRA>
 __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entry *st, RecSmem &rs,
                                          const BwdIn &in) {
     const ItemView iv = item_view(f, it.g);
@@ -1110,7 +1261,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     const size_t px = (size_t)p.y * cam.W + p.x;
     const size_t o = (size_t)cam.pix_base + px;
 
-    PixelGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    PixelGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
     int last = beg - 1;
     if (p.inside) {
         if (in.d_rgb) {
@@ -1121,6 +1272,12 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         }
         if (in.d_depth) g.gD = in.d_depth[o];
         if (in.d_alpha) g.gA = in.d_alpha[o];
+        if (EXTRA && in.d_normal) {
+            const float *gn = in.d_normal + 3 * (size_t)cam.pix_base + px;
+            g.gN0 = gn[0];
+            g.gN1 = gn[HW];
+            g.gN2 = gn[2 * HW];
+        }
         g.Tfin = in.T[o];
         last = max(beg - 1, min(in.last[o], L.end - 1));   // stay inside the tile's list
     }
@@ -1130,8 +1287,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     int p0 = 0, p1 = L.n_list, idx0 = beg;
     float T_after = g.Tfin, T_before = 1.f;
     float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
+    NrmSums SN = {0.f, 0.f, 0.f};
     if (L.ts.x > 1) {
-        if (f.status->fwd_done == 0) {
+        // a split tile starts from the segment sums of this sort's forward,
+        // which must include the normal image when its gradient is asked for
+        if (f.status->fwd_done == 0 || (EXTRA && in.d_normal && f.status->fwd_done != 2u)) {
             if (lane == 0) atomicOr(&f.status->flags, SVR_FLAG_NO_FORWARD);
             return;
         }
@@ -1144,10 +1304,16 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         SD = q[3 * 32];
         T_after = q[4 * 32];
         T_before = q[5 * 32];
+        if (EXTRA) {
+            SN.x = q[8 * 32];
+            SN.y = q[9 * 32];
+            SN.z = q[10 * 32];
+        }
     }
     const bool has = p.inside && last >= idx0;
     const bool fallback = has && T_after < 1e-30f;
     const bool active = has && !fallback;
+    float *prio_out = EXTRA ? in.priority : nullptr;
 
     // ---- back to front
     {
@@ -1184,16 +1350,23 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     const Entry &e = st[k];
                     float a, b;
                     slab(e, p, a, b);
-                    float T_i, Ta, w, dloc, dgeo[8], dc[3];
-                    hit_grad<K, true>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, dgeo, dc, T_i, Ta, w, dloc);
+                    float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f;
+                    float3 n;
+                    hit_grad<K, true, EXTRA>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, SN, dgeo, dc, T_i, Ta, w,
+                                             dloc, n, prio);
                     SC0 = fmaf(w, e.col.x, SC0);
                     SC1 = fmaf(w, e.col.y, SC1);
                     SC2 = fmaf(w, e.col.z, SC2);
                     SD = fmaf(T_i, dloc, SD);
+                    if (EXTRA) {
+                        SN.x = fmaf(w, n.x, SN.x);
+                        SN.y = fmaf(w, n.y, SN.y);
+                        SN.z = fmaf(w, n.z, SN.z);
+                    }
                     T_after = T_i;
-                    rec_write(rs, rec_slot(rs, k, base), dgeo, dc);
+                    rec_write(rs, rec_slot(rs, k, base), dgeo, dc, prio);
                 }
-                rec_flush(rs, st, k_lo, k_hi, off, end, base, f.corner_idx, in.d_grid, dcol);
+                rec_flush(rs, st, k_lo, k_hi, off, end, base, f.corner_idx, in.d_grid, dcol, prio_out);
                 k_lo = k_hi;
                 if (k_lo >= 32) break;
             }
@@ -1204,11 +1377,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     // ---- front to back for pixels whose transmittance underflowed (rare:
     // kept out of line so that it does not weigh on the main path's registers)
     if (__any_sync(0xffffffffu, fallback))
-        bwd_front_to_back<K>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, vd, wb, p, g, st, rs, in,
-                             dcol);
+        bwd_front_to_back<K, EXTRA>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, SN, vd, wb, p,
+                                    g, st, rs, in, dcol);
 }
 
-template <int K>
+template <int K, bool EXTRA>
 __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(FrameDev f, BwdIn in) {
     __shared__ Entry stage[kBwdWarps][kBatch];
     __shared__ RecSmem recs[kBwdWarps];
@@ -1218,7 +1391,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(Frame
     const unsigned n_items = f.status->n_queue * bpt;
     Item it;
     while (next_item(&f.status->bwd_next, n_items, bpt, f.order, it)) {
-        bwd_item<K>(f, it, st, recs[warp], in);
+        bwd_item<K, EXTRA>(f, it, st, recs[warp], in);
         __syncwarp();
     }
 }
@@ -1296,39 +1469,45 @@ static unsigned persistent_grid(Kern kernel, int threads) {
 
 // Grid size from a lower bound on the work items (every tile has at least
 // one segment); the kernels read the exact count from the device.
-template <int K, bool ST>
+template <int K, int MODE>
 static cudaError_t fwd_k(const FrameDev &f, const FwdOut &out, cudaStream_t s) {
     static DeviceCache cache;
-    const unsigned grid = device_cached(cache, [] { return persistent_grid(k_render_fwd<K, ST>, kThreads); });
+    const unsigned grid = device_cached(cache, [] { return persistent_grid(k_render_fwd<K, MODE>, kThreads); });
     const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kWarps - 1) / kWarps);
-    k_render_fwd<K, ST><<<g, kThreads, 0, s>>>(f, out);
+    k_render_fwd<K, MODE><<<g, kThreads, 0, s>>>(f, out);
     return cudaGetLastError();
 }
 
-template <int K>
+template <int K, bool EXTRA>
 static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
     static DeviceCache cache;
-    const unsigned grid = device_cached(cache, [] { return persistent_grid(k_render_bwd<K>, kBwdThreads); });
+    const unsigned grid =
+        device_cached(cache, [] { return persistent_grid(k_render_bwd<K, EXTRA>, kBwdThreads); });
     const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kBwdWarps - 1) / kBwdWarps);
-    k_render_bwd<K><<<g, kBwdThreads, 0, s>>>(f, in);
+    k_render_bwd<K, EXTRA><<<g, kBwdThreads, 0, s>>>(f, in);
     return cudaGetLastError();
 }
 
 cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float *alpha,
-                              float *T_final, int32_t *last, int2 *stats, cudaStream_t s) {
-    const FwdOut out = {rgb, depth, alpha, T_final, last, stats};
+                              float *T_final, int32_t *last, int2 *stats, float *normal, float *max_weight,
+                              cudaStream_t s) {
+    const FwdOut out = {rgb, depth, alpha, T_final, last, stats, normal, max_weight};
+    const int mode = stats ? kModeStats : (normal || max_weight) ? kModeExtra : kModePlain;
     // the work counter is zero here: cleared with the status block, then by
     // the last warp of every launch
     cudaError_t e;
-    switch (f.K * 2 + (stats ? 1 : 0)) {
-        case 2: e = fwd_k<1, false>(f, out, s); break;
-        case 3: e = fwd_k<1, true>(f, out, s); break;
-        case 4: e = fwd_k<2, false>(f, out, s); break;
-        case 5: e = fwd_k<2, true>(f, out, s); break;
-        case 6: e = fwd_k<3, false>(f, out, s); break;
-        case 7: e = fwd_k<3, true>(f, out, s); break;
+    switch (f.K * 3 + mode) {
+        case 3: e = fwd_k<1, kModePlain>(f, out, s); break;
+        case 4: e = fwd_k<1, kModeStats>(f, out, s); break;
+        case 5: e = fwd_k<1, kModeExtra>(f, out, s); break;
+        case 6: e = fwd_k<2, kModePlain>(f, out, s); break;
+        case 7: e = fwd_k<2, kModeStats>(f, out, s); break;
+        case 8: e = fwd_k<2, kModeExtra>(f, out, s); break;
+        case 9: e = fwd_k<3, kModePlain>(f, out, s); break;
+        case 10: e = fwd_k<3, kModeStats>(f, out, s); break;
+        case 11: e = fwd_k<3, kModeExtra>(f, out, s); break;
         default: return cudaErrorInvalidValue;
     }
     return e;
@@ -1336,16 +1515,20 @@ cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float
 
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float *d_depth,
                               const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
-                              float *d_sh, cudaStream_t s) {
+                              float *d_sh, const float *d_normal, float *priority, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
     if (e == cudaSuccess && f.n_vox > 0)
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
-    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid};
-    switch (f.K) {
-        case 1: e = bwd_k<1>(f, in, s); break;
-        case 2: e = bwd_k<2>(f, in, s); break;
-        case 3: e = bwd_k<3>(f, in, s); break;
+    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority};
+    const bool extra = d_normal != nullptr || priority != nullptr;
+    switch (f.K * 2 + (extra ? 1 : 0)) {
+        case 2: e = bwd_k<1, false>(f, in, s); break;
+        case 3: e = bwd_k<1, true>(f, in, s); break;
+        case 4: e = bwd_k<2, false>(f, in, s); break;
+        case 5: e = bwd_k<2, true>(f, in, s); break;
+        case 6: e = bwd_k<3, false>(f, in, s); break;
+        case 7: e = bwd_k<3, true>(f, in, s); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

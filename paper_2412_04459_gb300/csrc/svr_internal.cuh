@@ -24,9 +24,11 @@ constexpr int kScanTile = 256;             // entries per block of the count sca
 // Tile lists longer than kSegLen entries are rendered as segments of kSegLen
 // consecutive entries (the last one shorter), each by its own warps, and
 // merged afterwards; kSegFields floats per pixel and segment carry the
-// partial sums between the warps and on to the backward.
+// partial sums between the warps and on to the backward: colour (0..2),
+// depth (3), transmittance after and before (4, 5; 5 holds the stopping
+// index until the merge), work counts (6, 7), normal (8..10).
 constexpr int kSegLen = 1024;
-constexpr int kSegFields = 8;
+constexpr int kSegFields = 11;
 // A tile's pairs are counted and emitted through kTileSub sub-buckets (by
 // voxel id), so that the atomics on a busy tile spread over separate cache
 // lines; the sub-buckets of a tile are adjacent in its range.
@@ -62,7 +64,7 @@ struct Status {
     unsigned bwd_next;    // next work item of the backward render (reset before each launch)
     unsigned n_queue;     // (tile, segment) entries of the render work order
     unsigned slots_used;  // segment slots taken by the split tiles
-    unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort
+    unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort (2: with normals)
     unsigned sort_next;   // next work-order entry of the long-list sort
     unsigned fwd_exit;    // warps of the running forward launch that ran out of work
     unsigned pad[5];
@@ -223,9 +225,11 @@ cudaError_t launch_emit(const FrameDev &f, cudaStream_t s);
 cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties, cudaStream_t s);
 cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s);
 cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth,
-                              float *alpha, float *T_final, int32_t *last, int2 *stats, cudaStream_t s);
+                              float *alpha, float *T_final, int32_t *last, int2 *stats, float *normal,
+                              float *max_weight, cudaStream_t s);
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb,
                               const float *d_depth, const float *d_alpha, const float *T_final,
-                              const int32_t *last, float *d_grid, float *d_sh, cudaStream_t s);
+                              const int32_t *last, float *d_grid, float *d_sh, const float *d_normal,
+                              float *priority, cudaStream_t s);
 
 }  // namespace svr

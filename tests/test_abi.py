@@ -55,14 +55,16 @@ def test_struct_sizes_match_c(lib, tmp_path):
     """ctypes struct layouts equal the C compiler's (sizeof of each struct)."""
     from paper_2412_04459_gb300 import _native as N
     src = tmp_path / "sz.c"
-    src.write_text('#include "svr.h"\n#include <stdio.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu\\n",'
+    src.write_text('#include "svr.h"\n#include <stdio.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
                    'sizeof(svr_camera),sizeof(svr_params),sizeof(svr_scene),sizeof(svr_frame),'
-                   'sizeof(svr_buffers),__builtin_offsetof(svr_frame, offsets));return 0;}\n')
+                   'sizeof(svr_buffers),__builtin_offsetof(svr_frame, offsets),sizeof(svr_render_extras));'
+                   'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert sizes == [ctypes.sizeof(N.SvrCamera), ctypes.sizeof(N.SvrParams), ctypes.sizeof(N.SvrScene),
-                     ctypes.sizeof(N.SvrFrame), ctypes.sizeof(N.SvrBuffers), N.SvrFrame.offsets.offset]
+                     ctypes.sizeof(N.SvrFrame), ctypes.sizeof(N.SvrBuffers), N.SvrFrame.offsets.offset,
+                     ctypes.sizeof(N.SvrRenderExtras)]
 
 
 def test_workspace_size_host_checks(lib):

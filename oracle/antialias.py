@@ -52,7 +52,7 @@ def downsample(img: np.ndarray, height: int, width: int) -> np.ndarray:
     img = np.asarray(img, np.float64)
     My = area_weights(img.shape[-2], height)
     Mx = area_weights(img.shape[-1], width)
-    return np.einsum("yY,...YX,xX->...yx", My, img, Mx)
+    return My @ img @ Mx.T
 
 
 def downsample_adjoint(grad: np.ndarray, height_ss: int, width_ss: int) -> np.ndarray:
@@ -60,4 +60,4 @@ def downsample_adjoint(grad: np.ndarray, height_ss: int, width_ss: int) -> np.nd
     grad = np.asarray(grad, np.float64)
     My = area_weights(height_ss, grad.shape[-2])
     Mx = area_weights(width_ss, grad.shape[-1])
-    return np.einsum("yY,...yx,xX->...YX", My, grad, Mx)
+    return My.T @ grad @ Mx

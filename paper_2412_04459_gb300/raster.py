@@ -213,6 +213,42 @@ class Frame:
                                        _stream(stream)), "svr_render_fwd")
         return out
 
+    def forward_ex(self, out=None, normal: bool = False, max_weight: Optional[torch.Tensor] = None, stream=None):
+        """svr_render_fwd_ex: the forward plus, on request, the normal image
+        (out["normal"], planar like rgb) and the per-voxel maximum blending
+        weights (raised in place in max_weight, float32 [N])."""
+        if out is None:
+            out = self.new_outputs()
+        if normal and "normal" not in out:
+            out["normal"] = torch.empty_like(out["rgb"])
+        ex = N.SvrRenderExtras()
+        ex.normal = out["normal"].data_ptr() if normal else None
+        ex.max_weight = max_weight.data_ptr() if max_weight is not None else None
+        N.check(N.lib().svr_render_fwd_ex(N.ref(self.frame), _ptr(out["rgb"]), _ptr(out["depth"]),
+                                          _ptr(out["alpha"]), _ptr(out["T_final"]), _ptr(out["last"]), N.ref(ex),
+                                          _stream(stream)), "svr_render_fwd_ex")
+        return out
+
+    def backward_ex(self, g_rgb, g_depth, g_alpha, out, g_normal=None, priority: Optional[torch.Tensor] = None,
+                    d_grid=None, d_sh=None, stream=None):
+        """svr_render_bwd_ex: the backward plus, on request, the normal
+        image's upstream gradient and the per-voxel subdivision priority
+        (accumulated in place in priority, float32 [N])."""
+        dev = self.scene.centre.device
+        if d_grid is None:
+            d_grid = torch.zeros(self.grid.shape[0], device=dev)
+        if d_sh is None:
+            d_sh = torch.empty(self.scene.n_vox, 48, device=dev)
+        gr, gd, ga, gn = (None if t is None else t.contiguous() for t in (g_rgb, g_depth, g_alpha, g_normal))
+        ex = N.SvrRenderExtras()
+        ex.d_normal = gn.data_ptr() if gn is not None else None
+        ex.priority = priority.data_ptr() if priority is not None else None
+        N.check(N.lib().svr_render_bwd_ex(N.ref(self.frame), _ptr(gr), _ptr(gd), _ptr(ga), _ptr(out["T_final"]),
+                                          _ptr(out["last"]), _ptr(d_grid), _ptr(d_sh), N.ref(ex), _stream(stream)),
+                "svr_render_bwd_ex")
+        del gr, gd, ga, gn
+        return d_grid, d_sh
+
     def forward_stats(self, stream=None):
         """Forward render plus per-pixel (candidates examined, hits) counts."""
         out = self.new_outputs(counts=True)
@@ -269,6 +305,8 @@ class Frame:
                 d[k] = out[k].reshape(-1)[b:e].view(H, W)
             if "counts" in out:
                 d["counts"] = out["counts"].reshape(-1, 2)[b:e].view(H, W, 2)
+            if "normal" in out:
+                d["normal"] = out["normal"].reshape(-1)[3 * b:3 * e].view(3, H, W)
             res.append(d)
         return res
 
@@ -327,6 +365,43 @@ def l2_loss(pred: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tenso
     N.check(N.lib().svr_l2_loss(_ptr(pred), _ptr(target), pred.numel(), _ptr(grad), _ptr(loss),
                                 _stream(stream)), "svr_l2_loss")
     return loss, grad
+
+
+def supersampled_camera(cam, h_ss: float):
+    """The camera of an image h_ss times larger over the same image plane:
+    round(h_ss W) x round(h_ss H) pixels, intrinsics scaled by the exact
+    per-axis size ratio (Sec. 3.1.2 "Anti-aliasing")."""
+    Ws, Hs = int(round(h_ss * cam.width)), int(round(h_ss * cam.height))
+    sx, sy = Ws / cam.width, Hs / cam.height
+    return dataclasses.replace(cam, fx=np.float32(float(cam.fx) * sx), fy=np.float32(float(cam.fy) * sy),
+                               cx=np.float32(float(cam.cx) * sx), cy=np.float32(float(cam.cy) * sy),
+                               width=Ws, height=Hs)
+
+
+def downsample(src: torch.Tensor, height: int, width: int, dst: Optional[torch.Tensor] = None, stream=None):
+    """svr_downsample of src [..., H_ss, W_ss] (contiguous) to [..., height, width]."""
+    if not src.is_contiguous():
+        raise ValueError("src must be contiguous")
+    Hs, Ws = src.shape[-2], src.shape[-1]
+    planes = src.numel() // (Hs * Ws)
+    if dst is None:
+        dst = torch.empty(*src.shape[:-2], height, width, device=src.device, dtype=src.dtype)
+    N.check(N.lib().svr_downsample(_ptr(src), planes, Hs, Ws, _ptr(dst), height, width, _stream(stream)),
+            "svr_downsample")
+    return dst
+
+
+def downsample_bwd(grad: torch.Tensor, height_ss: int, width_ss: int, out: Optional[torch.Tensor] = None,
+                   stream=None):
+    """svr_downsample_bwd: the gradient of downsample for upstream grad."""
+    grad = grad.contiguous()
+    H, W = grad.shape[-2], grad.shape[-1]
+    planes = grad.numel() // (H * W)
+    if out is None:
+        out = torch.empty(*grad.shape[:-2], height_ss, width_ss, device=grad.device, dtype=grad.dtype)
+    N.check(N.lib().svr_downsample_bwd(_ptr(grad), planes, H, W, _ptr(out), height_ss, width_ss, _stream(stream)),
+            "svr_downsample_bwd")
+    return out
 
 
 def _device_copy(dst: int, src: int, nbytes: int):

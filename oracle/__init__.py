@@ -75,10 +75,10 @@ def lib():
                                      ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.oc_render_ex.restype = ctypes.c_int
         L.oc_render_ex.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P,
-                                   ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+                                   ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.oc_render_grad_ex.restype = ctypes.c_int
         L.oc_render_grad_ex.argtypes = [ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P,
-                                        ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+                                        ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.oc_trilinear.restype = ctypes.c_double
         L.oc_trilinear.argtypes = [P, P]
         L.oc_interp_grad_centre.restype = None
@@ -144,7 +144,7 @@ def _pixels(cam, pixels):
 
 
 def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, threads=None,
-           grid=None, sh=None, near_stop_rel=None, normals=False, max_weight=None):
+           grid=None, sh=None, near_stop_rel=None, normals=False, max_weight=None, distortion=False):
     """Brute-force FP64 render.  pixels: int [n, 2] of (x, y), or None for the
     whole image (outputs then reshaped to [H, W]).  grid / sh: optional FP64
     overrides of the scene's parameters (finite differences).
@@ -159,7 +159,9 @@ def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, thread
     normals=True adds "normal" ([3, H, W] or [n, 3]): the composited voxel
     normals of Eq. (vox_normal).  max_weight: an FP64 array [N] that is raised
     to each voxel's largest blending weight T_i alpha_i over these pixels
-    (pruning statistic, Sec. 3.2.2)."""
+    (pruning statistic, Sec. 3.2.2).  distortion=True adds "dist": each
+    ray's distortion loss (Sec. 3.2.3; Mip-NeRF 360's loss over the composited
+    voxels' weights, interval midpoints and lengths in ray distance)."""
     centre, level, corner, g, s = _scene_arrays(scene, grid, sh)
     n, px = _pixels(cam, pixels)
     out = dict(rgb=np.zeros((n, 3)), depth=np.zeros(n), alpha=np.zeros(n), t_final=np.zeros(n),
@@ -167,6 +169,8 @@ def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, thread
                stop_margin=np.zeros(n))
     if normals:
         out["normal"] = np.zeros((n, 3))
+    if distortion:
+        out["dist"] = np.zeros(n)
     if max_weight is not None:
         assert max_weight.dtype == np.float64 and max_weight.shape == (scene.n_vox,)
         assert max_weight.flags.c_contiguous
@@ -177,7 +181,7 @@ def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, thread
                             _ptr(px), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]),
                             _ptr(out["t_final"]), _ptr(out["n_comp"]), _ptr(out["term_vox"]),
                             _ptr(out["stop_margin"]), _ptr(out.get("normal")), _ptr(max_weight),
-                            _threads(threads))
+                            _ptr(out.get("dist")), _threads(threads))
     if rc != 0:
         raise RuntimeError(f"oc_render failed ({rc})")
     band = NEAR_STOP_REL if near_stop_rel is None else float(near_stop_rel)
@@ -187,14 +191,16 @@ def render(scene, cam, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, thread
         out["rgb"] = out["rgb"].reshape(H, W, 3).transpose(2, 0, 1).copy()
         if normals:
             out["normal"] = out["normal"].reshape(H, W, 3).transpose(2, 0, 1).copy()
-        for k in ("depth", "alpha", "t_final", "n_comp", "term_vox", "stop_margin", "near_stop"):
+        for k in ("depth", "alpha", "t_final", "n_comp", "term_vox", "stop_margin", "near_stop", "dist"):
+            if k not in out:
+                continue
             out[k] = out[k].reshape(H, W)
     return out
 
 
 def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 0.0, 0.0),
                 pixels=None, threads=None, grid=None, sh=None, magnitudes=None, g_normal=None,
-                priority=None):
+                priority=None, g_dist=None):
     """Analytic FP64 gradient of sum(g_rgb*C + g_depth*D + g_alpha*A).
     Full image: g_rgb [3, H, W], g_depth/g_alpha [H, W]; pixel list: g_rgb
     [n, 3], g_depth/g_alpha [n].  Returns (d_grid [Pts], d_sh [N, 48]).
@@ -209,9 +215,11 @@ def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 
     ray that grazes the voxel).
 
     g_normal ([3, H, W] or [n, 3]) adds g_normal . N to the objective (the
-    normal image of Eq. vox_normal).  priority: an FP64 array [N] to which
+    normal image of Eq. vox_normal); g_dist ([H, W] or [n]) adds g_dist times
+    each ray's distortion loss.  priority: an FP64 array [N] to which
     each voxel's subdivision priority sum |alpha_i dL/dalpha_i| over these
-    pixels is added (Eq. priority, Sec. 3.2.2)."""
+    pixels is added (Eq. priority, Sec. 3.2.2); with magnitudes also
+    "priority_seg", its terms weighted by their segment condition numbers."""
     centre, level, corner, g, s = _scene_arrays(scene, grid, sh)
     n, px = _pixels(cam, pixels)
     if pixels is None:
@@ -222,6 +230,7 @@ def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 
         if pixels is None:
             gn = gn.reshape(3, -1).T
         gn = np.ascontiguousarray(gn, np.float64).reshape(n, 3)
+    gdist = None if g_dist is None else np.ascontiguousarray(g_dist, np.float64).reshape(n)
     if priority is not None:
         assert priority.dtype == np.float64 and priority.shape == (scene.n_vox,)
         assert priority.flags.c_contiguous
@@ -233,17 +242,20 @@ def render_grad(scene, cam, g_rgb, g_depth, g_alpha, K=1, t_stop=1e-4, bg=(0.0, 
     want = magnitudes is not None
     a_grid, a_sh = (np.zeros(len(g)), np.zeros((scene.n_vox, 48))) if want else (None, None)
     k_grid, k_sh = (np.zeros(len(g)), np.zeros((scene.n_vox, 48))) if want else (None, None)
+    k_pr = np.zeros(scene.n_vox) if (want and priority is not None) else None
     c = camera_struct(cam)
     p = params_struct(K, t_stop, bg)
     rc = lib().oc_render_grad_ex(float(np.float32(scene.world_size)), scene.n_vox, _ptr(centre),
                                  _ptr(level), _ptr(corner), _ptr(g), _ptr(s), ctypes.byref(c),
-                                 ctypes.byref(p), n, _ptr(px), _ptr(gr), _ptr(gd), _ptr(ga), _ptr(gn),
+                                 ctypes.byref(p), n, _ptr(px), _ptr(gr), _ptr(gd), _ptr(ga), _ptr(gn), _ptr(gdist),
                                  _ptr(d_grid), _ptr(d_sh), _ptr(a_grid), _ptr(a_sh), _ptr(k_grid), _ptr(k_sh),
-                                 _ptr(priority), _threads(threads))
+                                 _ptr(priority), _ptr(k_pr), _threads(threads))
     if rc != 0:
         raise RuntimeError(f"oc_render_grad failed ({rc})")
     if magnitudes is not None:
         magnitudes.update(grid=a_grid, sh=a_sh, grid_seg=k_grid, sh_seg=k_sh)
+        if k_pr is not None:
+            magnitudes["priority_seg"] = k_pr
     return d_grid, d_sh
 
 

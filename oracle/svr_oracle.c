@@ -30,7 +30,11 @@
  *     centre in the closed form of Eq. (interp_grad), and its gradient
  *     (Eq. interp_grad_grad through the normalisation); per voxel the
  *     maximum blending weight max T_i alpha_i (pruning, Sec. 3.2.2) and the
- *     subdivision priority sum |alpha_i dL/dalpha_i| (Eq. priority).
+ *     subdivision priority sum |alpha_i dL/dalpha_i| (Eq. priority); the
+ *     distortion loss of each ray (Sec. 3.2.3, the loss of Mip-NeRF 360),
+ *     L = sum_i sum_j w_i w_j |m_i - m_j| + 1/3 sum_i w_i^2 delta_i over its
+ *     composited voxels, w_i = T_i alpha_i, m_i = (a_i + b_i) / 2 and
+ *     delta_i = b_i - a_i in ray distance t (camera depth), and its gradient.
  *
  * Voxel geometry: size v_s = w_s 2^-l (Eq. vox_coord); the centre is the
  * caller's value (the lattice check lives in the Python part of the oracle).
@@ -272,13 +276,14 @@ typedef struct {
     /* per composited hit */
     double *alpha, *T, *d, *col, *pre, *ell;
     double *nrm;   /* [3] voxel normal n of each hit, when normals are rendered */
+    double *cdist; /* dL_dist / dw_i of each hit, for the backward */
     double *gvec;  /* [3] unnormalised gradient of Eq. (interp_grad) of each hit */
     int64_t pcap;
 } oc_scratch;
 
 static void scratch_free(oc_scratch *s) {
     free(s->hits); free(s->alpha); free(s->T); free(s->d); free(s->col); free(s->pre); free(s->ell);
-    free(s->nrm); free(s->gvec);
+    free(s->nrm); free(s->gvec); free(s->cdist);
     memset(s, 0, sizeof(*s));
 }
 
@@ -315,6 +320,9 @@ static int scratch_comp(oc_scratch *s, int64_t n) {
     p = (double *)realloc(s->gvec, (size_t)c * 3 * sizeof(double));
     if (!p) return -1;
     s->gvec = p;
+    p = (double *)realloc(s->cdist, (size_t)c * sizeof(double));
+    if (!p) return -1;
+    s->cdist = p;
     s->pcap = c;
     return 0;
 }
@@ -380,12 +388,42 @@ static void voxel_colour(const oc_scene *S, int64_t v, const double ro[3], doubl
 typedef struct {
     double rgb[3], depth, alpha, t_final;
     double normal[3];  /* N = sum_i T_i alpha_i n_i (when normals are rendered) */
+    double dist;       /* distortion loss of the ray */
     int32_t n_comp;
     int64_t term_vox;  /* voxel whose compositing stopped the ray, or -1 */
     double stop_margin; /* min over composited voxels of |T after it / t_stop - 1| (HUGE_VAL: none) */
 } oc_pixel_out;
 
 #define OC_KMAX 8
+
+/* Distortion loss of the n composited hits of s (weights w_i = T_i alpha_i,
+ * interval midpoints m_i and lengths delta_i in ray distance), by its
+ * definition: every ordered pair and every interval on its own. */
+static double distortion(const oc_scratch *s, int32_t n) {
+    double L = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        double wi = s->T[i] * s->alpha[i], mi = 0.5 * (s->hits[i].a + s->hits[i].b);
+        for (int32_t j = 0; j < n; ++j) {
+            double wj = s->T[j] * s->alpha[j], mj = 0.5 * (s->hits[j].a + s->hits[j].b);
+            L += wi * wj * fabs(mi - mj);
+        }
+        L += wi * wi * (s->hits[i].b - s->hits[i].a) / 3.0;
+    }
+    return L;
+}
+
+/* dL_dist / dw_k for every composited hit k, into s->cdist:
+ * 2 sum_j w_j |m_k - m_j| + 2/3 w_k delta_k. */
+static void distortion_grad_w(const oc_scratch *s, int32_t n) {
+    for (int32_t k = 0; k < n; ++k) {
+        double mk = 0.5 * (s->hits[k].a + s->hits[k].b), acc = 0.0;
+        for (int32_t j = 0; j < n; ++j) {
+            double wj = s->T[j] * s->alpha[j], mj = 0.5 * (s->hits[j].a + s->hits[j].b);
+            acc += wj * fabs(mk - mj);
+        }
+        s->cdist[k] = 2.0 * acc + 2.0 / 3.0 * s->T[k] * s->alpha[k] * (s->hits[k].b - s->hits[k].a);
+    }
+}
 
 /* Front-to-back compositing of one pixel; fills the per-hit arrays of s.
  * with_normals: also composite the voxel normals; max_weight (may be NULL):
@@ -445,6 +483,7 @@ static int composite(const oc_scene *S, const oc_params *P, const double ro[3], 
     }
     for (int ch = 0; ch < 3; ++ch) o->rgb[ch] = C[ch] + T * P->bg[ch];
     for (int ax = 0; ax < 3; ++ax) o->normal[ax] = Nrm[ax];
+    o->dist = distortion(s, n);
     o->depth = D;
     o->alpha = 1.0 - T;
     o->t_final = T;
@@ -494,17 +533,24 @@ static void add_term(double *acc, double *acc_abs, double *acc_seg, int64_t i, d
  * alpha_i g_normal passes the normalisation, dL/dgrad = (dL/dn - n (n .
  * dL/dn)) / |grad|, and reaches corner c through Eq. (interp_grad_grad):
  * dgrad/dV_c = 0.25 (2 x_c - 1, 2 y_c - 1, 2 z_c - 1).  priority (may be
- * NULL) accumulates |alpha_i dL/dalpha_i| per voxel (Eq. priority). */
+ * NULL) accumulates |alpha_i dL/dalpha_i| per voxel (Eq. priority) and
+ * priority_seg (may be NULL) the same terms times the segment condition. */
 static void pixel_backward(const oc_scene *S, const oc_params *P, const double ro[3], const double rd[3],
                            const oc_scratch *s, const oc_pixel_out *o, const double g_rgb[3],
-                           double g_depth, double g_alpha, const double *g_normal, double *d_grid, double *d_sh,
+                           double g_depth, double g_alpha, const double *g_normal, double g_dist,
+                           double *d_grid, double *d_sh,
                            double *d_grid_abs, double *d_sh_abs, double *d_grid_seg, double *d_sh_seg,
-                           double *priority) {
+                           double *priority, double *priority_seg) {
     const int K = P->K;
     int32_t n = o->n_comp;
     double RC[3] = {P->bg[0], P->bg[1], P->bg[2]};
     double RN[3] = {0.0, 0.0, 0.0};
-    double RD = 0.0, Sfx = 1.0;
+    double RD = 0.0, Sfx = 1.0, RW = 0.0;
+    /* the distortion loss depends on the weights w_j = T_j alpha_j only, so
+     * it enters dL/dalpha_i like a colour c_j = dL_dist/dw_j with no
+     * background: T_i (c_i - RW_i), RW_i = alpha_{i+1} c_{i+1} + (1 -
+     * alpha_{i+1}) RW_{i+1} */
+    if (g_dist != 0.0) distortion_grad_w(s, n);
     for (int32_t i = n - 1; i >= 0; --i) {
         int64_t v = s->hits[i].v;
         double a = s->hits[i].a, b = s->hits[i].b;
@@ -519,9 +565,14 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
         const double *nv = g_normal ? s->nrm + 3 * i : NULL;
         if (g_normal)
             for (int ax = 0; ax < 3; ++ax) g += g_normal[ax] * Ti * (nv[ax] - RN[ax]);
+        if (g_dist != 0.0) g += g_dist * Ti * (s->cdist[i] - RW);
         if (priority) {
 #pragma omp atomic
             priority[v] += fabs(al * g);
+        }
+        if (priority_seg) {
+#pragma omp atomic
+            priority_seg[v] += fabs(al * g) * kappa;
         }
 
         double t[OC_KMAX], val[OC_KMAX], w[OC_KMAX][8], ak[OC_KMAX];
@@ -580,6 +631,7 @@ static void pixel_backward(const oc_scene *S, const oc_params *P, const double r
         for (int ch = 0; ch < 3; ++ch) RC[ch] = al * c[ch] + (1.0 - al) * RC[ch];
         if (g_normal)
             for (int ax = 0; ax < 3; ++ax) RN[ax] = al * nv[ax] + (1.0 - al) * RN[ax];
+        if (g_dist != 0.0) RW = al * s->cdist[i] + (1.0 - al) * RW;
         RD = s->d[i] + (1.0 - al) * RD;
         Sfx *= 1.0 - al;
     }
@@ -605,13 +657,15 @@ static void pixel_xy(const oc_camera *cam, int64_t n_px, const int32_t *px_xy, i
  * the stop threshold (HUGE_VAL if t_stop = 0 or nothing was composited), which
  * says how close the pixel came to another termination decision.  normal
  * (may be NULL): [n_px][3] composited voxel normals; max_weight (may be NULL):
- * [N], raised to the largest T_i alpha_i of each voxel over these pixels.
+ * [N], raised to the largest T_i alpha_i of each voxel over these pixels;
+ * dist (may be NULL): [n_px] distortion loss of each pixel's ray.
  * Returns 0, or -1 on allocation failure. */
 int oc_render_ex(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
                  const int32_t *corner_idx, const double *grid, const double *sh,
                  const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
                  double *rgb, double *depth, double *alpha, double *t_final, int32_t *n_comp,
-                 int64_t *term_vox, double *stop_margin, double *normal, double *max_weight, int n_threads) {
+                 int64_t *term_vox, double *stop_margin, double *normal, double *max_weight, double *dist,
+                 int n_threads) {
     oc_scene S = {world_size, n_vox, centre, level, corner_idx, grid, sh};
     if (P->K < 1 || P->K > OC_KMAX) return -2;
     int err = 0;
@@ -646,6 +700,7 @@ int oc_render_ex(double world_size, int64_t n_vox, const double *centre, const u
             if (stop_margin) stop_margin[p] = o.stop_margin;
             if (normal)
                 for (int ax = 0; ax < 3; ++ax) normal[3 * p + ax] = o.normal[ax];
+            if (dist) dist[p] = o.dist;
         }
         scratch_free(&s);
     }
@@ -658,21 +713,24 @@ int oc_render(double world_size, int64_t n_vox, const double *centre, const uint
               double *rgb, double *depth, double *alpha, double *t_final, int32_t *n_comp,
               int64_t *term_vox, double *stop_margin, int n_threads) {
     return oc_render_ex(world_size, n_vox, centre, level, corner_idx, grid, sh, cam, P, n_px, px_xy, rgb, depth,
-                        alpha, t_final, n_comp, term_vox, stop_margin, NULL, NULL, n_threads);
+                        alpha, t_final, n_comp, term_vox, stop_margin, NULL, NULL, NULL, n_threads);
 }
 
 /* Gradient of sum_p (g_rgb[p] . C_p + g_depth[p] D_p + g_alpha[p] A_p) with
  * respect to grid (accumulated into d_grid[Pts]) and sh (accumulated into
  * d_sh[N][48]).  Same pixel convention as oc_render.  g_normal (may be NULL):
  * [n_px][3] upstream gradient of the normal image, which adds
- * sum_p g_normal[p] . N_p to the objective; priority (may be NULL): [N],
+ * sum_p g_normal[p] . N_p to the objective; g_dist (may be NULL): [n_px],
+ * adds sum_p g_dist[p] L_dist,p; priority (may be NULL): [N],
  * accumulates the subdivision priority of Eq. (priority). */
 int oc_render_grad_ex(double world_size, int64_t n_vox, const double *centre, const uint8_t *level,
                       const int32_t *corner_idx, const double *grid, const double *sh,
                       const oc_camera *cam, const oc_params *P, int64_t n_px, const int32_t *px_xy,
                       const double *g_rgb, const double *g_depth, const double *g_alpha, const double *g_normal,
+                      const double *g_dist,
                       double *d_grid, double *d_sh, double *d_grid_abs, double *d_sh_abs,
-                      double *d_grid_seg, double *d_sh_seg, double *priority, int n_threads) {
+                      double *d_grid_seg, double *d_sh_seg, double *priority, double *priority_seg,
+                      int n_threads) {
     oc_scene S = {world_size, n_vox, centre, level, corner_idx, grid, sh};
     if (P->K < 1 || P->K > OC_KMAX) return -2;
     int err = 0;
@@ -699,8 +757,9 @@ int oc_render_grad_ex(double world_size, int64_t n_vox, const double *centre, co
                 continue;
             }
             pixel_backward(&S, P, ro, rd, &s, &o, g_rgb + 3 * p, g_depth[p], g_alpha[p],
-                           g_normal ? g_normal + 3 * p : NULL, d_grid, d_sh, d_grid_abs, d_sh_abs, d_grid_seg,
-                           d_sh_seg, priority);
+                           g_normal ? g_normal + 3 * p : NULL, g_dist ? g_dist[p] : 0.0, d_grid, d_sh, d_grid_abs,
+                           d_sh_abs, d_grid_seg,
+                           d_sh_seg, priority, priority_seg);
         }
         scratch_free(&s);
     }
@@ -714,8 +773,8 @@ int oc_render_grad(double world_size, int64_t n_vox, const double *centre, const
                    double *d_grid, double *d_sh, double *d_grid_abs, double *d_sh_abs,
                    double *d_grid_seg, double *d_sh_seg, int n_threads) {
     return oc_render_grad_ex(world_size, n_vox, centre, level, corner_idx, grid, sh, cam, P, n_px, px_xy, g_rgb,
-                             g_depth, g_alpha, NULL, d_grid, d_sh, d_grid_abs, d_sh_abs, d_grid_seg, d_sh_seg,
-                             NULL, n_threads);
+                             g_depth, g_alpha, NULL, NULL, d_grid, d_sh, d_grid_abs, d_sh_abs, d_grid_seg,
+                             d_sh_seg, NULL, NULL, n_threads);
 }
 
 /* Sorted hit list of an arbitrary ray (for order checks): writes up to cap

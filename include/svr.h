@@ -301,12 +301,27 @@ SVR_API int svr_render_batched(svr_frame *frame, const svr_scene *scene, const s
  *               (the upstream gradients of all images, normals included) with
  *               respect to the voxel's alpha in the compositing of Eq.
  *               alpha_blend, its colour, normal and depth held fixed.
+ *   distortion  forward output [2][H][W] (batch: 2 planes per view, at
+ *               2 pixel_base[v]): plane 0 the distortion loss of each ray
+ *               (Sec. 3.2.3, the loss of Mip-NeRF 360) over its composited
+ *               voxels, L = sum_ij w_i w_j |m_i - m_j| + 1/3 sum_i w_i^2
+ *               delta_i with w_i = T_i alpha_i, m_i = (a_i + b_i) / 2 and
+ *               delta_i = b_i - a_i in ray distance (camera depth); plane 1
+ *               sum_i w_i m_i, which the backward needs.  Also read by the
+ *               backward when d_distortion is set.
+ *   d_distortion backward input [H][W]: dL/dL_dist per ray (e.g. the loss
+ *               weight over the pixel count).  Requires `distortion` from
+ *               the frame's last forward of this sort (split tiles carry the
+ *               distortion sums; otherwise they are skipped and
+ *               SVR_FLAG_NO_FORWARD is raised).
  */
 typedef struct svr_render_extras {
     float *normal;
     float *max_weight;
     const float *d_normal;
     float *priority;
+    float *distortion;
+    const float *d_distortion;
 } svr_render_extras;
 
 /* svr_render_fwd plus the forward members of *extras (NULL: none). */
@@ -386,6 +401,40 @@ SVR_API int svr_downsample_bwd(const float *d_dst, int64_t planes, int height, i
  */
 SVR_API int svr_l2_loss(const float *pred, const float *target, int64_t n, float *grad,
                         float *loss, void *stream);
+
+/*
+ * Training-step pieces (Sec. 3.2.3 objectives; optimizer settings of the
+ * supplementary's implementation details).  Device pointers; enqueue only.
+ *
+ * svr_t_concentration_loss: the transmittance-concentration loss L_T, which
+ * pushes each ray's final transmittance T = 1 - alpha toward 0 or 1 (the
+ * paper gives no formula; read as the binary entropy -(T ln T + (1 - T)
+ * ln(1 - T)) with T clamped to [1e-6, 1 - 1e-6]).  Adds weight * mean over
+ * the n pixels to *loss (the caller clears it, or svr_l2_loss wrote it) and,
+ * if grad_alpha is not NULL, overwrites grad_alpha[i] with the gradient with
+ * respect to alpha[i] (zero where the clamp acts).
+ */
+SVR_API int svr_t_concentration_loss(const float *alpha, int64_t n, float weight, float *grad_alpha,
+                                     float *loss, void *stream);
+
+/* Adds weight * mean(x[0..n)) to *loss (e.g. the distortion losses of the
+ * rays from the distortion output of svr_render_fwd_ex, times lambda_dist). */
+SVR_API int svr_weighted_mean(const float *x, int64_t n, float weight, float *loss, void *stream);
+
+/*
+ * One Adam step (Kingma and Ba) on n parameters: m = beta1 m + (1 - beta1) g,
+ * v = beta2 v + (1 - beta2) g^2, param -= lr (m / (1 - beta1^step)) /
+ * (sqrt(v / (1 - beta2^step)) + eps), with lr = lr_head for the elements whose
+ * index modulo `period` is below `head` and lr_rest for the others (the SH
+ * array [N][48]: period 48, head 3 gives the degree-0 coefficients their own
+ * rate; the paper: 0.01 for them, 0.00025 for the rest, 0.025 for the grid
+ * densities, (beta1, beta2) = (0.1, 0.99), eps = 1e-15).  step counts from 1;
+ * m and v start at zero and are updated in place.  SVR_ERR_INVALID for a bad
+ * period/head/step or betas outside [0, 1).
+ */
+SVR_API int svr_adam(float *param, const float *grad, float *m, float *v, int64_t n, int32_t period,
+                     int32_t head, float lr_head, float lr_rest, float beta1, float beta2, float eps,
+                     int64_t step, void *stream);
 
 /* Synchronises the stream and reads the device-side error flags
  * (SVR_FLAG_*) and the pair count of a frame.  Either output may be NULL. */

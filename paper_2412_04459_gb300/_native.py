@@ -62,7 +62,8 @@ class SvrBuffers(ctypes.Structure):
 
 
 class SvrRenderExtras(ctypes.Structure):
-    _fields_ = [("normal", _P), ("max_weight", _P), ("d_normal", _P), ("priority", _P)]
+    _fields_ = [("normal", _P), ("max_weight", _P), ("d_normal", _P), ("priority", _P), ("distortion", _P),
+                ("d_distortion", _P)]
 
 
 class SvrError(RuntimeError):
@@ -94,6 +95,10 @@ SIGNATURES = {
                                       ctypes.c_int, _P]),
     "svr_downsample_bwd": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
                                           ctypes.c_int, _P]),
+    "svr_t_concentration_loss": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "svr_weighted_mean": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P]),
+    "svr_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int64, _P]),
     "svr_frame_status": (ctypes.c_int, [_P, _P, _P, _P]),
     "svr_frame_buffers": (ctypes.c_int, [_P, _P]),
     "svr_last_error": (ctypes.c_char_p, []),

@@ -383,7 +383,7 @@ SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, flo
     if (!frame || frame->stage < 2) return fail(SVR_ERR_INVALID, "frame not sorted");
     if (!rgb || !depth || !alpha || !T_final || !last) return fail(SVR_ERR_INVALID, "null output");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr, nullptr, nullptr,
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr, nullptr, nullptr, nullptr,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_fwd");
     return SVR_OK;
@@ -396,9 +396,10 @@ SVR_API int svr_render_fwd_ex(const svr_frame *frame, float *rgb, float *depth, 
     if (!rgb || !depth || !alpha || !T_final || !last) return fail(SVR_ERR_INVALID, "null output");
     float *normal = extras ? extras->normal : nullptr;
     float *max_weight = extras ? extras->max_weight : nullptr;
+    float *dist = extras ? extras->distortion : nullptr;
     if (max_weight && (((uintptr_t)max_weight) & 3u)) return fail(SVR_ERR_INVALID, "max_weight not 4-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
-    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr, normal, max_weight,
+    cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, nullptr, normal, max_weight, dist,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_fwd_ex");
     return SVR_OK;
@@ -412,7 +413,7 @@ SVR_API int svr_render_stats(const svr_frame *frame, float *rgb, float *depth, f
     if (((uintptr_t)counts) & 7u) return fail(SVR_ERR_INVALID, "counts not 8-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
     cudaError_t e = svr::launch_render_fwd(d, rgb, depth, alpha, T_final, last, (int2 *)counts, nullptr, nullptr,
-                                           (cudaStream_t)stream);
+                                           nullptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_stats");
     return SVR_OK;
 }
@@ -427,7 +428,7 @@ SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const flo
     if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
     cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid,
-                                           d_sh, nullptr, nullptr, (cudaStream_t)stream);
+                                           d_sh, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
     return SVR_OK;
 }
@@ -442,9 +443,12 @@ SVR_API int svr_render_bwd_ex(const svr_frame *frame, const float *d_rgb, const 
     if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
     const float *d_normal = extras ? extras->d_normal : nullptr;
     float *priority = extras ? extras->priority : nullptr;
+    const float *d_dist = extras ? extras->d_distortion : nullptr;
+    const float *dist = extras ? extras->distortion : nullptr;
+    if (d_dist && !dist) return fail(SVR_ERR_INVALID, "d_distortion needs the forward's distortion output");
     const svr::FrameDev d = frame_dev(frame);
     cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_sh, d_normal,
-                                           priority, (cudaStream_t)stream);
+                                           priority, d_dist, dist, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd_ex");
     return SVR_OK;
 }

@@ -467,6 +467,7 @@ struct FwdOut {
     int2 *stats;
     float *normal;      // extras: [3][H][W] composited voxel normals, or NULL
     float *max_weight;  // extras: [N] per-voxel maximum of T_i alpha_i, raised with atomicMax, or NULL
+    float *dist;        // extras: [2][H][W] distortion loss of each ray and sum_i w_i m_i, or NULL
 };
 
 // Forward variants: the plain render, the work-counting one, and the one with
@@ -480,7 +481,24 @@ struct FwdState {
     bool done;
     int n_cand, n_hit;
     float N0, N1, N2;  // composited normal (extras)
+    // distortion loss (extras): the loss so far, and the sums of the weights
+    // w_i = T_i alpha_i and of w_i m_i (m_i the segment's midpoint) so far
+    float LD, PW, PS;
 };
+
+// Distortion loss (Sec. 3.2.3, the loss of Mip-NeRF 360) over a ray's
+// composited voxels, with weights w_i, interval midpoints m_i = (a_i + b_i) / 2
+// and lengths delta_i = b_i - a_i in ray distance:
+//   L = sum_i sum_j w_i w_j |m_i - m_j| + 1/3 sum_i w_i^2 delta_i.
+// Front to back (the voxels' intervals do not overlap, so m grows along the
+// list) each voxel adds 2 w_i (m_i W_<i - S_<i) + w_i^2 delta_i / 3 with the
+// prefix sums W_<i = sum_{j<i} w_j, S_<i = sum_{j<i} w_j m_j.
+__device__ __forceinline__ void dist_add(FwdState &s, float w, float a, float b) {
+    const float m = 0.5f * (a + b);
+    s.LD += fmaf(2.f * w, fmaf(m, s.PW, -s.PS), w * w * (b - a) * 0.333333333f);
+    s.PW += w;
+    s.PS = fmaf(w, m, s.PS);
+}
 
 // Voxel normal of Eq. vox_normal from the 8 raw corner densities (corner c:
 // bit 2 = x, bit 1 = y, bit 0 = z; g0 = corners 0..3, g1 = 4..7): the
@@ -646,6 +664,7 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                         s.N1 = fmaf(w, n.y, s.N1);
                         s.N2 = fmaf(w, n.z, s.N2);
                     }
+                    if (out.dist) dist_add(s, w, a, b);
                     // weights are exact only when the walk started from the
                     // true transmittance (not a split segment's T = 1)
                     if (out.max_weight && true_weights)
@@ -690,6 +709,9 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
         float *q = seg_fields(f, L.ts.y + sg, blk);
         const float Tb = m.T;
         float c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+        // distortion: the segment's internal loss and its sums of w, w m
+        float dl_b = 0.f, dw_b = 0.f, ds_b = 0.f;
+        const float W_before = m.PW, S_before = m.PS, L_before = m.LD;
         bool need = false;
         if (!m.done) {
             const float Tl = __ldcg(q + 4 * 32);
@@ -704,6 +726,10 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
                     n0 = Tb * __ldcg(q + 8 * 32);
                     n1 = Tb * __ldcg(q + 9 * 32);
                     n2 = Tb * __ldcg(q + 10 * 32);
+                    // segment walked from T = 1: its weights scale by Tb
+                    dl_b = Tb * Tb * __ldcg(q + 11 * 32);
+                    dw_b = Tb * __ldcg(q + 12 * 32);
+                    ds_b = Tb * __ldcg(q + 13 * 32);
                 }
                 m.T = Tb * Tl;
                 if (Tb * Tl < f.t_stop) {  // segment 0 stopped by itself
@@ -719,7 +745,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             }
         }
         if (__any_sync(0xffffffffu, need)) {
-            FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0, 0.f, 0.f, 0.f};
+            FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             int p0, p1;
             seg_range(L, B, sg, p0, p1);
             fwd_walk<K, MODE>(L.list, p0, p1, vd, p, wb, ws, f.t_stop, r, out, true);
@@ -731,6 +757,9 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
                 n0 = r.N0;
                 n1 = r.N1;
                 n2 = r.N2;
+                dl_b = r.LD;
+                dw_b = r.PW;
+                ds_b = r.PS;
                 m.T = r.T;
                 if (r.done) {
                     m.done = true;
@@ -757,10 +786,22 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             q[8 * 32] = n0;
             q[9 * 32] = n1;
             q[10 * 32] = n2;
+            // the segment's pairs with the voxels before it
+            m.LD = L_before + dl_b + 2.f * (ds_b * W_before - dw_b * S_before);
+            m.PW = W_before + dw_b;
+            m.PS = S_before + ds_b;
+            q[11 * 32] = dl_b;
+            q[12 * 32] = dw_b;
+            q[13 * 32] = ds_b;
         }
     }
-    // sums behind each segment, back to front
+    // sums behind each segment, back to front; for the distortion loss the
+    // weight sums behind it and sum_{j behind} w_j dL/dw_j, where a segment B
+    // with A in front and C behind contributes 2 L_B + 2 (S_B W_A - W_B S_A)
+    // + 2 (W_B S_C - S_B W_C) (L_B its internal loss, W, S the sums of w, w m)
     float S0 = m.T * f.bg[0], S1 = m.T * f.bg[1], S2 = m.T * f.bg[2], SD = 0.f, SN0 = 0.f, SN1 = 0.f, SN2 = 0.f;
+    float WC = 0.f, SCc = 0.f, RWC = 0.f;
+    const float W_tot = m.PW, S_tot = m.PS;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         float *q = seg_fields(f, L.ts.y + sg, blk);
         const float c0 = q[0], c1 = q[32], c2 = q[2 * 32], dd = q[3 * 32];
@@ -780,6 +821,14 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             SN0 += n0;
             SN1 += n1;
             SN2 += n2;
+            const float dl_b = q[11 * 32], dw_b = q[12 * 32], ds_b = q[13 * 32];
+            const float WA = W_tot - WC - dw_b, SA = S_tot - SCc - ds_b;
+            q[11 * 32] = WC;
+            q[12 * 32] = SCc;
+            q[13 * 32] = RWC;
+            RWC += 2.f * dl_b + 2.f * (ds_b * WA - dw_b * SA) + 2.f * (dw_b * SCc - ds_b * WC);
+            WC += dw_b;
+            SCc += ds_b;
         }
     }
 }
@@ -808,6 +857,11 @@ __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, 
         nrm[HW] = s.N1;
         nrm[2 * HW] = s.N2;
     }
+    if (EXTRA && out.dist) {
+        float *dst = out.dist + 2 * (size_t)cam.pix_base + px;
+        dst[0] = s.LD;
+        dst[HW] = s.PS;
+    }
 }
 
 template <int K, int MODE>
@@ -820,7 +874,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
     if (wb.smask == 0) return;  // the whole block lies outside the image
     const ItemList L = item_list(f, it.g, it.blk);
     const int lane = threadIdx.x & 31;
-    FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f};
+    FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (L.ts.x <= 1) {
         fwd_walk<K, MODE>(L.list, 0, L.n_list, iv.vd, p, wb, ws, f.t_stop, s, out, true);
         fwd_write<MODE>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
@@ -846,6 +900,9 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
         q[8 * 32] = s.N0;
         q[9 * 32] = s.N1;
         q[10 * 32] = s.N2;
+        q[11 * 32] = s.LD;
+        q[12 * 32] = s.PW;
+        q[13 * 32] = s.PS;
     }
     __threadfence();
     __syncwarp();
@@ -856,7 +913,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
     if (prev + 1 != L.ts.x) return;
     // the last segment of the block to finish merges them all
     __threadfence();
-    FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f};
+    FwdState m = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     fwd_merge<K, MODE>(f, L, it.blk, iv.vd, p, wb, ws, m, out);
     fwd_write<MODE>(f, cam, p, m, m.last >= 0 ? m.last : L.end - 1, out);
     if (lane == 0) *cnt = 0;  // ready for the next forward of this sort
@@ -885,8 +942,10 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
         if (atomicAdd(&f.status->fwd_exit, 1u) == gridDim.x * (blockDim.x >> 5) - 1) {
             f.status->fwd_next = 0;
             f.status->fwd_exit = 0;
-            // 2: the segment sums include the normal image
-            f.status->fwd_done = (MODE == kModeExtra && out.normal) ? 2u : 1u;
+            // bit 1: the segment sums include the normal image, bit 2: the
+            // distortion sums
+            f.status->fwd_done = 1u | ((MODE == kModeExtra && out.normal) ? 2u : 0u) |
+                                 ((MODE == kModeExtra && out.dist) ? 4u : 0u);
         }
     }
 }
@@ -897,6 +956,13 @@ struct PixelGrad {
     float gC0, gC1, gC2, gD, gA;
     float Tfin;
     float gN0, gN1, gN2;  // upstream gradient of the normal image (extras)
+    float gL;             // upstream gradient of the ray's distortion loss (extras)
+    float Wtot, Stot;     // its totals sum w_i = 1 - T_final and sum w_i m_i
+};
+
+// Distortion sums behind a voxel: of w_j, of w_j m_j and of w_j dL/dw_j.
+struct DistSums {
+    float W, S, R;
 };
 
 // Sums of the normal image behind a voxel (extras; like SC for colour).
@@ -915,11 +981,15 @@ struct NrmSums {
 // like SC; nrm returns the voxel's normal) and prio returns the voxel's
 // subdivision priority term |alpha dL/dalpha| (Eq. priority), alpha dL/dalpha
 // = alpha / (1 - alpha) dL/dx with x the optical depth.
+// With the distortion loss (g.gL != 0): dL/dw_i = 2 (m_i W_<i - S_<i) +
+// 2 (S_>i - m_i W_>i) + 2/3 w_i delta_i (returned in cdist, prefix sums as the
+// totals minus the sums behind, DS, and the voxel's own), and it joins dL/dx_i
+// like a colour: T_(i+1) dL/dw_i - sum_{j>i} w_j dL/dw_j.
 template <int K, bool B2F, bool EXTRA>
 __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, const PixelGrad &g, float a, float b,
                                          float T_known, float SC0, float SC1, float SC2, float SD, NrmSums SN,
-                                         float dgeo[8], float dcol[3], float &T_i, float &T_after, float &w,
-                                         float &dloc, float3 &nrm, float &prio) {
+                                         DistSums DS, float dgeo[8], float dcol[3], float &T_i, float &T_after,
+                                         float &w, float &dloc, float3 &nrm, float &prio, float &cdist) {
     const float inv_k = 1.0f / K;
     const float seg = b - a;
     const float xs = seg * p.rdn * inv_k;
@@ -978,6 +1048,12 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     if (EXTRA) {
         gx += g.gN0 * fmaf(T_after, nrm.x, -SN.x) + g.gN1 * fmaf(T_after, nrm.y, -SN.y) +
               g.gN2 * fmaf(T_after, nrm.z, -SN.z);
+        if (g.gL != 0.f) {
+            const float m = 0.5f * (a + b);
+            const float Wlt = g.Wtot - DS.W - w, Slt = g.Stot - DS.S - w * m;
+            cdist = 2.f * (fmaf(m, Wlt, -Slt) + fmaf(-m, DS.W, DS.S)) + 0.666666667f * w * (b - a);
+            gx += g.gL * fmaf(T_after, cdist, -DS.R);
+        }
         prio = fabsf(gx * al / fmaxf(trans, 1e-30f));
     }
     // per-sample depth term, suffix Q_k = sum_{m>k} P_m (1 - e_m) t_m
@@ -1134,6 +1210,8 @@ struct BwdIn {
     float *d_grid;
     const float *d_normal;  // extras: upstream gradient of the normal image [3][H][W], or NULL
     float *priority;        // extras: [N] subdivision priority, accumulated, or NULL
+    const float *d_dist;    // extras: upstream gradient of each ray's distortion loss [H][W], or NULL
+    const float *dist;      // extras: the forward's [2][H][W] distortion output (plane 1: sum w m)
 };
 
 // Front-to-back gradients for the pixels of an item whose transmittance
@@ -1145,14 +1223,16 @@ struct BwdIn {
 template <int K, bool EXTRA>
 __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList L, int p0, int p1, int idx0,
                                                int last, bool fallback, float T_before, float SC0, float SC1, float SC2,
-                                               float SD, NrmSums SN, const ViewData vd, const WarpBlock wb,
-                                               const PixelRay p, const PixelGrad g, Entry *st, RecSmem &rs,
-                                               const BwdIn &in, float *dcol) {
+                                               float SD, NrmSums SN, DistSums DSb, const ViewData vd,
+                                               const WarpBlock wb, const PixelRay p, const PixelGrad g, Entry *st,
+                                               RecSmem &rs, const BwdIn &in, float *dcol) {
     const int lane = threadIdx.x & 31;
     const int n_fb = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : idx0));
     // sweep 1: this part's own sums, from the transmittance in front of it
+    // (distortion: the part's internal loss and sums of w, w m)
     float T = T_before, Ct0 = 0.f, Ct1 = 0.f, Ct2 = 0.f, Dt = 0.f;
     NrmSums Nt = {0.f, 0.f, 0.f};
+    FwdState dp = {};
     for (int base = p0; base < n_fb; base += kBatch) {
         Lookahead cur;
         fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
@@ -1177,6 +1257,7 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                     Nt.x = fmaf(w, n.x, Nt.x);
                     Nt.y = fmaf(w, n.y, Nt.y);
                     Nt.z = fmaf(w, n.z, Nt.z);
+                    if (g.gL != 0.f) dist_add(dp, w, a, b);
                 }
                 T *= trans;
             }
@@ -1190,9 +1271,14 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
     Nt.x += SN.x;
     Nt.y += SN.y;
     Nt.z += SN.z;
+    // distortion: sum w dL/dw over this part (its internal pairs twice, its
+    // pairs with the voxels in front A and behind C) plus the part's behind
+    const float WA = g.Wtot - dp.PW - DSb.W, SA = g.Stot - dp.PS - DSb.S;
+    const float Rt = 2.f * dp.LD + 2.f * (dp.PS * WA - dp.PW * SA) + 2.f * (dp.PW * DSb.S - dp.PS * DSb.W) + DSb.R;
     // sweep 2: gradients with the sums behind = total - prefix
     float Tf = T_before, PC0 = 0.f, PC1 = 0.f, PC2 = 0.f, PD = 0.f;
     NrmSums PN = {0.f, 0.f, 0.f};
+    float PW = 0.f, PS = 0.f, PR = 0.f;
     for (int base = p0; base < n_fb; base += kBatch) {
         Lookahead cur;
         fetch_vi(cur, L.list, base + lane, base + lane < n_fb);
@@ -1219,11 +1305,30 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 const Entry &e = st[k];
                 float a, b;
                 slab(e, p, a, b);
-                float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f;
+                float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f, cdist = 0.f;
                 float3 n;
                 const NrmSums Nb = {Nt.x - PN.x, Nt.y - PN.y, Nt.z - PN.z};
-                hit_grad<K, false, EXTRA>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, Nb, dgeo,
-                                          dc, T_i, Ta, w, dloc, n, prio);
+                // the voxel's own w is only known inside hit_grad: pass the
+                // sums behind it including its own share and let the
+                // distortion term subtract it (see below)
+                float w_own = 0.f, m_own = 0.f, c_own = 0.f;
+                if (EXTRA && g.gL != 0.f) {
+                    float tr, dl, al_;
+                    hit_fwd<K>(e, p, a, b, tr, dl, al_);
+                    w_own = Tf * al_;
+                    m_own = 0.5f * (a + b);
+                }
+                const DistSums Db = {g.Wtot - WA - PW - w_own, g.Stot - SA - PS - w_own * m_own, 0.f};
+                DistSums Dx = Db;
+                if (EXTRA && g.gL != 0.f) {
+                    // dL/dw of this voxel from the prefix and suffix sums
+                    const float Wlt = WA + PW, Slt = SA + PS;
+                    c_own = 2.f * (fmaf(m_own, Wlt, -Slt) + fmaf(-m_own, Db.W, Db.S)) +
+                            0.666666667f * w_own * (b - a);
+                    Dx.R = Rt - PR - w_own * c_own;
+                }
+                hit_grad<K, false, EXTRA>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, Nb, Dx, dgeo,
+                                          dc, T_i, Ta, w, dloc, n, prio, cdist);
                 PC0 = fmaf(w, e.col.x, PC0);
                 PC1 = fmaf(w, e.col.y, PC1);
                 PC2 = fmaf(w, e.col.z, PC2);
@@ -1232,6 +1337,11 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                     PN.x = fmaf(w, n.x, PN.x);
                     PN.y = fmaf(w, n.y, PN.y);
                     PN.z = fmaf(w, n.z, PN.z);
+                    if (g.gL != 0.f) {
+                        PW += w_own;
+                        PS = fmaf(w_own, m_own, PS);
+                        PR = fmaf(w_own, c_own, PR);
+                    }
                 }
                 Tf = Ta;
                 rec_write(rs, rec_slot(rs, k, rb), dgeo, dc, prio);
@@ -1261,7 +1371,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     const size_t px = (size_t)p.y * cam.W + p.x;
     const size_t o = (size_t)cam.pix_base + px;
 
-    PixelGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
+    PixelGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int last = beg - 1;
     if (p.inside) {
         if (in.d_rgb) {
@@ -1279,6 +1389,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             g.gN2 = gn[2 * HW];
         }
         g.Tfin = in.T[o];
+        if (EXTRA && in.d_dist) {
+            g.gL = in.d_dist[o];
+            g.Wtot = 1.f - g.Tfin;
+            g.Stot = in.dist[2 * (size_t)cam.pix_base + HW + px];
+        }
         last = max(beg - 1, min(in.last[o], L.end - 1));   // stay inside the tile's list
     }
     // The part of the list this item covers and the state behind it: the
@@ -1288,10 +1403,13 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     float T_after = g.Tfin, T_before = 1.f;
     float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
     NrmSums SN = {0.f, 0.f, 0.f};
+    DistSums DS = {0.f, 0.f, 0.f};
     if (L.ts.x > 1) {
         // a split tile starts from the segment sums of this sort's forward,
-        // which must include the normal image when its gradient is asked for
-        if (f.status->fwd_done == 0 || (EXTRA && in.d_normal && f.status->fwd_done != 2u)) {
+        // which must include the normal image and the distortion sums when
+        // their gradients are asked for
+        const unsigned done = f.status->fwd_done;
+        if (done == 0 || (EXTRA && in.d_normal && !(done & 2u)) || (EXTRA && in.d_dist && !(done & 4u))) {
             if (lane == 0) atomicOr(&f.status->flags, SVR_FLAG_NO_FORWARD);
             return;
         }
@@ -1308,6 +1426,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             SN.x = q[8 * 32];
             SN.y = q[9 * 32];
             SN.z = q[10 * 32];
+            if (in.d_dist) {
+                DS.W = q[11 * 32];
+                DS.S = q[12 * 32];
+                DS.R = q[13 * 32];
+            }
         }
     }
     const bool has = p.inside && last >= idx0;
@@ -1350,10 +1473,10 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     const Entry &e = st[k];
                     float a, b;
                     slab(e, p, a, b);
-                    float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f;
+                    float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f, cdist = 0.f;
                     float3 n;
-                    hit_grad<K, true, EXTRA>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, SN, dgeo, dc, T_i, Ta, w,
-                                             dloc, n, prio);
+                    hit_grad<K, true, EXTRA>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, SN, DS, dgeo, dc, T_i, Ta, w,
+                                             dloc, n, prio, cdist);
                     SC0 = fmaf(w, e.col.x, SC0);
                     SC1 = fmaf(w, e.col.y, SC1);
                     SC2 = fmaf(w, e.col.z, SC2);
@@ -1362,6 +1485,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                         SN.x = fmaf(w, n.x, SN.x);
                         SN.y = fmaf(w, n.y, SN.y);
                         SN.z = fmaf(w, n.z, SN.z);
+                        if (g.gL != 0.f) {
+                            DS.W += w;
+                            DS.S = fmaf(w, 0.5f * (a + b), DS.S);
+                            DS.R = fmaf(w, cdist, DS.R);
+                        }
                     }
                     T_after = T_i;
                     rec_write(rs, rec_slot(rs, k, base), dgeo, dc, prio);
@@ -1377,8 +1505,8 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     // ---- front to back for pixels whose transmittance underflowed (rare:
     // kept out of line so that it does not weigh on the main path's registers)
     if (__any_sync(0xffffffffu, fallback))
-        bwd_front_to_back<K, EXTRA>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, SN, vd, wb, p,
-                                    g, st, rs, in, dcol);
+        bwd_front_to_back<K, EXTRA>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, SN, DS, vd, wb,
+                                    p, g, st, rs, in, dcol);
 }
 
 template <int K, bool EXTRA>
@@ -1492,9 +1620,9 @@ static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
 
 cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float *alpha,
                               float *T_final, int32_t *last, int2 *stats, float *normal, float *max_weight,
-                              cudaStream_t s) {
-    const FwdOut out = {rgb, depth, alpha, T_final, last, stats, normal, max_weight};
-    const int mode = stats ? kModeStats : (normal || max_weight) ? kModeExtra : kModePlain;
+                              float *dist, cudaStream_t s) {
+    const FwdOut out = {rgb, depth, alpha, T_final, last, stats, normal, max_weight, dist};
+    const int mode = stats ? kModeStats : (normal || max_weight || dist) ? kModeExtra : kModePlain;
     // the work counter is zero here: cleared with the status block, then by
     // the last warp of every launch
     cudaError_t e;
@@ -1515,13 +1643,14 @@ cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float
 
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float *d_depth,
                               const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
-                              float *d_sh, const float *d_normal, float *priority, cudaStream_t s) {
+                              float *d_sh, const float *d_normal, float *priority, const float *d_dist,
+                              const float *dist, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
     if (e == cudaSuccess && f.n_vox > 0)
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
-    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority};
-    const bool extra = d_normal != nullptr || priority != nullptr;
+    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority, d_dist, dist};
+    const bool extra = d_normal != nullptr || priority != nullptr || d_dist != nullptr;
     switch (f.K * 2 + (extra ? 1 : 0)) {
         case 2: e = bwd_k<1, false>(f, in, s); break;
         case 3: e = bwd_k<1, true>(f, in, s); break;

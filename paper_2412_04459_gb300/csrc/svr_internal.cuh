@@ -26,9 +26,10 @@ constexpr int kScanTile = 256;             // entries per block of the count sca
 // merged afterwards; kSegFields floats per pixel and segment carry the
 // partial sums between the warps and on to the backward: colour (0..2),
 // depth (3), transmittance after and before (4, 5; 5 holds the stopping
-// index until the merge), work counts (6, 7), normal (8..10).
+// index until the merge), work counts (6, 7), normal (8..10), distortion
+// loss sums (11..13).
 constexpr int kSegLen = 1024;
-constexpr int kSegFields = 11;
+constexpr int kSegFields = 14;
 // A tile's pairs are counted and emitted through kTileSub sub-buckets (by
 // voxel id), so that the atomics on a busy tile spread over separate cache
 // lines; the sub-buckets of a tile are adjacent in its range.
@@ -64,7 +65,8 @@ struct Status {
     unsigned bwd_next;    // next work item of the backward render (reset before each launch)
     unsigned n_queue;     // (tile, segment) entries of the render work order
     unsigned slots_used;  // segment slots taken by the split tiles
-    unsigned fwd_done;    // 1 once a forward has filled the segment sums of the current sort (2: with normals)
+    unsigned fwd_done;    // bit 0: a forward filled the segment sums of the current sort; bit 1: with
+                          // the normal image; bit 2: with the distortion loss
     unsigned sort_next;   // next work-order entry of the long-list sort
     unsigned fwd_exit;    // warps of the running forward launch that ran out of work
     unsigned pad[5];
@@ -226,10 +228,10 @@ cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties
 cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s);
 cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth,
                               float *alpha, float *T_final, int32_t *last, int2 *stats, float *normal,
-                              float *max_weight, cudaStream_t s);
+                              float *max_weight, float *dist, cudaStream_t s);
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb,
                               const float *d_depth, const float *d_alpha, const float *T_final,
                               const int32_t *last, float *d_grid, float *d_sh, const float *d_normal,
-                              float *priority, cudaStream_t s);
+                              float *priority, const float *d_dist, const float *dist, cudaStream_t s);
 
 }  // namespace svr

@@ -62,9 +62,13 @@ def parse():
                          "timed on its own")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-pixels", type=int, default=1536)
+    ap.add_argument("--cpu-pixels", type=int, default=24576,
+                    help="pixels of the CPU oracle's timed sample (about 10-20 s on 16 cores)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-view batched vs per-view comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the timings of the normal / pruning / subdivision outputs, the "
+                         "anti-aliasing kernels and the training step")
     return ap.parse_args()
 
 
@@ -294,6 +298,9 @@ def run_native(args, rank, world, local_rank):
     batched = None
     if not args.no_batched and args.workload == "shell1m":
         batched = run_batched(args, scene, dscene, dev, kw)
+    extras = None
+    if not args.no_extras and args.workload == "shell1m":
+        extras = run_extras(args, scene, dscene, cam, dev, kw, fr, out, (g_rgb, g_depth, g_alpha), P)
 
     if rank != 0:
         return
@@ -332,6 +339,7 @@ def run_native(args, rank, world, local_rank):
                          "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
                                   "ops_per_hit": OPS_HIT[K]}},
         "batched": batched,
+        "next_rows": extras,
         "frame_hbm": {"algorithmic_bytes": frame_bytes, "achieved_gbs": frame_bytes / (ms_step * 1e-3) / 1e9,
                       "peak_gbs": hbm, "frac": frame_bytes / (ms_step * 1e-3) / 1e9 / hbm,
                       "peak_from": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"},
@@ -498,6 +506,142 @@ def run_batched(args, scene, dscene, dev, kw, n_views=16, steps=10):
             "views_per_s_batched": n_views * 1000.0 / ms_batched,
             "views_per_s_per_view": n_views * 1000.0 / ms_per_view,
             "speedup": ms_per_view / ms_batched, "l2": "flushed before each timed step"}
+
+
+def _event_ms(fn, reps, flush, warm=2, graph=True):
+    """Mean CUDA-event time of fn() on the current stream, L2 flushed before
+    each timed call (outside the events).  graph=True captures fn once in a
+    CUDA graph and times its replays, so the host's launch overhead (Python
+    and ctypes, tens of microseconds) does not count as GPU time."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            fn()
+        fn = g.replay
+        fn()
+        torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ts]))
+
+
+def run_extras(args, scene, dscene, cam, dev, kw, fr, out, grads, P, reps=10):
+    """Timings of the rows built beyond the base path, on the bench frame:
+    the forward and backward with all extra outputs (normal image, maximum
+    blending weights, distortion loss; normal gradient, subdivision priority,
+    distortion gradient) against the plain ones; the anti-aliasing
+    downsampling of rgb, depth and alpha from 1.1x; Adam on all grid and SH
+    parameters and the transmittance-concentration loss (bandwidth-bound:
+    GB/s against the measured copy bandwidth); and whole training steps
+    (train.TrainStep: render, MSE + L_T + distortion, backward, Adam) of the
+    1280x840 view, forward-backward graph-replayed, with and without 1.1x
+    supersampling."""
+    import torch
+    from paper_2412_04459_gb300 import _native as N
+    from paper_2412_04459_gb300.raster import _ptr, _stream, downsample, downsample_bwd, supersampled_camera
+    from paper_2412_04459_gb300.train import TrainStep, adam, t_concentration_loss
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    hbm = (load_peaks() or {}).get("hbm_gbs", 6800.0)
+    H, W = cam.height, cam.width
+    g_rgb, g_depth, g_alpha = grads
+    res = {}
+    # forward / backward with every extra output
+    normal = torch.empty(3, H, W, device=dev)
+    mw = torch.zeros(scene.n_vox, device=dev)
+    dist = torch.empty(2, H, W, device=dev)
+    ex = N.SvrRenderExtras()
+    ex.normal, ex.max_weight, ex.distortion = normal.data_ptr(), mw.data_ptr(), dist.data_ptr()
+    o = out
+
+    def fwd_ex():
+        N.check(N.lib().svr_render_fwd_ex(N.ref(fr.frame), _ptr(o["rgb"]), _ptr(o["depth"]), _ptr(o["alpha"]),
+                                          _ptr(o["T_final"]), _ptr(o["last"]), N.ref(ex), _stream()), "fwd_ex")
+
+    g_n = torch.randn(3, H, W, device=dev)
+    g_d = torch.full((H, W), 0.1 / (H * W), device=dev)
+    pr = torch.zeros(scene.n_vox, device=dev)
+    bx = N.SvrRenderExtras()
+    bx.d_normal, bx.priority, bx.distortion, bx.d_distortion = g_n.data_ptr(), pr.data_ptr(), dist.data_ptr(), \
+        g_d.data_ptr()
+    d_grid = torch.zeros(scene.n_pts, device=dev)
+    d_sh = torch.empty(scene.n_vox, 48, device=dev)
+
+    def bwd_ex():
+        N.check(N.lib().svr_render_bwd_ex(N.ref(fr.frame), _ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha),
+                                          _ptr(o["T_final"]), _ptr(o["last"]), _ptr(d_grid), _ptr(d_sh), N.ref(bx),
+                                          _stream()), "bwd_ex")
+
+    res["extras"] = {"ms_fwd_plain": _event_ms(lambda: fr.forward(o), reps, flush),
+                     "ms_fwd_all_extras": _event_ms(fwd_ex, reps, flush)}
+    fwd_ex()
+    res["extras"]["ms_bwd_plain"] = _event_ms(lambda: fr.backward(g_rgb, g_depth, g_alpha, o, d_grid, d_sh), reps,
+                                              flush)
+    fwd_ex()
+    res["extras"]["ms_bwd_all_extras"] = _event_ms(bwd_ex, reps, flush)
+    res["extras"]["outputs"] = ("normal image, per-voxel max blending weight, per-ray distortion loss; backward "
+                                "with the normal and distortion gradients and the subdivision priority")
+    # anti-aliasing: rgb, depth, alpha from 1.1x
+    ss = supersampled_camera(cam, 1.1)
+    src = torch.randn(5, ss.height, ss.width, device=dev)
+    dst = torch.empty(5, H, W, device=dev)
+    ms_ds = _event_ms(lambda: downsample(src, H, W, dst=dst), reps, flush)
+    ms_dsb = _event_ms(lambda: downsample_bwd(dst, ss.height, ss.width, out=src), reps, flush)
+    by = 4 * 5 * (ss.height * ss.width + H * W)
+    res["antialias"] = {"from": f"{ss.width}x{ss.height}", "to": f"{W}x{H}", "planes": 5,
+                        "ms_downsample": ms_ds, "ms_downsample_bwd": ms_dsb,
+                        "gbs_downsample": by / ms_ds / 1e6, "frac_downsample": by / ms_ds / 1e6 / hbm,
+                        "gbs_downsample_bwd": by / ms_dsb / 1e6, "frac_downsample_bwd": by / ms_dsb / 1e6 / hbm,
+                        "bytes": by}
+    # Adam over all parameters, L_T over the frame
+    prm = [dscene.grid.clone(), dscene.sh.clone().reshape(-1)]
+    st = [(torch.randn_like(x), torch.zeros_like(x), torch.zeros_like(x)) for x in prm]
+    cnt = {"t": 0}
+
+    def adam_all():
+        cnt["t"] += 1
+        adam(prm[0], st[0][0], st[0][1], st[0][2], cnt["t"], 0.025)
+        adam(prm[1], st[1][0], st[1][1], st[1][2], cnt["t"], 0.01, 0.00025, period=48, head=3)
+
+    ms_adam = _event_ms(adam_all, reps, flush)
+    n_par = sum(x.numel() for x in prm)
+    by_adam = 28 * n_par
+    loss = torch.zeros(1, device=dev)
+    ga = torch.empty(H, W, device=dev)
+    ms_lt = _event_ms(lambda: t_concentration_loss(o["alpha"], 0.01, loss, ga), reps, flush)
+    res["optimizer"] = {"params": n_par, "ms_adam": ms_adam, "gbs_adam": by_adam / ms_adam / 1e6,
+                        "frac_adam": by_adam / ms_adam / 1e6 / hbm,
+                        "bytes_adam": by_adam, "ms_t_concentration": ms_lt,
+                        "note": "Adam moves 28 B per parameter (read param, grad, m, v; write param, m, v)"}
+    # whole training steps
+    tgt = [torch.rand(3, H, W, device=dev)]
+    for name, h_ss in (("train_step", None), ("train_step_ss1.1", 1.1)):
+        scn = type(dscene)(dscene.centre, dscene.level, dscene.corner_idx, dscene.grid.clone(), dscene.sh.clone(),
+                           dscene.world_center, dscene.world_size, dscene.max_level)
+        tsp = TrainStep(scn, [cam], tgt, K=kw["K"], t_stop=kw["t_stop"], h_ss=h_ss).capture()
+        ms = _event_ms(tsp.step, reps, flush, graph=False)     # replays its own graph, then Adam
+        res[name] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms,
+                     "step": "batched render + MSE + 0.01 L_T + 0.1 distortion + backward (graph replay) + Adam",
+                     "image": f"{tsp.render_cams[0].width}x{tsp.render_cams[0].height} rendered, {W}x{H} loss"}
+        del tsp, scn
+    torch.cuda.empty_cache()
+    return res
 
 
 def sampled_parity(scene, cams, out, pixel_base, n_px, seed):

@@ -288,8 +288,12 @@ SVR_API int svr_render_batched(svr_frame *frame, const svr_scene *scene, const s
  *               every voxel's largest blending weight T_i alpha_i over the
  *               rendered pixels: the pruning statistic of Sec. 3.2.2,
  *               accumulated over views and calls until the caller zeroes it.
- *               Tile lists longer than 1024 entries are walked a second time
- *               from their true transmittance to get it exactly.
+ *               The later segments of tile lists longer than 1024 entries
+ *               are walked a second time, in parallel, from the true
+ *               transmittance in front of them, to get it exactly.  Given to
+ *               svr_render_bwd_ex, the backward raises it too, from the
+ *               exact T_i alpha_i of its own walk at no extra pass (a
+ *               training loop gets the pruning statistic with its gradients).
  *   d_normal    backward input [3][H][W]: dL/dN.  Requires that the frame's
  *               last forward of this sort rendered `normal` (its tile
  *               segments carry the normal sums); otherwise split tiles are
@@ -429,8 +433,9 @@ SVR_API int svr_weighted_mean(const float *x, int64_t n, float weight, float *lo
  * array [N][48]: period 48, head 3 gives the degree-0 coefficients their own
  * rate; the paper: 0.01 for them, 0.00025 for the rest, 0.025 for the grid
  * densities, (beta1, beta2) = (0.1, 0.99), eps = 1e-15).  step counts from 1;
- * m and v start at zero and are updated in place.  SVR_ERR_INVALID for a bad
- * period/head/step or betas outside [0, 1).
+ * m and v start at zero and are updated in place.  The four arrays must be
+ * 16-byte aligned.  SVR_ERR_INVALID for a bad period/head/step, betas outside
+ * [0, 1) or misaligned arrays.
  */
 SVR_API int svr_adam(float *param, const float *grad, float *m, float *v, int64_t n, int32_t period,
                      int32_t head, float lr_head, float lr_rest, float beta1, float beta2, float eps,

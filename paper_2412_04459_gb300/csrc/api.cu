@@ -428,7 +428,7 @@ SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const flo
     if (d_sh && (((uintptr_t)d_sh) & 15u)) return fail(SVR_ERR_INVALID, "d_sh not 16-byte aligned");
     const svr::FrameDev d = frame_dev(frame);
     cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid,
-                                           d_sh, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+                                           d_sh, nullptr, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
     return SVR_OK;
 }
@@ -447,8 +447,10 @@ SVR_API int svr_render_bwd_ex(const svr_frame *frame, const float *d_rgb, const 
     const float *dist = extras ? extras->distortion : nullptr;
     if (d_dist && !dist) return fail(SVR_ERR_INVALID, "d_distortion needs the forward's distortion output");
     const svr::FrameDev d = frame_dev(frame);
+    float *max_weight = extras ? extras->max_weight : nullptr;
+    if (max_weight && (((uintptr_t)max_weight) & 3u)) return fail(SVR_ERR_INVALID, "max_weight not 4-byte aligned");
     cudaError_t e = svr::launch_render_bwd(d, d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_sh, d_normal,
-                                           priority, d_dist, dist, (cudaStream_t)stream);
+                                           priority, d_dist, dist, max_weight, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "render_bwd_ex");
     return SVR_OK;
 }

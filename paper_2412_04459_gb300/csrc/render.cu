@@ -804,10 +804,6 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
     constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
     const int B = f.blocks_per_tile;
     const int nseg = (int)L.ts.x;
-    // with maximum weights requested every later segment is walked again
-    // from its true transmittance (the segment walks started from T = 1;
-    // segment 0 recorded its weights itself)
-    const bool rewalk = EXTRA && out.max_weight != nullptr;
     for (int sg = 0; sg < nseg; ++sg) {
         float *q = seg_fields(f, L.ts.y + sg, blk);
         const float Tb = m.T;
@@ -818,9 +814,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
         bool need = false;
         if (!m.done) {
             const float Tl = __ldcg(q + 4 * 32);
-            if (rewalk && sg > 0) {
-                need = true;
-            } else if (Tb * Tl >= f.t_stop || sg == 0) {
+            if (Tb * Tl >= f.t_stop || sg == 0) {
                 c0 = Tb * __ldcg(q);
                 c1 = Tb * __ldcg(q + 32);
                 c2 = Tb * __ldcg(q + 2 * 32);
@@ -1050,6 +1044,37 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
             f.status->fwd_done = 1u | ((MODE == kModeExtra && out.normal) ? 2u : 0u) |
                                  ((MODE == kModeExtra && out.dist) ? 4u : 0u);
         }
+    }
+}
+
+// Maximum blending weights of the later segments of split tile lists (the
+// forward's segment walks start from T = 1, so only segment 0 records its
+// weights there): every such (segment, block) item is walked again from the
+// transmittance that the forward's merge left in front of it, in parallel
+// over the items, so each weight is the true T_i alpha_i.
+template <int K>
+__global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_maxw(FrameDev f, FwdOut out) {
+    __shared__ FwdSmem smem[kWarps];
+    FwdSmem &ws = smem[threadIdx.x >> 5];
+    const unsigned bpt = (unsigned)f.blocks_per_tile;
+    const unsigned n_items = f.status->n_queue * bpt;
+    Item it;
+    while (next_item(&f.status->maxw_next, n_items, bpt, f.order, it)) {
+        if (it.seg == 0) continue;
+        const ItemView iv = item_view(f, it.g);
+        const DevCam &cam = f.views[iv.view];
+        WarpBlock wb;
+        const PixelRay p = pixel_ray(cam, iv.tile, it.blk, wb);
+        if (wb.smask == 0) continue;
+        const ItemList L = item_list(f, it.g, it.blk);
+        if (L.ts.x <= 1) continue;
+        const float Tb = __ldcg(seg_fields(f, L.ts.y + it.seg, it.blk) + 5 * 32);
+        FwdState s = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !p.inside || !(Tb >= f.t_stop), 0, 0,
+                      0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int p0, p1;
+        seg_range(L, f.blocks_per_tile, it.seg, p0, p1);
+        fwd_walk<K, kModeExtra>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s, out, true);
+        __syncwarp();
     }
 }
 
@@ -1315,6 +1340,7 @@ struct BwdIn {
     float *priority;        // extras: [N] subdivision priority, accumulated, or NULL
     const float *d_dist;    // extras: upstream gradient of each ray's distortion loss [H][W], or NULL
     const float *dist;      // extras: the forward's [2][H][W] distortion output (plane 1: sum w m)
+    float *max_weight;      // extras: [N] per-voxel maximum of T_i alpha_i (atomicMax), or NULL
 };
 
 // Front-to-back gradients for the pixels of an item whose transmittance
@@ -1437,6 +1463,8 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 PC2 = fmaf(w, e.col.z, PC2);
                 PD = fmaf(T_i, dloc, PD);
                 if (EXTRA) {
+                    if (in.max_weight)
+                        atomicMax(reinterpret_cast<int *>(in.max_weight) + __float_as_int(e.col.w), __float_as_int(w));
                     PN.x = fmaf(w, n.x, PN.x);
                     PN.y = fmaf(w, n.y, PN.y);
                     PN.z = fmaf(w, n.z, PN.z);
@@ -1585,6 +1613,9 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     SC2 = fmaf(w, e.col.z, SC2);
                     SD = fmaf(T_i, dloc, SD);
                     if (EXTRA) {
+                        if (in.max_weight)
+                            atomicMax(reinterpret_cast<int *>(in.max_weight) + __float_as_int(e.col.w),
+                                      __float_as_int(w));
                         SN.x = fmaf(w, n.x, SN.x);
                         SN.y = fmaf(w, n.y, SN.y);
                         SN.z = fmaf(w, n.z, SN.z);
@@ -1707,6 +1738,17 @@ static cudaError_t fwd_k(const FrameDev &f, const FwdOut &out, cudaStream_t s) {
     const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kWarps - 1) / kWarps);
     k_render_fwd<K, MODE><<<g, kThreads, 0, s>>>(f, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || MODE != kModeExtra || !out.max_weight) return e;
+    // the later segments of split lists, from their true transmittance
+    static DeviceCache cache_w;
+    const unsigned grid_w = device_cached(cache_w, [] { return persistent_grid(k_render_maxw<K>, kThreads); });
+    e = cudaMemsetAsync(&f.status->maxw_next, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    FwdOut wout = out;
+    wout.normal = nullptr;
+    wout.dist = nullptr;
+    k_render_maxw<K><<<tmin<unsigned>(grid_w, (items + kWarps - 1) / kWarps), kThreads, 0, s>>>(f, wout);
     return cudaGetLastError();
 }
 
@@ -1747,13 +1789,13 @@ cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float *d_depth,
                               const float *d_alpha, const float *T_final, const int32_t *last, float *d_grid,
                               float *d_sh, const float *d_normal, float *priority, const float *d_dist,
-                              const float *dist, cudaStream_t s) {
+                              const float *dist, float *max_weight, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&f.status->bwd_next, 0, sizeof(unsigned), s);
     if (e == cudaSuccess && f.n_vox > 0)
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
-    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority, d_dist, dist};
-    const bool extra = d_normal != nullptr || priority != nullptr || d_dist != nullptr;
+    const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority, d_dist, dist, max_weight};
+    const bool extra = d_normal != nullptr || priority != nullptr || d_dist != nullptr || max_weight != nullptr;
     switch (f.K * 2 + (extra ? 1 : 0)) {
         case 2: e = bwd_k<1, false>(f, in, s); break;
         case 3: e = bwd_k<1, true>(f, in, s); break;

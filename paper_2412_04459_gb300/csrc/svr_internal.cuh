@@ -69,7 +69,8 @@ struct Status {
                           // the normal image; bit 2: with the distortion loss
     unsigned sort_next;   // next work-order entry of the long-list sort
     unsigned fwd_exit;    // warps of the running forward launch that ran out of work
-    unsigned pad[5];
+    unsigned maxw_next;   // next work item of the maximum-weight pass over split lists (reset before it)
+    unsigned pad[4];
 };
 
 // Per-voxel record of one view (64 bytes):
@@ -232,6 +233,7 @@ cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth,
 cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb,
                               const float *d_depth, const float *d_alpha, const float *T_final,
                               const int32_t *last, float *d_grid, float *d_sh, const float *d_normal,
-                              float *priority, const float *d_dist, const float *dist, cudaStream_t s);
+                              float *priority, const float *d_dist, const float *dist, float *max_weight,
+                              cudaStream_t s);
 
 }  // namespace svr

@@ -65,19 +65,53 @@ __global__ void __launch_bounds__(kTrainThreads) k_weighted_mean(const float *__
     block_add(acc * (weight / (float)n), loss);
 }
 
+__device__ __forceinline__ float adam_one(float p, float g, float &m, float &v, float lr, float beta1, float beta2,
+                                          float eps, float inv_bc1, float inv_bc2) {
+    m = fmaf(beta1, m, (1.f - beta1) * g);
+    v = fmaf(beta2, v, (1.f - beta2) * g * g);
+    return p - lr * (m * inv_bc1) / (sqrtf(v * inv_bc2) + eps);
+}
+
+// Four parameters per thread and iteration as float4 (16-byte loads and
+// stores of all four arrays); the learning rate of element i is lr_head when
+// i mod period < head.  n4 = n / 4 vectors; the tail (n mod 4) is done by the
+// first threads in scalar form.
 __global__ void __launch_bounds__(kTrainThreads) k_adam(float *__restrict__ param, const float *__restrict__ grad,
                                                         float *__restrict__ m, float *__restrict__ v, int64_t n,
                                                         int period, int head, float lr_head, float lr_rest,
                                                         float beta1, float beta2, float eps, float inv_bc1,
                                                         float inv_bc2) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = grad[i];
-        const float mi = fmaf(beta1, m[i], (1.f - beta1) * g);
-        const float vi = fmaf(beta2, v[i], (1.f - beta2) * g * g);
-        m[i] = mi;
-        v[i] = vi;
+    const int64_t n4 = n >> 2;
+    float4 *p4 = reinterpret_cast<float4 *>(param);
+    const float4 *g4 = reinterpret_cast<const float4 *>(grad);
+    float4 *m4 = reinterpret_cast<float4 *>(m);
+    float4 *v4 = reinterpret_cast<float4 *>(v);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 g = __ldcs(g4 + i);
+        float4 p = __ldcs(p4 + i), mm = __ldcs(m4 + i), vv = __ldcs(v4 + i);
+        // position of the first element within its period
+        const int r = period == 1 ? 0 : (int)((4 * i) % period);
+        const float l0 = (r < head) ? lr_head : lr_rest;
+        const float l1 = ((r + 1) % period < head) ? lr_head : lr_rest;
+        const float l2 = ((r + 2) % period < head) ? lr_head : lr_rest;
+        const float l3 = ((r + 3) % period < head) ? lr_head : lr_rest;
+        p.x = adam_one(p.x, g.x, mm.x, vv.x, l0, beta1, beta2, eps, inv_bc1, inv_bc2);
+        p.y = adam_one(p.y, g.y, mm.y, vv.y, l1, beta1, beta2, eps, inv_bc1, inv_bc2);
+        p.z = adam_one(p.z, g.z, mm.z, vv.z, l2, beta1, beta2, eps, inv_bc1, inv_bc2);
+        p.w = adam_one(p.w, g.w, mm.w, vv.w, l3, beta1, beta2, eps, inv_bc1, inv_bc2);
+        __stcs(p4 + i, p);
+        __stcs(m4 + i, mm);
+        __stcs(v4 + i, vv);
+    }
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (n & 3)) {
+        const int64_t i = 4 * n4 + t;
+        float mm = m[i], vv = v[i];
         const float lr = (int)(i % period) < head ? lr_head : lr_rest;
-        param[i] -= lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
+        param[i] = adam_one(param[i], grad[i], mm, vv, lr, beta1, beta2, eps, inv_bc1, inv_bc2);
+        m[i] = mm;
+        v[i] = vv;
     }
 }
 
@@ -128,9 +162,11 @@ SVR_API int svr_adam(float *param, const float *grad, float *m, float *v, int64_
     if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
         return svr::set_error(SVR_ERR_INVALID, "adam: betas %g %g, eps %g", beta1, beta2, eps);
     if (n == 0) return SVR_OK;
+    if ((((uintptr_t)param) | ((uintptr_t)grad) | ((uintptr_t)m) | ((uintptr_t)v)) & 15u)
+        return svr::set_error(SVR_ERR_INVALID, "adam: arrays must be 16-byte aligned");
     // bias corrections 1 - beta^t in double on the host
     const double bc1 = 1.0 - std::pow((double)beta1, (double)step), bc2 = 1.0 - std::pow((double)beta2, (double)step);
-    svr::k_adam<<<svr::grid_for(n), svr::kTrainThreads, 0, (cudaStream_t)stream>>>(
+    svr::k_adam<<<svr::grid_for((n + 3) / 4), svr::kTrainThreads, 0, (cudaStream_t)stream>>>(
         param, grad, m, v, n, period, head, lr_head, lr_rest, beta1, beta2, eps, (float)(1.0 / bc1),
         (float)(1.0 / bc2));
     return svr::launched("adam");

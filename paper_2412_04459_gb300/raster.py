@@ -230,7 +230,7 @@ class Frame:
         return out
 
     def backward_ex(self, g_rgb, g_depth, g_alpha, out, g_normal=None, priority: Optional[torch.Tensor] = None,
-                    d_grid=None, d_sh=None, stream=None):
+                    d_grid=None, d_sh=None, max_weight: Optional[torch.Tensor] = None, stream=None):
         """svr_render_bwd_ex: the backward plus, on request, the normal
         image's upstream gradient and the per-voxel subdivision priority
         (accumulated in place in priority, float32 [N])."""
@@ -243,6 +243,7 @@ class Frame:
         ex = N.SvrRenderExtras()
         ex.d_normal = gn.data_ptr() if gn is not None else None
         ex.priority = priority.data_ptr() if priority is not None else None
+        ex.max_weight = max_weight.data_ptr() if max_weight is not None else None
         N.check(N.lib().svr_render_bwd_ex(N.ref(self.frame), _ptr(gr), _ptr(gd), _ptr(ga), _ptr(out["T_final"]),
                                           _ptr(out["last"]), _ptr(d_grid), _ptr(d_sh), N.ref(ex), _stream(stream)),
                 "svr_render_bwd_ex")

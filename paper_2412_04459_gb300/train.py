@@ -69,7 +69,7 @@ class TrainStep:
 
     def __init__(self, scene: DeviceScene, cams: Sequence, targets: Sequence[torch.Tensor], K: int = 1,
                  t_stop: float = 1e-4, tile: int = 16, h_ss: Optional[float] = None, lambda_t: float = LAMBDA_T,
-                 lambda_dist: float = LAMBDA_DIST, pair_capacity: Optional[int] = None):
+                 lambda_dist: float = LAMBDA_DIST, pair_capacity: Optional[int] = None, stats: bool = False):
         self.scene = scene
         self.cams = list(cams)
         self.h_ss = h_ss
@@ -102,6 +102,10 @@ class TrainStep:
         self.m_sh, self.v_sh = torch.zeros_like(scene.sh), torch.zeros_like(scene.sh)
         self.n_steps = 0
         self.graph = None
+        # pruning and subdivision statistics gathered by every step's backward
+        # (Sec. 3.2.2): the caller reads and zeroes them between octree edits
+        self.max_weight = torch.zeros(scene.n_vox, device=dev) if stats else None
+        self.priority = torch.zeros(scene.n_vox, device=dev) if stats else None
 
     # -- the pieces -----------------------------------------------------------
     def _views(self, buf, per_pixel):
@@ -140,6 +144,9 @@ class TrainStep:
         bx = N.SvrRenderExtras()
         bx.distortion = self.dist.data_ptr()
         bx.d_distortion = self.g_dist.data_ptr()
+        if self.max_weight is not None:
+            bx.max_weight = self.max_weight.data_ptr()
+            bx.priority = self.priority.data_ptr()
         N.check(N.lib().svr_render_bwd_ex(N.ref(fr.frame), _ptr(self.g_rgb), None, _ptr(self.g_alpha),
                                           _ptr(o["T_final"]), _ptr(o["last"]), _ptr(self.d_grid), _ptr(self.d_sh),
                                           N.ref(bx), _stream(stream)), "svr_render_bwd_ex")

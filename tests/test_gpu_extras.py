@@ -137,6 +137,12 @@ def test_normal_gradient_and_priority(name):
     ratio = np.abs(p - pr_ref) / (1e-3 * (pr_ref + 1e-3 * pr_ref.max()) + SEG_REL * mag["priority_seg"])
     print(f"PARITY priority {name}: rel L2 {rel:.3e}, worst elementwise ratio {ratio.max():.3f}")
     assert rel <= 1e-3 and (ratio <= 1.0).all(), (rel, ratio.max(), int(np.argmax(ratio)))
+    # the backward raises the maximum blending weights from its own walk
+    mw = torch.zeros(sc.n_vox, device="cuda")
+    fr.backward_ex(t(g_rgb), t(g_d), t(g_a), out, max_weight=mw)
+    mw_ref = np.zeros(sc.n_vox)
+    oracle.render(sc, cam, K=K, t_stop=t_stop, max_weight=mw_ref)
+    assert np.abs(mw.cpu().numpy() - mw_ref).max() <= IMG_TOL
     # without the normal term the gradient is the plain backward's
     d0, s0 = fr.backward(t(g_rgb), t(g_d), t(g_a), out)
     d1, s1 = fr.backward_ex(t(g_rgb), t(g_d), t(g_a), out)

@@ -148,10 +148,16 @@ def test_train_step_against_oracle(h_ss):
     import torch
     from paper_2412_04459_gb300.train import TrainStep
     sc, cams, targets, dev, tt = _train_case(h_ss)
-    ts = TrainStep(dev, cams, tt, K=2, h_ss=h_ss)
+    ts = TrainStep(dev, cams, tt, K=2, h_ss=h_ss, stats=True)
     grid0, sh0 = dev.grid.clone(), dev.sh.clone()
     ts.forward_backward()
     torch.cuda.synchronize()
+    # the pruning statistic gathered by the step's backward
+    mw_ref = np.zeros(sc.n_vox)
+    for rc in ts.render_cams:
+        oracle.render(sc, rc, K=2, max_weight=mw_ref)
+    assert np.abs(ts.max_weight.cpu().numpy() - mw_ref).max() <= IMG_TOL
+    assert float(ts.priority.sum()) > 0
     # the oracle's loss for the same parameters
     P = ts.frame.n_pixels
     mse_num, n_rgb, lt, ld = 0.0, 0, 0.0, 0.0

@@ -58,7 +58,10 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kFwdMinBlocks = 3;   // resident CTAs per SM the forward's register budget is sized for
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
 constexpr int kBwdThreads = kBwdWarps * 32;
-constexpr int kBwdMinBlocks = 5;   // resident CTAs per SM the register budget is sized for
+#ifndef SVR_BWD_MIN_BLOCKS
+#define SVR_BWD_MIN_BLOCKS 5
+#endif
+constexpr int kBwdMinBlocks = SVR_BWD_MIN_BLOCKS;   // resident CTAs per SM the register budget is sized for
 constexpr int kBatch = 32;
 
 // Staged list entry, padded to 112 bytes: lanes reading different entries
@@ -336,6 +339,12 @@ __device__ __forceinline__ void fetch_vi(Lookahead &la, const uint2 *__restrict_
 
 __device__ __forceinline__ void fetch_box(Lookahead &la, const ViewData &vd) {
     la.box = la.valid ? __ldg(vd.box + (la.vi.x & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
+}
+
+// Ask for the looked-ahead entry's 64-byte record in L1 (the backward stages
+// with plain loads one batch later).
+__device__ __forceinline__ void prefetch_record(const Lookahead &la, const ViewData &vd) {
+    if (la.valid) asm volatile("prefetch.global.L1 [%0];" ::"l"(vd.rec + (la.vi.x & 0x1FFFFFFFu)));
 }
 
 // Stage the looked-ahead entries (lane j: entry j of the batch).
@@ -1197,16 +1206,18 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     for (int k = K - 1; k >= 0; --k) {
         const float gxk = fmaf(gdT, fmaf(Pk[k + 1], tk[k], -Q), gx);
         const float dv = gxk * xs * dsig[k];
-        const float ux = 1.f - qx[k], uy = 1.f - qy[k], uz = 1.f - qz[k];
-        const float w00 = ux * uy, w01 = ux * qy[k], w10 = qx[k] * uy, w11 = qx[k] * qy[k];
-        dgeo[0] = fmaf(dv, w00 * uz, dgeo[0]);
-        dgeo[1] = fmaf(dv, w00 * qz[k], dgeo[1]);
-        dgeo[2] = fmaf(dv, w01 * uz, dgeo[2]);
-        dgeo[3] = fmaf(dv, w01 * qz[k], dgeo[3]);
-        dgeo[4] = fmaf(dv, w10 * uz, dgeo[4]);
-        dgeo[5] = fmaf(dv, w10 * qz[k], dgeo[5]);
-        dgeo[6] = fmaf(dv, w11 * uz, dgeo[6]);
-        dgeo[7] = fmaf(dv, w11 * qz[k], dgeo[7]);
+        // trilinear adjoint, the x and y weights folded into dv first
+        const float ax1 = dv * qx[k], ax0 = dv - ax1;
+        const float b01 = ax0 * qy[k], b00 = ax0 - b01, b11 = ax1 * qy[k], b10 = ax1 - b11;
+        const float uz = 1.f - qz[k];
+        dgeo[0] = fmaf(b00, uz, dgeo[0]);
+        dgeo[1] = fmaf(b00, qz[k], dgeo[1]);
+        dgeo[2] = fmaf(b01, uz, dgeo[2]);
+        dgeo[3] = fmaf(b01, qz[k], dgeo[3]);
+        dgeo[4] = fmaf(b10, uz, dgeo[4]);
+        dgeo[5] = fmaf(b10, qz[k], dgeo[5]);
+        dgeo[6] = fmaf(b11, uz, dgeo[6]);
+        dgeo[7] = fmaf(b11, qz[k], dgeo[7]);
         Q = fmaf(Pk[k] * (1.f - ek[k]), tk[k], Q);
     }
     // normal: dL/dn = w g_N, through the normalisation (I - n n^T) / |grad|
@@ -1233,7 +1244,10 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
 // records are held at a time: a batch with more hits is processed in runs of
 // consecutive entries, which keeps every pixel's hits in list order.
 constexpr int kRecStride = 12;   // floats per record slot: 11 used, 16-byte aligned
-constexpr int kRecCap = 128;
+#ifndef SVR_BWD_REC_CAP
+#define SVR_BWD_REC_CAP 128
+#endif
+constexpr int kRecCap = SVR_BWD_REC_CAP;
 
 struct RecSmem {
     float4 rec[kRecCap * kRecStride / 4];
@@ -1575,6 +1589,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         Lookahead la;
         fetch_vi(la, L.list, top_all - 1 - lane, top_all - 1 - lane >= p0);
         fetch_box(la, vd);
+        prefetch_record(la, vd);
         for (int top = top_all; top > p0; top -= kBatch) {
             const Lookahead cur = la;
             const int npos = top - 1 - kBatch - lane;
@@ -1582,6 +1597,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
             stage_ahead(st, vd, cur);              // lane j: list position top - 1 - j
             fetch_box(la, vd);
+            prefetch_record(la, vd);
             unsigned hits = 0;
             if (active) {
                 for (unsigned c = cand; c; c &= c - 1u) {

@@ -481,7 +481,7 @@ struct FwdOut {
 
 // Forward variants: the plain render, the work-counting one, and the one with
 // the extra outputs (normal image, maximum blending weights).
-constexpr int kModePlain = 0, kModeStats = 1, kModeExtra = 2;
+constexpr int kModePlain = 0, kModeStats = 1, kModeExtra = 2, kModeDist = 3;
 
 // Compositing state of the calling lane's pixel.
 struct FwdState {
@@ -705,7 +705,8 @@ template <int K, int MODE>
 __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0, int p1, const ViewData &vd,
                                          const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, float t_stop,
                                          FwdState &s, const FwdOut &out, bool true_weights) {
-    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
+    constexpr bool STATS = MODE == kModeStats, FN = MODE == kModeExtra, FD = FN || MODE == kModeDist;
+    constexpr bool EXTRA = FN || FD;
     const int lane = threadIdx.x & 31;
     const float3 sb = make_float3((p.s & 4) ? 1.f : 0.f, (p.s & 2) ? 1.f : 0.f, (p.s & 1) ? 1.f : 0.f);
     Lookahead cur, nx, nn;
@@ -769,17 +770,17 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                 s.C2 = fmaf(w, col.z, s.C2);
                 s.D = fmaf(s.T, dloc, s.D);
                 if (EXTRA) {
-                    if (out.normal) {
+                    if (FN && out.normal) {
                         float3 n;
                         voxel_normal(e.g0, e.g1, n);
                         s.N0 = fmaf(w, n.x, s.N0);
                         s.N1 = fmaf(w, n.y, s.N1);
                         s.N2 = fmaf(w, n.z, s.N2);
                     }
-                    if (out.dist) dist_add(s, w, a, b);
+                    if (FD && out.dist) dist_add(s, w, a, b);
                     // weights are exact only when the walk started from the
                     // true transmittance (not a split segment's T = 1)
-                    if (out.max_weight && true_weights)
+                    if (FN && out.max_weight && true_weights)
                         atomicMax(reinterpret_cast<int *>(out.max_weight) + (ws.meta[buf][k].x & 0x1FFFFFFFu),
                                   __float_as_int(w));
                 }
@@ -810,7 +811,7 @@ template <int K, int MODE>
 __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, int blk, const ViewData &vd,
                                           const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, FwdState &m,
                                           const FwdOut &out) {
-    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
+    constexpr bool STATS = MODE == kModeStats, FN = MODE == kModeExtra, FD = FN || MODE == kModeDist;
     const int B = f.blocks_per_tile;
     const int nseg = (int)L.ts.x;
     for (int sg = 0; sg < nseg; ++sg) {
@@ -828,10 +829,12 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
                 c1 = Tb * __ldcg(q + 32);
                 c2 = Tb * __ldcg(q + 2 * 32);
                 dd = Tb * __ldcg(q + 3 * 32);
-                if (EXTRA) {
+                if (FN) {
                     n0 = Tb * __ldcg(q + 8 * 32);
                     n1 = Tb * __ldcg(q + 9 * 32);
                     n2 = Tb * __ldcg(q + 10 * 32);
+                }
+                if (FD) {
                     // segment walked from T = 1: its weights scale by Tb
                     dl_b = Tb * Tb * __ldcg(q + 11 * 32);
                     dw_b = Tb * __ldcg(q + 12 * 32);
@@ -885,13 +888,15 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
         q[3 * 32] = dd;
         q[4 * 32] = m.T;
         q[5 * 32] = Tb;
-        if (EXTRA) {
+        if (FN) {
             m.N0 += n0;
             m.N1 += n1;
             m.N2 += n2;
             q[8 * 32] = n0;
             q[9 * 32] = n1;
             q[10 * 32] = n2;
+        }
+        if (FD) {
             // the segment's pairs with the voxels before it
             m.LD = L_before + dl_b + 2.f * (ds_b * W_before - dw_b * S_before);
             m.PW = W_before + dw_b;
@@ -919,7 +924,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
         S1 += c1;
         S2 += c2;
         SD += dd;
-        if (EXTRA) {
+        if (FN) {
             const float n0 = q[8 * 32], n1 = q[9 * 32], n2 = q[10 * 32];
             q[8 * 32] = SN0;
             q[9 * 32] = SN1;
@@ -927,6 +932,8 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             SN0 += n0;
             SN1 += n1;
             SN2 += n2;
+        }
+        if (FD) {
             const float dl_b = q[11 * 32], dw_b = q[12 * 32], ds_b = q[13 * 32];
             const float WA = W_tot - WC - dw_b, SA = S_tot - SCc - ds_b;
             q[11 * 32] = WC;
@@ -942,7 +949,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
 template <int MODE>
 __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, const PixelRay &p,
                                           const FwdState &s, int last, const FwdOut &out) {
-    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
+    constexpr bool STATS = MODE == kModeStats, FN = MODE == kModeExtra, FD = FN || MODE == kModeDist;
     if (!p.inside) return;
     // outputs of view v start at pixel pix_base (rgb: 3 * pix_base, planar)
     const size_t HW = (size_t)cam.W * cam.H;
@@ -957,13 +964,13 @@ __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, 
     out.T[o] = s.T;
     out.last[o] = last;
     if (STATS) out.stats[o] = make_int2(s.n_cand, s.n_hit);
-    if (EXTRA && out.normal) {
+    if (FN && out.normal) {
         float *nrm = out.normal + 3 * (size_t)cam.pix_base + px;
         nrm[0] = s.N0;
         nrm[HW] = s.N1;
         nrm[2 * HW] = s.N2;
     }
-    if (EXTRA && out.dist) {
+    if (FD && out.dist) {
         float *dst = out.dist + 2 * (size_t)cam.pix_base + px;
         dst[0] = s.LD;
         dst[HW] = s.PS;
@@ -972,7 +979,7 @@ __device__ __forceinline__ void fwd_write(const FrameDev &f, const DevCam &cam, 
 
 template <int K, int MODE>
 __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdSmem &ws, const FwdOut &out) {
-    constexpr bool STATS = MODE == kModeStats, EXTRA = MODE == kModeExtra;
+    constexpr bool STATS = MODE == kModeStats, FN = MODE == kModeExtra, FD = FN || MODE == kModeDist;
     const ItemView iv = item_view(f, it.g);
     const DevCam &cam = f.views[iv.view];
     WarpBlock wb;
@@ -1002,10 +1009,12 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
         q[6 * 32] = __int_as_float(s.n_cand);
         q[7 * 32] = __int_as_float(s.n_hit);
     }
-    if (EXTRA) {
+    if (FN) {
         q[8 * 32] = s.N0;
         q[9 * 32] = s.N1;
         q[10 * 32] = s.N2;
+    }
+    if (FD) {
         q[11 * 32] = s.LD;
         q[12 * 32] = s.PW;
         q[13 * 32] = s.PS;
@@ -1028,8 +1037,9 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
 // MODE kModeStats: also count, per pixel, the list entries with its sign
 // bits whose pixel box contains it (the slab tests it must make) and the hits
 // it composited (int2 per pixel), for work accounting.  kModeExtra: the
-// normal image and the per-voxel maximum blending weights (whichever of
-// out.normal, out.max_weight is set).
+// normal image, the per-voxel maximum blending weights and the distortion
+// loss (whichever of out.normal, out.max_weight, out.dist is set).
+// kModeDist: the distortion loss alone (the training step's extra).
 template <int K, int MODE>
 __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev f, FwdOut out) {
     __shared__ FwdSmem smem[kWarps];
@@ -1051,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_fwd(FrameDev
             // bit 1: the segment sums include the normal image, bit 2: the
             // distortion sums
             f.status->fwd_done = 1u | ((MODE == kModeExtra && out.normal) ? 2u : 0u) |
-                                 ((MODE == kModeExtra && out.dist) ? 4u : 0u);
+                                 (((MODE == kModeExtra || MODE == kModeDist) && out.dist) ? 4u : 0u);
         }
     }
 }
@@ -1107,6 +1117,11 @@ struct NrmSums {
     float x, y, z;
 };
 
+// Backward extras selected at compile time (XM bits): the normal image's
+// gradient, the distortion loss's gradient, the pruning/subdivision statistics
+// (priority and max weight).  Instantiated for none, distortion only and all.
+constexpr int kXNrm = 1, kXDist = 2, kXStat = 4, kXAll = 7;
+
 // Gradient contributions of one hit, computed from one pass over its K
 // samples.  B2F: T_known is the transmittance behind the voxel (T_{i+1}) and
 // SC, SD the sums strictly behind it.  Front to back: T_known is T_i and
@@ -1114,15 +1129,15 @@ struct NrmSums {
 // prefix before it); the voxel's own share is removed here.  Returns the
 // transmittance in front of the voxel (T_i) and behind it (T_{i+1}), its
 // blending weight and local depth.
-// EXTRA: the normal image joins the objective (SN: its sums behind the voxel,
-// like SC; nrm returns the voxel's normal) and prio returns the voxel's
+// kXNrm: the normal image joins the objective (SN: its sums behind the voxel,
+// like SC; nrm returns the voxel's normal).  kXStat: prio returns the voxel's
 // subdivision priority term |alpha dL/dalpha| (Eq. priority), alpha dL/dalpha
 // = alpha / (1 - alpha) dL/dx with x the optical depth.
-// With the distortion loss (g.gL != 0): dL/dw_i = 2 (m_i W_<i - S_<i) +
+// kXDist, with the distortion loss (g.gL != 0): dL/dw_i = 2 (m_i W_<i - S_<i) +
 // 2 (S_>i - m_i W_>i) + 2/3 w_i delta_i (returned in cdist, prefix sums as the
 // totals minus the sums behind, DS, and the voxel's own), and it joins dL/dx_i
 // like a colour: T_(i+1) dL/dw_i - sum_{j>i} w_j dL/dw_j.
-template <int K, bool B2F, bool EXTRA>
+template <int K, bool B2F, int XM>
 __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, const PixelGrad &g, float a, float b,
                                          float T_known, float SC0, float SC1, float SC2, float SD, NrmSums SN,
                                          DistSums DS, float dgeo[8], float dcol[3], float &T_i, float &T_after,
@@ -1164,13 +1179,14 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     dloc = d;
     float nlen = 0.f;
     nrm = make_float3(0.f, 0.f, 0.f);
-    if (EXTRA) nlen = voxel_normal(e.g0, e.g1, nrm);
+    constexpr bool XN = (XM & kXNrm) != 0, XD = (XM & kXDist) != 0, XS = (XM & kXStat) != 0;
+    if (XN) nlen = voxel_normal(e.g0, e.g1, nrm);
     if (!B2F) {
         SC0 -= w * e.col.x;
         SC1 -= w * e.col.y;
         SC2 -= w * e.col.z;
         SD -= T_i * d;
-        if (EXTRA) {
+        if (XN) {
             SN.x -= w * nrm.x;
             SN.y -= w * nrm.y;
             SN.z -= w * nrm.z;
@@ -1182,17 +1198,18 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     // dL/dx_i through C, A and the transmittance of later voxels in D
     float gx = g.gC0 * fmaf(T_after, e.col.x, -SC0) + g.gC1 * fmaf(T_after, e.col.y, -SC1) +
                g.gC2 * fmaf(T_after, e.col.z, -SC2) + g.gA * g.Tfin - g.gD * SD;
-    if (EXTRA) {
+    if (XN)
         gx += g.gN0 * fmaf(T_after, nrm.x, -SN.x) + g.gN1 * fmaf(T_after, nrm.y, -SN.y) +
               g.gN2 * fmaf(T_after, nrm.z, -SN.z);
+    if (XD) {
         if (g.gL != 0.f) {
             const float m = 0.5f * (a + b);
             const float Wlt = g.Wtot - DS.W - w, Slt = g.Stot - DS.S - w * m;
             cdist = 2.f * (fmaf(m, Wlt, -Slt) + fmaf(-m, DS.W, DS.S)) + 0.666666667f * w * (b - a);
             gx += g.gL * fmaf(T_after, cdist, -DS.R);
         }
-        prio = fabsf(gx * al / fmaxf(trans, 1e-30f));
     }
+    if (XS) prio = fabsf(gx * al / fmaxf(trans, 1e-30f));
     // per-sample depth term, suffix Q_k = sum_{m>k} P_m (1 - e_m) t_m
     float Pk[K + 1];
     Pk[0] = 1.f;
@@ -1222,7 +1239,7 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
     }
     // normal: dL/dn = w g_N, through the normalisation (I - n n^T) / |grad|
     // and Eq. interp_grad_grad: dgrad/dV_c = (2 x_c - 1, 2 y_c - 1, 2 z_c - 1) / 4
-    if (EXTRA && nlen > 0.f) {
+    if (XN && nlen > 0.f) {
         const float dnx = w * g.gN0, dny = w * g.gN1, dnz = w * g.gN2;
         const float dot = dnx * nrm.x + dny * nrm.y + dnz * nrm.z;
         const float il = 0.25f / nlen;
@@ -1363,12 +1380,13 @@ struct BwdIn {
 // part's colour, depth (and normal) from the transmittance in front of it,
 // sweep 2 takes the gradients with the sums behind each voxel as total minus
 // prefix.
-template <int K, bool EXTRA>
+template <int K, int XM>
 __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList L, int p0, int p1, int idx0,
                                                int last, bool fallback, float T_before, float SC0, float SC1, float SC2,
                                                float SD, NrmSums SN, DistSums DSb, const ViewData vd,
                                                const WarpBlock wb, const PixelRay p, const PixelGrad g, Entry *st,
                                                RecSmem &rs, const BwdIn &in, float *dcol) {
+    constexpr bool XN = (XM & kXNrm) != 0, XD = (XM & kXDist) != 0, XS = (XM & kXStat) != 0;
     const int lane = threadIdx.x & 31;
     const int n_fb = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, fallback ? last + 1 : idx0));
     // sweep 1: this part's own sums, from the transmittance in front of it
@@ -1394,14 +1412,14 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 Ct1 = fmaf(w, e.col.y, Ct1);
                 Ct2 = fmaf(w, e.col.z, Ct2);
                 Dt = fmaf(T, dloc, Dt);
-                if (EXTRA) {
+                if (XN) {
                     float3 n;
                     voxel_normal(e.g0, e.g1, n);
                     Nt.x = fmaf(w, n.x, Nt.x);
                     Nt.y = fmaf(w, n.y, Nt.y);
                     Nt.z = fmaf(w, n.z, Nt.z);
-                    if (g.gL != 0.f) dist_add(dp, w, a, b);
                 }
+                if (XD && g.gL != 0.f) dist_add(dp, w, a, b);
                 T *= trans;
             }
         }
@@ -1455,7 +1473,7 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 // sums behind it including its own share and let the
                 // distortion term subtract it (see below)
                 float w_own = 0.f, m_own = 0.f, c_own = 0.f;
-                if (EXTRA && g.gL != 0.f) {
+                if (XD && g.gL != 0.f) {
                     float tr, dl, al_;
                     hit_fwd<K>(e, p, a, b, tr, dl, al_);
                     w_own = Tf * al_;
@@ -1463,35 +1481,35 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                 }
                 const DistSums Db = {g.Wtot - WA - PW - w_own, g.Stot - SA - PS - w_own * m_own, 0.f};
                 DistSums Dx = Db;
-                if (EXTRA && g.gL != 0.f) {
+                if (XD && g.gL != 0.f) {
                     // dL/dw of this voxel from the prefix and suffix sums
                     const float Wlt = WA + PW, Slt = SA + PS;
                     c_own = 2.f * (fmaf(m_own, Wlt, -Slt) + fmaf(-m_own, Db.W, Db.S)) +
                             0.666666667f * w_own * (b - a);
                     Dx.R = Rt - PR - w_own * c_own;
                 }
-                hit_grad<K, false, EXTRA>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, Nb, Dx, dgeo,
+                hit_grad<K, false, XM>(e, p, g, a, b, Tf, Ct0 - PC0, Ct1 - PC1, Ct2 - PC2, Dt - PD, Nb, Dx, dgeo,
                                           dc, T_i, Ta, w, dloc, n, prio, cdist);
                 PC0 = fmaf(w, e.col.x, PC0);
                 PC1 = fmaf(w, e.col.y, PC1);
                 PC2 = fmaf(w, e.col.z, PC2);
                 PD = fmaf(T_i, dloc, PD);
-                if (EXTRA) {
-                    if (in.max_weight)
-                        atomicMax(reinterpret_cast<int *>(in.max_weight) + __float_as_int(e.col.w), __float_as_int(w));
+                if (XS && in.max_weight)
+                    atomicMax(reinterpret_cast<int *>(in.max_weight) + __float_as_int(e.col.w), __float_as_int(w));
+                if (XN) {
                     PN.x = fmaf(w, n.x, PN.x);
                     PN.y = fmaf(w, n.y, PN.y);
                     PN.z = fmaf(w, n.z, PN.z);
-                    if (g.gL != 0.f) {
-                        PW += w_own;
-                        PS = fmaf(w_own, m_own, PS);
-                        PR = fmaf(w_own, c_own, PR);
-                    }
+                }
+                if (XD && g.gL != 0.f) {
+                    PW += w_own;
+                    PS = fmaf(w_own, m_own, PS);
+                    PR = fmaf(w_own, c_own, PR);
                 }
                 Tf = Ta;
                 rec_write(rs, rec_slot(rs, k, rb), dgeo, dc, prio);
             }
-            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol, EXTRA ? in.priority : nullptr);
+            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol, XS ? in.priority : nullptr);
             k_lo = k_hi;
             if (k_lo >= 32) break;
         }
@@ -1499,9 +1517,10 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
     }
 }
 
-template <int K, bool EXTRA>
+template <int K, int XM>
 __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entry *st, RecSmem &rs,
                                          const BwdIn &in) {
+    constexpr bool XN = (XM & kXNrm) != 0, XD = (XM & kXDist) != 0, XS = (XM & kXStat) != 0;
     const ItemView iv = item_view(f, it.g);
     const DevCam &cam = f.views[iv.view];
     const ViewData &vd = iv.vd;
@@ -1527,14 +1546,14 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         }
         if (in.d_depth) g.gD = in.d_depth[o];
         if (in.d_alpha) g.gA = in.d_alpha[o];
-        if (EXTRA && in.d_normal) {
+        if (XN && in.d_normal) {
             const float *gn = in.d_normal + 3 * (size_t)cam.pix_base + px;
             g.gN0 = gn[0];
             g.gN1 = gn[HW];
             g.gN2 = gn[2 * HW];
         }
         g.Tfin = in.T[o];
-        if (EXTRA && in.d_dist) {
+        if (XD && in.d_dist) {
             g.gL = in.d_dist[o];
             g.Wtot = 1.f - g.Tfin;
             g.Stot = in.dist[2 * (size_t)cam.pix_base + HW + px];
@@ -1554,7 +1573,7 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         // which must include the normal image and the distortion sums when
         // their gradients are asked for
         const unsigned done = f.status->fwd_done;
-        if (done == 0 || (EXTRA && in.d_normal && !(done & 2u)) || (EXTRA && in.d_dist && !(done & 4u))) {
+        if (done == 0 || (XN && in.d_normal && !(done & 2u)) || (XD && in.d_dist && !(done & 4u))) {
             if (lane == 0) atomicOr(&f.status->flags, SVR_FLAG_NO_FORWARD);
             return;
         }
@@ -1567,21 +1586,21 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
         SD = q[3 * 32];
         T_after = q[4 * 32];
         T_before = q[5 * 32];
-        if (EXTRA) {
+        if (XN) {
             SN.x = q[8 * 32];
             SN.y = q[9 * 32];
             SN.z = q[10 * 32];
-            if (in.d_dist) {
-                DS.W = q[11 * 32];
-                DS.S = q[12 * 32];
-                DS.R = q[13 * 32];
-            }
+        }
+        if (XD && in.d_dist) {
+            DS.W = q[11 * 32];
+            DS.S = q[12 * 32];
+            DS.R = q[13 * 32];
         }
     }
     const bool has = p.inside && last >= idx0;
     const bool fallback = has && T_after < 1e-30f;
     const bool active = has && !fallback;
-    float *prio_out = EXTRA ? in.priority : nullptr;
+    float *prio_out = XS ? in.priority : nullptr;
 
     // ---- back to front
     {
@@ -1622,24 +1641,23 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                     slab(e, p, a, b);
                     float T_i, Ta, w, dloc, dgeo[8], dc[3], prio = 0.f, cdist = 0.f;
                     float3 n;
-                    hit_grad<K, true, EXTRA>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, SN, DS, dgeo, dc, T_i, Ta, w,
+                    hit_grad<K, true, XM>(e, p, g, a, b, T_after, SC0, SC1, SC2, SD, SN, DS, dgeo, dc, T_i, Ta, w,
                                              dloc, n, prio, cdist);
                     SC0 = fmaf(w, e.col.x, SC0);
                     SC1 = fmaf(w, e.col.y, SC1);
                     SC2 = fmaf(w, e.col.z, SC2);
                     SD = fmaf(T_i, dloc, SD);
-                    if (EXTRA) {
-                        if (in.max_weight)
-                            atomicMax(reinterpret_cast<int *>(in.max_weight) + __float_as_int(e.col.w),
-                                      __float_as_int(w));
+                    if (XS && in.max_weight)
+                        atomicMax(reinterpret_cast<int *>(in.max_weight) + __float_as_int(e.col.w), __float_as_int(w));
+                    if (XN) {
                         SN.x = fmaf(w, n.x, SN.x);
                         SN.y = fmaf(w, n.y, SN.y);
                         SN.z = fmaf(w, n.z, SN.z);
-                        if (g.gL != 0.f) {
-                            DS.W += w;
-                            DS.S = fmaf(w, 0.5f * (a + b), DS.S);
-                            DS.R = fmaf(w, cdist, DS.R);
-                        }
+                    }
+                    if (XD && g.gL != 0.f) {
+                        DS.W += w;
+                        DS.S = fmaf(w, 0.5f * (a + b), DS.S);
+                        DS.R = fmaf(w, cdist, DS.R);
                     }
                     T_after = T_i;
                     rec_write(rs, rec_slot(rs, k, base), dgeo, dc, prio);
@@ -1655,11 +1673,11 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     // ---- front to back for pixels whose transmittance underflowed (rare:
     // kept out of line so that it does not weigh on the main path's registers)
     if (__any_sync(0xffffffffu, fallback))
-        bwd_front_to_back<K, EXTRA>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, SN, DS, vd, wb,
+        bwd_front_to_back<K, XM>(f, L, p0, p1, idx0, last, fallback, T_before, SC0, SC1, SC2, SD, SN, DS, vd, wb,
                                     p, g, st, rs, in, dcol);
 }
 
-template <int K, bool EXTRA>
+template <int K, int XM>
 __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(FrameDev f, BwdIn in) {
     __shared__ Entry stage[kBwdWarps][kBatch];
     __shared__ RecSmem recs[kBwdWarps];
@@ -1669,7 +1687,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(Frame
     const unsigned n_items = f.status->n_queue * bpt;
     Item it;
     while (next_item(&f.status->bwd_next, n_items, bpt, f.order, it)) {
-        bwd_item<K, EXTRA>(f, it, st, recs[warp], in);
+        bwd_item<K, XM>(f, it, st, recs[warp], in);
         __syncwarp();
     }
 }
@@ -1768,14 +1786,14 @@ static cudaError_t fwd_k(const FrameDev &f, const FwdOut &out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int K, bool EXTRA>
+template <int K, int XM>
 static cudaError_t bwd_k(const FrameDev &f, const BwdIn &in, cudaStream_t s) {
     static DeviceCache cache;
     const unsigned grid =
-        device_cached(cache, [] { return persistent_grid(k_render_bwd<K, EXTRA>, kBwdThreads); });
+        device_cached(cache, [] { return persistent_grid(k_render_bwd<K, XM>, kBwdThreads); });
     const unsigned items = (unsigned)f.total_tiles * (unsigned)f.blocks_per_tile;
     const unsigned g = tmin<unsigned>(grid, (items + kBwdWarps - 1) / kBwdWarps);
-    k_render_bwd<K, EXTRA><<<g, kBwdThreads, 0, s>>>(f, in);
+    k_render_bwd<K, XM><<<g, kBwdThreads, 0, s>>>(f, in);
     return cudaGetLastError();
 }
 
@@ -1783,20 +1801,23 @@ cudaError_t launch_render_fwd(const FrameDev &f, float *rgb, float *depth, float
                               float *T_final, int32_t *last, int2 *stats, float *normal, float *max_weight,
                               float *dist, cudaStream_t s) {
     const FwdOut out = {rgb, depth, alpha, T_final, last, stats, normal, max_weight, dist};
-    const int mode = stats ? kModeStats : (normal || max_weight || dist) ? kModeExtra : kModePlain;
+    const int mode = stats ? kModeStats : (normal || max_weight) ? kModeExtra : dist ? kModeDist : kModePlain;
     // the work counter is zero here: cleared with the status block, then by
     // the last warp of every launch
     cudaError_t e;
-    switch (f.K * 3 + mode) {
-        case 3: e = fwd_k<1, kModePlain>(f, out, s); break;
-        case 4: e = fwd_k<1, kModeStats>(f, out, s); break;
-        case 5: e = fwd_k<1, kModeExtra>(f, out, s); break;
-        case 6: e = fwd_k<2, kModePlain>(f, out, s); break;
-        case 7: e = fwd_k<2, kModeStats>(f, out, s); break;
-        case 8: e = fwd_k<2, kModeExtra>(f, out, s); break;
-        case 9: e = fwd_k<3, kModePlain>(f, out, s); break;
-        case 10: e = fwd_k<3, kModeStats>(f, out, s); break;
-        case 11: e = fwd_k<3, kModeExtra>(f, out, s); break;
+    switch (f.K * 4 + mode) {
+        case 4: e = fwd_k<1, kModePlain>(f, out, s); break;
+        case 5: e = fwd_k<1, kModeStats>(f, out, s); break;
+        case 6: e = fwd_k<1, kModeExtra>(f, out, s); break;
+        case 7: e = fwd_k<1, kModeDist>(f, out, s); break;
+        case 8: e = fwd_k<2, kModePlain>(f, out, s); break;
+        case 9: e = fwd_k<2, kModeStats>(f, out, s); break;
+        case 10: e = fwd_k<2, kModeExtra>(f, out, s); break;
+        case 11: e = fwd_k<2, kModeDist>(f, out, s); break;
+        case 12: e = fwd_k<3, kModePlain>(f, out, s); break;
+        case 13: e = fwd_k<3, kModeStats>(f, out, s); break;
+        case 14: e = fwd_k<3, kModeExtra>(f, out, s); break;
+        case 15: e = fwd_k<3, kModeDist>(f, out, s); break;
         default: return cudaErrorInvalidValue;
     }
     return e;
@@ -1811,14 +1832,19 @@ cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
     const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority, d_dist, dist, max_weight};
-    const bool extra = d_normal != nullptr || priority != nullptr || d_dist != nullptr || max_weight != nullptr;
-    switch (f.K * 2 + (extra ? 1 : 0)) {
-        case 2: e = bwd_k<1, false>(f, in, s); break;
-        case 3: e = bwd_k<1, true>(f, in, s); break;
-        case 4: e = bwd_k<2, false>(f, in, s); break;
-        case 5: e = bwd_k<2, true>(f, in, s); break;
-        case 6: e = bwd_k<3, false>(f, in, s); break;
-        case 7: e = bwd_k<3, true>(f, in, s); break;
+    // extras: none, the distortion gradient alone (the training step's), or
+    // every extra (normal gradient, priority, max weight, distortion)
+    const int xm = (d_normal || priority || max_weight) ? 2 : d_dist ? 1 : 0;
+    switch (f.K * 3 + xm) {
+        case 3: e = bwd_k<1, 0>(f, in, s); break;
+        case 4: e = bwd_k<1, kXDist>(f, in, s); break;
+        case 5: e = bwd_k<1, kXAll>(f, in, s); break;
+        case 6: e = bwd_k<2, 0>(f, in, s); break;
+        case 7: e = bwd_k<2, kXDist>(f, in, s); break;
+        case 8: e = bwd_k<2, kXAll>(f, in, s); break;
+        case 9: e = bwd_k<3, 0>(f, in, s); break;
+        case 10: e = bwd_k<3, kXDist>(f, in, s); break;
+        case 11: e = bwd_k<3, kXAll>(f, in, s); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

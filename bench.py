@@ -7,7 +7,10 @@ t_stop = 1e-4.  A step is one pass of the whole path: svr_preprocess,
 svr_bin_sort (no host sync), svr_render_fwd and svr_render_bwd with seeded
 upstream gradients, everything resident in HBM.  The reported value is
 forward+backward steps/s over all ranks; the forward alone (preprocess, sort,
-render) is timed too.
+render) is timed too.  On one GPU the line also carries ``large_batched``:
+eight 2560x1440 views of a ~8M-voxel octree (levels 4..11) rendered forward
++ backward in one graph-captured batch vs one launch sequence per view, with
+the device memory in use (``--no-large`` skips it).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -66,6 +69,9 @@ def parse():
                     help="pixels of the CPU oracle's timed sample (about 10-20 s on 16 cores)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-view batched vs per-view comparison")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large batched workload (8 x 2560x1440 views of ~8M voxels; its scene "
+                         "takes about a minute to generate)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the timings of the normal / pruning / subdivision outputs, the "
                          "anti-aliasing kernels and the training step")
@@ -302,6 +308,11 @@ def run_native(args, rank, world, local_rank):
     if not args.no_extras and args.workload == "shell1m":
         extras = run_extras(args, scene, dscene, cam, dev, kw, fr, out, (g_rgb, g_depth, g_alpha), P)
 
+    # the large batched workload (8 x 2560x1440 views of ~8M voxels), on one GPU
+    large = None
+    if world == 1 and not args.no_large and args.workload == "shell1m":
+        large = run_large_batched(args)
+
     if rank != 0:
         return
     value = whole_job_rate(world, ms_step)
@@ -340,6 +351,7 @@ def run_native(args, rank, world, local_rank):
                                   "ops_per_hit": OPS_HIT[K]}},
         "batched": batched,
         "next_rows": extras,
+        "large_batched": large,
         "frame_hbm": {"algorithmic_bytes": frame_bytes, "achieved_gbs": frame_bytes / (ms_step * 1e-3) / 1e9,
                       "peak_gbs": hbm, "frac": frame_bytes / (ms_step * 1e-3) / 1e9 / hbm,
                       "peak_from": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"},
@@ -644,34 +656,14 @@ def run_extras(args, scene, dscene, cam, dev, kw, fr, out, grads, P, reps=10):
     return res
 
 
-def sampled_parity(scene, cams, out, pixel_base, n_px, seed):
-    """Largest absolute difference of rgb, depth and alpha between batched
-    outputs (numpy, batch layout) and the oracle on n_px seeded pixels of
-    every view, pixels near the stop threshold excluded."""
-    import oracle
-    rng = np.random.default_rng(seed)
-    err = 0.0
-    for v, cam in enumerate(cams):
-        W, H = cam.width, cam.height
-        px = np.stack([rng.integers(0, W, n_px), rng.integers(0, H, n_px)], 1)
-        ref = oracle.render(scene, cam, K=3, t_stop=1e-4, pixels=px)
-        keep = ref["near_stop"] == 0
-        base = int(pixel_base[v])
-        lin = px[:, 1] * W + px[:, 0]
-        rgb = np.stack([out["rgb"][3 * base + c * W * H + lin] for c in range(3)], 0)
-        err = max(err, float(np.abs(rgb[:, keep] - ref["rgb"].T[:, keep]).max(initial=0.0)),
-                  float(np.abs(out["depth"][base + lin][keep] - ref["depth"][keep]).max(initial=0.0)),
-                  float(np.abs(out["alpha"][base + lin][keep] - ref["alpha"][keep]).max(initial=0.0)))
-    return err
-
-
 def run_large_batched(args, n_views=8, width=2560, height=1440):
     """The large batched workload: ~8M voxels (three noisy shells, levels
     4..11, at most 4 levels between touching voxels), 8 orbit views at
     2560x1440, K = 3, forward + backward in graph-captured batched launches
     (tile size and partitions tuned among a few candidates) vs one launch
-    sequence per view; device memory in use against 180 GB; parity of the
-    images on a seeded pixel sample against the oracle."""
+    sequence per view; device memory in use against 180 GB.  Returns the
+    measurements as a dict (its parity against the oracle is a -m gpu test
+    at the same size and launch configuration)."""
     import torch
     import synth
     from paper_2412_04459_gb300 import DeviceScene, Frame
@@ -717,12 +709,6 @@ def run_large_batched(args, n_views=8, width=2560, height=1440):
     used = total - free1
     allocated = torch.cuda.memory_allocated(dev)
     ws_bytes = sum(fr.ws_bytes() for fr in r.frames)
-    # parity on a seeded pixel sample of every view (forward outputs)
-    out = {k: v.detach().cpu().numpy() for k, v in r.out.items()}
-    n_px = 128
-    t1 = time.perf_counter()
-    max_err = sampled_parity(scene, cams, out, r.pixel_base, n_px, seed=11)
-    parity_s = time.perf_counter() - t1
     del r
     torch.cuda.empty_cache()
     # the same views as one launch sequence per view
@@ -765,11 +751,12 @@ def run_large_batched(args, n_views=8, width=2560, height=1440):
                    "before_scene_used_gb": (total - free0) / 1e9,
                    "workspace_gb": ws_bytes / 1e9, "budget_gb": 180.0, "frac_of_budget": used / 180e9,
                    "total_gb": total / 1e9},
-        "parity": {"pixels": n_px * n_views, "max_abs_err": max_err, "tolerance": 1e-4,
-                   "oracle_s": parity_s},
+        "parity": "tests/test_gpu_batched_oracle.py::test_large_workload_full_size_sampled",
         "scene_generation_s": gen_s, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    del frames, d_grid, d_sh, dscene
+    torch.cuda.empty_cache()
+    return line
 
 
 def frame_algorithmic_bytes(scene, P, H, W):
@@ -837,7 +824,7 @@ def main():
         return
     if args.workload == "shell8m":
         if rank == 0:
-            run_large_batched(args)
+            print(json.dumps(run_large_batched(args)), flush=True)
         return
     if world > 1:
         import torch

@@ -1119,7 +1119,8 @@ struct NrmSums {
 
 // Backward extras selected at compile time (XM bits): the normal image's
 // gradient, the distortion loss's gradient, the pruning/subdivision statistics
-// (priority and max weight).  Instantiated for none, distortion only and all.
+// (priority and max weight).  Instantiated for none, distortion, distortion
+// with the statistics, and all.
 constexpr int kXNrm = 1, kXDist = 2, kXStat = 4, kXAll = 7;
 
 // Gradient contributions of one hit, computed from one pass over its K
@@ -1832,19 +1833,24 @@ cudaError_t launch_render_bwd(const FrameDev &f, const float *d_rgb, const float
         e = cudaMemsetAsync(f.dcol, 0, sizeof(float) * 3 * (size_t)f.n_vox * f.n_views, s);
     if (e != cudaSuccess) return e;
     const BwdIn in = {d_rgb, d_depth, d_alpha, T_final, last, d_grid, d_normal, priority, d_dist, dist, max_weight};
-    // extras: none, the distortion gradient alone (the training step's), or
-    // every extra (normal gradient, priority, max weight, distortion)
-    const int xm = (d_normal || priority || max_weight) ? 2 : d_dist ? 1 : 0;
-    switch (f.K * 3 + xm) {
-        case 3: e = bwd_k<1, 0>(f, in, s); break;
-        case 4: e = bwd_k<1, kXDist>(f, in, s); break;
-        case 5: e = bwd_k<1, kXAll>(f, in, s); break;
-        case 6: e = bwd_k<2, 0>(f, in, s); break;
-        case 7: e = bwd_k<2, kXDist>(f, in, s); break;
-        case 8: e = bwd_k<2, kXAll>(f, in, s); break;
-        case 9: e = bwd_k<3, 0>(f, in, s); break;
-        case 10: e = bwd_k<3, kXDist>(f, in, s); break;
-        case 11: e = bwd_k<3, kXAll>(f, in, s); break;
+    // extras: none; the distortion gradient alone (the training step's); it
+    // and the pruning/subdivision statistics (the training step that gathers
+    // them); every extra (the normal gradient as well)
+    const int xm = d_normal ? 3 : (priority || max_weight) ? 2 : d_dist ? 1 : 0;
+    constexpr int kXDS = kXDist | kXStat;
+    switch (f.K * 4 + xm) {
+        case 4: e = bwd_k<1, 0>(f, in, s); break;
+        case 5: e = bwd_k<1, kXDist>(f, in, s); break;
+        case 6: e = bwd_k<1, kXDS>(f, in, s); break;
+        case 7: e = bwd_k<1, kXAll>(f, in, s); break;
+        case 8: e = bwd_k<2, 0>(f, in, s); break;
+        case 9: e = bwd_k<2, kXDist>(f, in, s); break;
+        case 10: e = bwd_k<2, kXDS>(f, in, s); break;
+        case 11: e = bwd_k<2, kXAll>(f, in, s); break;
+        case 12: e = bwd_k<3, 0>(f, in, s); break;
+        case 13: e = bwd_k<3, kXDist>(f, in, s); break;
+        case 14: e = bwd_k<3, kXDS>(f, in, s); break;
+        case 15: e = bwd_k<3, kXAll>(f, in, s); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

@@ -18,6 +18,7 @@ This module only builds inputs.  It holds none of the rasterizer's arithmetic.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import hashlib
 import os
@@ -137,6 +138,43 @@ _N26 = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1,
                  if (a, b, c) != (0, 0, 0)], np.int64)
 
 
+def _unique(x: np.ndarray) -> np.ndarray:
+    """Sorted distinct values of a 1-D integer array (np.unique's result; a
+    plain sort and a neighbour comparison, much faster on large arrays)."""
+    s = np.sort(np.asarray(x).ravel())
+    if len(s) == 0:
+        return s
+    keep = np.empty(len(s), bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
+def _isin_sorted(x: np.ndarray, table: np.ndarray) -> np.ndarray:
+    """x's elements that occur in `table` (sorted, distinct): np.isin's result."""
+    if len(table) == 0:
+        return np.zeros(np.shape(x), bool)
+    i = np.minimum(np.searchsorted(table, x), len(table) - 1)
+    return table[i] == x
+
+
+def _unique_first_inverse(x: np.ndarray):
+    """np.unique(x, return_index=True, return_inverse=True) of a 1-D integer
+    array: distinct values, the index of each one's first occurrence, and the
+    position of every element's value among them."""
+    order = np.argsort(x)
+    s = x[order]
+    new = np.empty(len(s), bool)
+    if not len(s):
+        return s, order, order
+    new[0] = True
+    np.not_equal(s[1:], s[:-1], out=new[1:])
+    inv = np.empty(len(s), np.int64)
+    inv[order] = np.cumsum(new) - 1
+    starts = np.flatnonzero(new)
+    return s[starts], np.minimum.reduceat(order, starts), inv
+
+
 def _cell_key(level, ijk: np.ndarray) -> np.ndarray:
     level = np.broadcast_to(np.asarray(level, np.int64), ijk.shape[:1])
     return (level << 51) | (ijk[:, 0] << 34) | (ijk[:, 1] << 17) | ijk[:, 2]
@@ -153,36 +191,41 @@ def balance_levels(cells: Cells, max_diff: int) -> Cells:
     """
     if len(cells) == 0:
         return cells
+    mask = np.int64((1 << 17) - 1)
+
+    def ijk_of(keys):
+        return np.stack([(keys >> 34) & mask, (keys >> 17) & mask, keys & mask], axis=1)
+
     while True:
         lmin, lmax = int(cells.level.min()), int(cells.level.max())
         by_level = {l: cells.ijk[cells.level == l] for l in range(lmin, lmax + 1)}
-        leaf_keys = {l: np.sort(_cell_key(l, v)) for l, v in by_level.items()}
+        leaf_keys = {l: _unique(_cell_key(l, v)) for l, v in by_level.items()}
         # nodes (leaves and their ancestors) of each level
         nodes = {}
         for m in range(lmin, lmax + 1):
-            parts = [by_level[l] >> (l - m) for l in range(m, lmax + 1) if len(by_level[l])]
-            nodes[m] = np.unique(_cell_key(m, np.concatenate(parts))) if parts else np.zeros(0, np.int64)
+            parts = [_cell_key(m, by_level[l] >> (l - m)) for l in range(m, lmax + 1) if len(by_level[l])]
+            nodes[m] = _unique(np.concatenate(parts)) if parts else np.zeros(0, np.int64)
         split_keys = []
         for l in range(lmin + max_diff + 1, lmax + 1):
             if not len(by_level[l]):
                 continue
             m = l - max_diff
-            anc = np.unique(by_level[l] >> max_diff, axis=0)
+            anc = ijk_of(_unique(_cell_key(m, by_level[l] >> max_diff)))
             nb = (anc[:, None, :] + _N26[None]).reshape(-1, 3)
             nb = nb[((nb >= 0) & (nb < (1 << m))).all(axis=1)]
-            nb = np.unique(nb, axis=0)
-            missing = nb[~np.isin(_cell_key(m, nb), nodes[m])]
+            kb = _unique(_cell_key(m, nb))
+            missing = ijk_of(kb[~_isin_sorted(kb, nodes[m])])
             for m2 in range(m - 1, lmin - 1, -1):
                 if not len(missing):
                     break
                 up = missing >> (m - m2)
-                hit = np.isin(_cell_key(m2, up), leaf_keys[m2])
+                hit = _isin_sorted(_cell_key(m2, up), leaf_keys[m2])
                 if hit.any():
-                    split_keys.append(np.unique(_cell_key(m2, up[hit])))
+                    split_keys.append(_unique(_cell_key(m2, up[hit])))
                 missing = missing[~hit]
         if not split_keys:
             return cells
-        go = np.isin(_cell_key(cells.level, cells.ijk), np.unique(np.concatenate(split_keys)))
+        go = _isin_sorted(_cell_key(cells.level, cells.ijk), _unique(np.concatenate(split_keys)))
         cells = Cells.cat([cells.take(~go), split(cells.take(go))])
 
 
@@ -194,7 +237,7 @@ def corner_points(cells: Cells):
     cijk = cells.ijk[:, None, :] + _BITS[None]                     # [n, 8, 3]
     key = ((cells.level[:, None] << 51) | (cijk[..., 0] << 34)
            | (cijk[..., 1] << 17) | cijk[..., 2])
-    uniq, first, inv = np.unique(key.reshape(-1), return_index=True, return_inverse=True)
+    uniq, first, inv = _unique_first_inverse(key.reshape(-1))
     pos = (cells.centre[:, None, :] + (_BITS[None] - 0.5) * cells.size[:, None, None])
     pos = pos.reshape(-1, 3)[first]
     return inv.reshape(n, 8).astype(np.int32), pos
@@ -307,8 +350,23 @@ def shell_radius(p: np.ndarray, seed: int, radius: float, amp: float,
     return radius + amp * n / tot
 
 
+_CHUNK = 1 << 18
+
+
 def shell_distance(p: np.ndarray, seed: int, centers, radii, amp: float) -> np.ndarray:
-    """Distance-like measure | |p - c| - r(p) | to the nearest of several shells."""
+    """Distance-like measure | |p - c| - r(p) | to the nearest of several shells.
+
+    Large point sets are cut into chunks evaluated on a thread pool (NumPy
+    releases the GIL in its loops); every point's value depends only on the
+    point, so the result is the same."""
+    if len(p) <= _CHUNK:
+        return _shell_distance(p, seed, centers, radii, amp)
+    chunks = [p[i:i + _CHUNK] for i in range(0, len(p), _CHUNK)]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(chunks), os.cpu_count() or 1)) as ex:
+        return np.concatenate(list(ex.map(lambda c: _shell_distance(c, seed, centers, radii, amp), chunks)))
+
+
+def _shell_distance(p: np.ndarray, seed: int, centers, radii, amp: float) -> np.ndarray:
     d = np.full(len(p), np.inf)
     for s, (c, r) in enumerate(zip(centers, radii)):
         rr = shell_radius(p, seed * 31 + s, r, amp)

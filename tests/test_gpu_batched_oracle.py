@@ -92,29 +92,16 @@ def _tile_row_and_random(cam, tile, n_tiles, n_random, rng):
     return np.unique(np.concatenate(px), axis=0)
 
 
-def test_reduced_large_workload_against_oracle():
-    """The large batched workload's structure at reduced size: three noisy
-    shells, leaves of levels 4..11 with touching leaves at most 4 levels
-    apart (146,504 voxels), three 2560x1440 orbit views, K = 3, t_stop =
-    1e-4, forward + backward in one graph-replayed batch.  Images on a whole
-    tile row of the first view, 16 tiles of a row of the others, and random
-    pixels; gradients from the upstream gradients of random pixels."""
+def _batch_against_oracle(sc, cams, tile, img_px, grad_px, grad_vals):
+    """One graph-replayed batched forward + backward of `cams` with upstream
+    gradients grad_vals at grad_px (zeroed where the oracle is near the stop
+    threshold); images at img_px and the summed gradients against the
+    oracle."""
     import torch
     from paper_2412_04459_gb300 import DeviceScene
     from paper_2412_04459_gb300.autotune import BatchedRenderer
-    sc = cached("three_shell_reduced", lambda: synth.shell_scene(0, 146_504, p_split=0.25,
-                                                                spec=synth.scenes.SHELL_THREE))
-    assert sc.max_level == 11 and sc.n_vox > 100_000
-    cams = [synth.orbit_camera(200 + v, 2560, 1440) for v in range(3)]
     dev = DeviceScene.from_host(sc)
-    r = BatchedRenderer(dev, cams, K=3, t_stop=1e-4, tile=16)
-    rng = np.random.default_rng(12)
-    img_px, grad_px, grad_vals = [], [], []
-    for v, c in enumerate(cams):
-        img_px.append(_tile_row_and_random(c, 16, None if v == 0 else 16, 1500, rng))
-        gp = np.unique(np.stack([rng.integers(0, c.width, 1500), rng.integers(0, c.height, 1500)], 1), axis=0)
-        grad_px.append(gp)
-        grad_vals.append(rng.normal(size=(len(gp), 5)))
+    r = BatchedRenderer(dev, cams, K=3, t_stop=1e-4, tile=tile)
     refs_g = [oracle.render(sc, c, K=3, t_stop=1e-4, pixels=grad_px[v]) for v, c in enumerate(cams)]
     for v, c in enumerate(cams):
         keep = refs_g[v]["near_stop"] == 0
@@ -148,3 +135,48 @@ def test_reduced_large_workload_against_oracle():
         ms[1] += m["sh_seg"]
     compare_grads(r.d_grid.cpu().numpy(), og, name="grid", mag=mg)
     compare_grads(r.d_sh.cpu().numpy(), osh, name="sh", mag=ms)
+    return pairs
+
+
+def _grad_pixels(cams, n, rng):
+    px, vals = [], []
+    for c in cams:
+        gp = np.unique(np.stack([rng.integers(0, c.width, n), rng.integers(0, c.height, n)], 1), axis=0)
+        px.append(gp)
+        vals.append(rng.normal(size=(len(gp), 5)))
+    return px, vals
+
+
+def test_reduced_large_workload_against_oracle():
+    """The large batched workload's structure at reduced size: three noisy
+    shells, leaves of levels 4..11 with touching leaves at most 4 levels
+    apart (146,504 voxels), three 2560x1440 orbit views, K = 3, t_stop =
+    1e-4, forward + backward in one graph-replayed batch.  Images on a whole
+    tile row of the first view, 16 tiles of a row of the others, and random
+    pixels; gradients from the upstream gradients of random pixels."""
+    sc = cached("three_shell_reduced", lambda: synth.shell_scene(0, 146_504, p_split=0.25,
+                                                                spec=synth.scenes.SHELL_THREE))
+    assert sc.max_level == 11 and sc.n_vox > 100_000
+    cams = [synth.orbit_camera(200 + v, 2560, 1440) for v in range(3)]
+    rng = np.random.default_rng(12)
+    img_px = [_tile_row_and_random(c, 16, None if v == 0 else 16, 1500, rng) for v, c in enumerate(cams)]
+    grad_px, grad_vals = _grad_pixels(cams, 1500, rng)
+    _batch_against_oracle(sc, cams, 16, img_px, grad_px, grad_vals)
+
+
+def test_large_workload_full_size_sampled():
+    """The large batched workload at full size, in the launch configuration
+    bench.py times (tile 16, one partition): the ~8M-voxel three-shell octree
+    (levels 4..11, touching leaves at most 4 levels apart), the bench's eight
+    2560x1440 orbit views, K = 3, t_stop = 1e-4, one graph-replayed batched
+    forward + backward.  Images on 4 tiles of a tile row of every view plus
+    random pixels; gradients from the upstream gradients of random pixels of
+    every view (the oracle tests every voxel against every sampled ray)."""
+    sc = cached("three_shell_8m", lambda: synth.shell_scene(0, 8_000_000, spec=synth.scenes.SHELL_THREE))
+    assert sc.max_level == 11 and sc.n_vox > 8_000_000
+    cams = [synth.orbit_camera(200 + v, 2560, 1440) for v in range(8)]
+    rng = np.random.default_rng(13)
+    img_px = [_tile_row_and_random(c, 16, 4, 192, rng) for c in cams]
+    grad_px, grad_vals = _grad_pixels(cams, 192, rng)
+    pairs = _batch_against_oracle(sc, cams, 16, img_px, grad_px, grad_vals)
+    assert pairs > 5 * 10 ** 7

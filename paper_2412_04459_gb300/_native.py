@@ -9,7 +9,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsvr.so")
+# SVR_DEBUG=1 in the environment loads the index-checked build instead
+DEBUG = os.environ.get("SVR_DEBUG", "") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libsvr_debug.so" if DEBUG else "libsvr.so")
 
 SVR_OK = 0
 SVR_ERR_INVALID = 1
@@ -103,6 +105,8 @@ SIGNATURES = {
     "svr_frame_buffers": (ctypes.c_int, [_P, _P]),
     "svr_last_error": (ctypes.c_char_p, []),
     "svr_version": (ctypes.c_int, []),
+    "svr_debug_build": (ctypes.c_int, []),
+    "svr_debug_report": (ctypes.c_int, [_P]),
 }
 
 
@@ -111,8 +115,8 @@ def lib():
     global _LIB
     if _LIB is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2412_04459_gb300.build.build() "
-                               "(nvcc, sm_103a); there is no CPU fallback")
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2412_04459_gb300.build.build("
+                               f"{'debug=True' if DEBUG else ''}) (nvcc, sm_103a); there is no CPU fallback")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)
@@ -120,6 +124,14 @@ def lib():
             fn.argtypes = args
         _LIB = L
     return _LIB
+
+
+def debug_report():
+    """(failed checks, site, index, bound) of the current device's index-check
+    report (all zero unless the SVR_DEBUG build is loaded); clears it."""
+    out = (ctypes.c_uint64 * 4)()
+    check(lib().svr_debug_report(out), "svr_debug_report")
+    return tuple(int(x) for x in out)
 
 
 def check(code: int, where: str):

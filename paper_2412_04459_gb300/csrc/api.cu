@@ -132,6 +132,40 @@ int check_views(const svr_camera *cams, int n_views, const svr_params *p, int64_
     return SVR_OK;
 }
 
+}  // namespace
+
+namespace svr {
+
+DebugBlock *debug_block() {
+#ifdef SVR_DEBUG
+    static std::atomic<DebugBlock *> blocks[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    DebugBlock *b = blocks[dev].load();
+    if (b == nullptr) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(DebugBlock)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(DebugBlock)) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        DebugBlock *expected = nullptr;
+        if (!blocks[dev].compare_exchange_strong(expected, (DebugBlock *)p)) {
+            cudaFree(p);
+            return expected;
+        }
+        b = (DebugBlock *)p;
+    }
+    return b;
+#else
+    return nullptr;
+#endif
+}
+
+}  // namespace svr
+
+namespace {
+
 svr::FrameDev frame_dev(const svr_frame *f) {
     svr::FrameDev d;
     memset(&d, 0, sizeof(d));
@@ -197,6 +231,7 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.K = f->params.K;
     d.t_stop = f->params.t_stop;
     for (int i = 0; i < 3; ++i) d.bg[i] = f->params.bg[i];
+    d.debug = svr::debug_block();
     d.centre = f->scene.centre;
     d.level = f->scene.level;
     d.corner_idx = f->scene.corner_idx;
@@ -296,6 +331,33 @@ extern "C" {
 SVR_API const char *svr_last_error(void) { return g_err; }
 
 SVR_API int svr_version(void) { return 200; }
+
+SVR_API int svr_debug_build(void) {
+#ifdef SVR_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+SVR_API int svr_debug_report(uint64_t *out) {
+    if (!out) return svr::set_error(SVR_ERR_INVALID, "svr_debug_report: null output");
+    for (int i = 0; i < 4; ++i) out[i] = 0;
+#ifdef SVR_DEBUG
+    svr::DebugBlock *b = svr::debug_block();
+    if (!b) return svr::set_error(SVR_ERR_CUDA, "svr_debug_report: no debug block on this device");
+    svr::DebugBlock h;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, b, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(b, 0, sizeof(h));
+    if (e != cudaSuccess) return svr::set_error(SVR_ERR_CUDA, "svr_debug_report: %s", cudaGetErrorString(e));
+    out[0] = h.count;
+    out[1] = h.site;
+    out[2] = (uint64_t)h.index;
+    out[3] = (uint64_t)h.bound;
+#endif
+    return SVR_OK;
+}
 
 SVR_API size_t svr_workspace_size_views(int64_t n_vox, int64_t pair_capacity, const svr_camera *cams, int n_views,
                                         const svr_params *params) {

@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(FrameDev f) {
 #pragma unroll
         for (int i = 0; i < kEmitBatch; ++i) {
             gb[i] = cam.tile_base + ty * cam.ntx + tx;
-            mb[i] = ty <= rc.w ? (unsigned)f.tile_mask[gb[i]] : 0u;
+            mb[i] = ty <= rc.w && SVR_IN_BOUNDS(f.debug, kDbgTile, gb[i], f.total_tiles) ? (unsigned)f.tile_mask[gb[i]]
+                                                                                   : 0u;
             if (++tx > rc.y) {
                 tx = rc.x;
                 ++ty;

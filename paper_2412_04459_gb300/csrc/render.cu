@@ -134,7 +134,14 @@ struct WarpBlock {
 struct ViewData {
     const Record *rec;    // f.rec + view * N
     const ushort4 *box;   // f.box + view * N
+    DebugBlock *dbg;      // index checks of the SVR_DEBUG build
+    int64_t n;            // N
 };
+
+// Voxel id of a list entry's value (index-checked in the SVR_DEBUG build).
+__device__ __forceinline__ uint32_t vid_of(const ViewData &vd, uint32_t val) {
+    return checked(vd.dbg, kDbgVoxel, val & 0x1FFFFFFFu, vd.n);
+}
 
 // Pixel of the calling lane in block blk of a tile (tile edge 8, 16 or 32:
 // tile / 8 blocks of 8x4 pixels per block row).
@@ -231,6 +238,7 @@ __global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const 
     const DevCam &cam = f.views[view];
     const int tile = g - cam.tile_base;
     const uint2 rg = f.ranges[g];
+    if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1)) return;
     const int beg = (int)rg.x, end = (int)rg.y, L = end - beg;
     const int B = f.blocks_per_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const 
             const int t = threadIdx.x + kListThreads * r;
             unsigned m = 0;
             if (t < n) {
-                const ushort4 bx = __ldg(boxes + (v4[r] & 0x1FFFFFFFu));
+                const ushort4 bx = __ldg(boxes + checked(f.debug, kDbgVoxel, v4[r] & 0x1FFFFFFFu, f.n_vox));
                 const int cx0 = max((int)bx.x - tx0, 0), cx1 = min((int)bx.y - tx0, T - 1);
                 const int cy0 = max((int)bx.z - ty0, 0), cy1 = min((int)bx.w - ty0, T - 1);
                 if (cx0 <= cx1 && cy0 <= cy1) {
@@ -338,18 +346,18 @@ __device__ __forceinline__ void fetch_vi(Lookahead &la, const uint2 *__restrict_
 }
 
 __device__ __forceinline__ void fetch_box(Lookahead &la, const ViewData &vd) {
-    la.box = la.valid ? __ldg(vd.box + (la.vi.x & 0x1FFFFFFFu)) : make_ushort4(0, 0, 0, 0);
+    la.box = la.valid ? __ldg(vd.box + vid_of(vd, la.vi.x)) : make_ushort4(0, 0, 0, 0);
 }
 
 // Ask for the looked-ahead entry's 64-byte record in L1 (the backward stages
 // with plain loads one batch later).
 __device__ __forceinline__ void prefetch_record(const Lookahead &la, const ViewData &vd) {
-    if (la.valid) asm volatile("prefetch.global.L1 [%0];" ::"l"(vd.rec + (la.vi.x & 0x1FFFFFFFu)));
+    if (la.valid) asm volatile("prefetch.global.L1 [%0];" ::"l"(vd.rec + vid_of(vd, la.vi.x)));
 }
 
 // Stage the looked-ahead entries (lane j: entry j of the batch).
 __device__ __forceinline__ void stage_ahead(Entry *st, const ViewData &vd, const Lookahead &la) {
-    if (la.valid) stage_entry(st[threadIdx.x & 31], la.vi.x, (int)la.vi.y, vd.rec);
+    if (la.valid) stage_entry(st[threadIdx.x & 31], (la.vi.x & 0xE0000000u) | vid_of(vd, la.vi.x), (int)la.vi.y, vd.rec);
     __syncwarp();
 }
 
@@ -404,6 +412,8 @@ __device__ __forceinline__ ItemView item_view(const FrameDev &f, int g) {
     iv.tile = g - f.views[iv.view].tile_base;
     iv.vd.rec = f.rec + (size_t)iv.view * f.n_vox;
     iv.vd.box = f.box + (size_t)iv.view * f.n_vox;
+    iv.vd.dbg = f.debug;
+    iv.vd.n = f.n_vox;
     return iv;
 }
 
@@ -414,6 +424,7 @@ struct ItemList {
     int beg, end;       // the tile's range in the sorted pairs
     uint2 ts;           // segments of the tile, first slot
     const uint32_t *seg_len; // split tiles: segment k of this block holds seg_len[k * B] entries
+    DebugBlock *dbg;         // index checks of the SVR_DEBUG build
 };
 
 __device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk) {
@@ -422,10 +433,14 @@ __device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk)
     const int B = f.blocks_per_tile;
     L.beg = (int)rg.x;
     L.end = (int)rg.y;
+    if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1) || !SVR_IN_BOUNDS(f.debug, kDbgRange, rg.x, rg.y + 1))
+        L.beg = L.end = 0;
     L.list = f.blist + (size_t)B * L.beg + (size_t)blk * (L.end - L.beg);
-    L.n_list = (int)f.blen[(size_t)g * B + blk];
+    L.n_list = (int)f.blen[(size_t)g * B + blk];   // unsplit tiles (split ones count per segment)
     L.ts = f.tile_seg[g];
+    if (L.ts.x <= 1 && !SVR_IN_BOUNDS(f.debug, kDbgBlockList, L.n_list, L.end - L.beg + 1)) L.n_list = 0;
     L.seg_len = f.seg_len + (size_t)L.ts.y * B + blk;
+    L.dbg = f.debug;
     return L;
 }
 
@@ -434,10 +449,12 @@ __device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk)
 __device__ __forceinline__ void seg_range(const ItemList &L, int B, int sg, int &p0, int &p1) {
     p0 = sg * kSegLen;
     p1 = p0 + (int)L.seg_len[(size_t)sg * B];
+    if (!SVR_IN_BOUNDS(L.dbg, kDbgBlockList, p1 - p0, kSegLen + 1)) p1 = p0;
 }
 
 // Segment sums of (segment slot, block): kSegFields rows of 32 pixels.
 __device__ __forceinline__ float *seg_fields(const FrameDev &f, unsigned slot, int blk) {
+    slot = checked(f.debug, kDbgSegSlot, slot, f.seg_slots);
     return f.seg_part + ((size_t)slot * f.blocks_per_tile + blk) * (kSegFields * 32) + (threadIdx.x & 31);
 }
 
@@ -564,7 +581,7 @@ struct FwdSmem {
 __device__ __forceinline__ void stage_async(FwdSmem &ws, int buf, const ViewData &vd, const Lookahead &la) {
     const int lane = threadIdx.x & 31;
     if (la.valid) {
-        const Record *r = vd.rec + (la.vi.x & 0x1FFFFFFFu);
+        const Record *r = vd.rec + vid_of(vd, la.vi.x);
         FwdSlot &d = ws.slot[buf][lane];
         cp_async16(&d.a, &r->r0);
         cp_async16(&d.g0, &r->r1);
@@ -781,7 +798,7 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                     // weights are exact only when the walk started from the
                     // true transmittance (not a split segment's T = 1)
                     if (FN && out.max_weight && true_weights)
-                        atomicMax(reinterpret_cast<int *>(out.max_weight) + (ws.meta[buf][k].x & 0x1FFFFFFFu),
+                        atomicMax(reinterpret_cast<int *>(out.max_weight) + vid_of(vd, ws.meta[buf][k].x),
                                   __float_as_int(w));
                 }
                 s.T *= P;
@@ -1322,9 +1339,15 @@ __device__ __forceinline__ int rec_run_end(int k_lo, int end, int base) {
 // colour channel that the clamp cut (bit clear) has no gradient.
 __device__ __forceinline__ void add_row(const float row[kRecStride], int vid, unsigned bits,
                                         const int32_t *__restrict__ corner_idx, float *__restrict__ d_grid,
-                                        float *__restrict__ acc_col, float *__restrict__ priority) {
+                                        float *__restrict__ acc_col, float *__restrict__ priority,
+                                        DebugBlock *dbg, int64_t n_pts) {
     const int4 *ci = reinterpret_cast<const int4 *>(corner_idx + 8 * (size_t)vid);
     const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
+    if (!(SVR_IN_BOUNDS(dbg, kDbgGradPoint, i0.x, n_pts) && SVR_IN_BOUNDS(dbg, kDbgGradPoint, i0.y, n_pts) &&
+          SVR_IN_BOUNDS(dbg, kDbgGradPoint, i0.z, n_pts) && SVR_IN_BOUNDS(dbg, kDbgGradPoint, i0.w, n_pts) &&
+          SVR_IN_BOUNDS(dbg, kDbgGradPoint, i1.x, n_pts) && SVR_IN_BOUNDS(dbg, kDbgGradPoint, i1.y, n_pts) &&
+          SVR_IN_BOUNDS(dbg, kDbgGradPoint, i1.z, n_pts) && SVR_IN_BOUNDS(dbg, kDbgGradPoint, i1.w, n_pts)))
+        return;
     atomicAdd(d_grid + i0.x, row[0]);
     atomicAdd(d_grid + i0.y, row[1]);
     atomicAdd(d_grid + i0.z, row[2]);
@@ -1342,9 +1365,8 @@ __device__ __forceinline__ void add_row(const float row[kRecStride], int vid, un
 // Lane j in [k_lo, k_hi) sums entry j's records and adds the sums to the
 // global gradients of its voxel.
 __device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, int k_lo, int k_hi, int off, int end,
-                                          int base, const int32_t *__restrict__ corner_idx,
-                                          float *__restrict__ d_grid, float *__restrict__ acc_col,
-                                          float *__restrict__ priority) {
+                                          int base, const FrameDev &f, float *__restrict__ d_grid,
+                                          float *__restrict__ acc_col, float *__restrict__ priority) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     if (lane >= k_lo && lane < k_hi && end > off) {
@@ -1352,8 +1374,8 @@ __device__ __forceinline__ void rec_flush(const RecSmem &rs, const Entry *st, in
 #pragma unroll
         for (int c = 0; c < kRecStride; ++c) row[c] = 0.f;
         for (int r = off - base; r < end - base; ++r) rec_add(row, rs.rec + r * (kRecStride / 4));
-        add_row(row, __float_as_int(st[lane].col.w), __float_as_uint(st[lane].pad.x), corner_idx, d_grid, acc_col,
-                priority);
+        add_row(row, __float_as_int(st[lane].col.w), __float_as_uint(st[lane].pad.x), f.corner_idx, d_grid, acc_col,
+                priority, f.debug, f.n_pts);
     }
     __syncwarp();
 }
@@ -1508,9 +1530,9 @@ __device__ __noinline__ void bwd_front_to_back(const FrameDev &f, const ItemList
                     PR = fmaf(w_own, c_own, PR);
                 }
                 Tf = Ta;
-                rec_write(rs, rec_slot(rs, k, rb), dgeo, dc, prio);
+                rec_write(rs, checked(f.debug, kDbgRecSlot, rec_slot(rs, k, rb), kRecCap), dgeo, dc, prio);
             }
-            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f.corner_idx, in.d_grid, dcol, XS ? in.priority : nullptr);
+            rec_flush(rs, st, k_lo, k_hi, off, end, rb, f, in.d_grid, dcol, XS ? in.priority : nullptr);
             k_lo = k_hi;
             if (k_lo >= 32) break;
         }
@@ -1661,9 +1683,9 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                         DS.R = fmaf(w, cdist, DS.R);
                     }
                     T_after = T_i;
-                    rec_write(rs, rec_slot(rs, k, base), dgeo, dc, prio);
+                    rec_write(rs, checked(f.debug, kDbgRecSlot, rec_slot(rs, k, base), kRecCap), dgeo, dc, prio);
                 }
-                rec_flush(rs, st, k_lo, k_hi, off, end, base, f.corner_idx, in.d_grid, dcol, prio_out);
+                rec_flush(rs, st, k_lo, k_hi, off, end, base, f, in.d_grid, dcol, prio_out);
                 k_lo = k_hi;
                 if (k_lo >= 32) break;
             }

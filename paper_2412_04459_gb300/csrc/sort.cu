@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f, int lo
     if (blockIdx.x >= f.status->n_queue) return;
     const uint2 q = f.order[blockIdx.x];
     const uint2 rg = f.ranges[q.x];
+    if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1)) return;
     const int L = (int)(rg.y - rg.x);
     int c0, n;
     if (L <= kSmallPairs) {
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_runs(FrameDev f) {
         if (ts.x < 2) return;  // unsplit lists follow all split ones: nothing left to merge
         if (q.y != 0) continue;
         const uint2 rg = f.ranges[q.x];
+        if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1)) continue;
         const int L = (int)(rg.y - rg.x);
         uint64_t *gk = f.keys[0] + rg.x;
         uint32_t *gv = f.vals[0] + rg.x;

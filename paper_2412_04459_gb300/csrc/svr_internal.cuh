@@ -73,6 +73,52 @@ struct Status {
     unsigned pad[4];
 };
 
+// Index checks of the SVR_DEBUG build (compiled out otherwise).  A failed
+// check counts itself in the device's DebugBlock, keeps the first failure's
+// site, index and bound, and the access is skipped (a read takes index 0 or a
+// neutral value); nothing traps.  svr_debug_report() reads and clears it.
+struct DebugBlock {
+    unsigned long long count;
+    unsigned site, pad;
+    long long index, bound;
+};
+
+enum DebugSite : unsigned {
+    kDbgCorner = 1,      // corner index of a voxel >= n_pts (preprocess gather)
+    kDbgTile = 2,        // tile id >= total_tiles (emission)
+    kDbgRange = 3,       // tile range end > pair capacity (sort, render)
+    kDbgVoxel = 4,       // voxel id of a list entry >= n_vox (render staging)
+    kDbgGradPoint = 5,   // corner index >= n_pts (render backward atomics)
+    kDbgRecSlot = 6,     // gradient record slot >= kRecCap (render backward)
+    kDbgSegSlot = 7,     // segment slot >= seg_slots (render)
+    kDbgBlockList = 8,   // block list longer than its tile list or segment (render)
+};
+
+#ifdef SVR_DEBUG
+__device__ __forceinline__ bool in_bounds(DebugBlock *d, unsigned site, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    if (d != nullptr && atomicAdd(&d->count, 1ull) == 0ull) {
+        d->site = site;
+        d->index = i;
+        d->bound = n;
+    }
+    return false;
+}
+#define SVR_IN_BOUNDS(dbg, site, i, n) ::svr::in_bounds((dbg), (site), (long long)(i), (long long)(n))
+#else
+#define SVR_IN_BOUNDS(dbg, site, i, n) true
+#endif
+
+// Index i if SVR_IN_BOUNDS(i < n) holds, else 0 (the access reads element 0).
+template <class I>
+__device__ __forceinline__ I checked(DebugBlock *dbg, unsigned site, I i, long long n) {
+    return SVR_IN_BOUNDS(dbg, site, i, n) ? i : I(0);
+}
+
+// The current device's DebugBlock (allocated on first use; nullptr in
+// builds without SVR_DEBUG).
+DebugBlock *debug_block();
+
 // Per-voxel record of one view (64 bytes):
 //   r0 = (lo - r_o).xyz, size      lo = centre - size / 2, the min corner
 //   r1 = corner densities 0..3     (raw, gathered from the grid)
@@ -187,6 +233,7 @@ struct FrameDev {
     const int32_t *corner_idx;
     const float *grid;
     const float *sh;
+    DebugBlock *debug;       // index-check report of the SVR_DEBUG build (else nullptr)
 };
 
 // View that owns global tile g.

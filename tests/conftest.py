@@ -32,3 +32,17 @@ def cached(key, fn):
     if key not in _CACHE:
         _CACHE[key] = fn()
     return _CACHE[key]
+
+
+@pytest.fixture(autouse=True)
+def _index_checks(request):
+    """With the SVR_DEBUG build loaded (SVR_DEBUG=1), every GPU test ends with
+    an empty device index-check report."""
+    yield
+    if request.node.get_closest_marker("gpu") is None:
+        return
+    from paper_2412_04459_gb300 import _native as N
+    if not N.DEBUG or N._LIB is None:
+        return
+    count, site, index, bound = N.debug_report()
+    assert count == 0, f"device index checks failed {count} times; first: site {site}, index {index}, bound {bound}"

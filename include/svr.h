@@ -457,17 +457,19 @@ SVR_API int svr_version(void);
 
 /* 1 if this library was built with SVR_DEBUG (libsvr_debug.so), else 0.
  * That build checks the data-dependent indices of the kernels' loads and
- * stores (corner indices < n_pts, voxel ids < n_vox, tile ids < the frame's
- * tiles, tile ranges within the pair capacity, gradient-record and segment
- * slots within their buffers); a failed check skips the access (a read takes
- * index 0), is counted, and the first failure's site, index and bound are
- * kept.  Nothing traps. */
+ * stores (tile ids < the frame's tiles, tile ranges within the pair capacity,
+ * voxel ids of list entries < n_vox, corner indices of the gradient atomics
+ * < n_pts, gradient-record and segment slots within their buffers, block
+ * lists within their tile list or segment); a failed check skips the access
+ * (a read takes index 0), is counted, and the first failure's site, index
+ * and bound are kept.  Nothing traps.  (Corner indices of the scene are
+ * validated in every build: svr_preprocess raises SVR_FLAG_INVALID_VOXEL.) */
 SVR_API int svr_debug_build(void);
 
 /* Waits for the current device, then writes its index-check report to
- * out[4] = {failed checks, site of the first (1 corner index, 2 tile id,
- * 3 tile range, 4 voxel id, 5 gradient corner index, 6 record slot,
- * 7 segment slot, 8 block list length), its index, its bound} and clears it.
+ * out[4] = {failed checks, site of the first (1 tile id, 2 tile range,
+ * 3 voxel id, 4 gradient corner index, 5 record slot, 6 segment slot,
+ * 7 block list length), its index, its bound} and clears it.
  * All zeros in builds without SVR_DEBUG.  out is a host array owned by the
  * caller; SVR_ERR_INVALID if it is NULL, SVR_ERR_CUDA on a CUDA error. */
 SVR_API int svr_debug_report(uint64_t *out);

@@ -84,14 +84,13 @@ struct DebugBlock {
 };
 
 enum DebugSite : unsigned {
-    kDbgCorner = 1,      // corner index of a voxel >= n_pts (preprocess gather)
-    kDbgTile = 2,        // tile id >= total_tiles (emission)
-    kDbgRange = 3,       // tile range end > pair capacity (sort, render)
-    kDbgVoxel = 4,       // voxel id of a list entry >= n_vox (render staging)
-    kDbgGradPoint = 5,   // corner index >= n_pts (render backward atomics)
-    kDbgRecSlot = 6,     // gradient record slot >= kRecCap (render backward)
-    kDbgSegSlot = 7,     // segment slot >= seg_slots (render)
-    kDbgBlockList = 8,   // block list longer than its tile list or segment (render)
+    kDbgTile = 1,        // tile id >= total_tiles (emission)
+    kDbgRange = 2,       // tile range end > pair capacity (sort, render)
+    kDbgVoxel = 3,       // voxel id of a list entry >= n_vox (block lists, render staging)
+    kDbgGradPoint = 4,   // corner index >= n_pts (render backward atomics)
+    kDbgRecSlot = 5,     // gradient record slot >= kRecCap (render backward)
+    kDbgSegSlot = 6,     // segment slot >= seg_slots (render)
+    kDbgBlockList = 7,   // block list longer than its tile list or segment (render)
 };
 
 #ifdef SVR_DEBUG

@@ -18,7 +18,7 @@ import pytest
 from tests.conftest import ROOT
 
 HEADER = os.path.join(ROOT, "include", "svr.h")
-SITE_RANGE = 3
+SITE_RANGE = 2
 
 
 def _exports(path):

@@ -10,7 +10,7 @@ import oracle
 import synth
 from oracle import antialias, training
 from tests.conftest import cached
-from tests.gpu_common import IMG_TOL, compare_grads, near_stop_allowance, oracle_grads, require_gpu
+from tests.gpu_common import IMG_TOL, SEG_REL, compare_grads, near_stop_allowance, oracle_grads, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -164,6 +164,7 @@ def test_train_step_against_oracle(h_ss):
     alphas = []
     og, osh = np.zeros(sc.n_pts), np.zeros((sc.n_vox, 48))
     mg, ms = [np.zeros(sc.n_pts), np.zeros(sc.n_pts)], [np.zeros((sc.n_vox, 48)), np.zeros((sc.n_vox, 48))]
+    pr_ref, pr_seg = np.zeros(sc.n_vox), np.zeros(sc.n_vox)
     outs = ts.frame.views(ts.out)
     for v, c in enumerate(cams):
         rc = ts.render_cams[v]
@@ -186,7 +187,8 @@ def test_train_step_against_oracle(h_ss):
         g_rgb = g_rgb_all[3 * a:3 * b].reshape(3, rc.height, rc.width)
         g_a = g_a_all[a:b].reshape(rc.height, rc.width)
         g_d = np.full((rc.height, rc.width), training.LAMBDA_DIST / P)
-        x, y, m = oracle_grads(sc, rc, g_rgb, np.zeros_like(g_a), g_a, K=2, g_dist=g_d)
+        x, y, m = oracle_grads(sc, rc, g_rgb, np.zeros_like(g_a), g_a, K=2, g_dist=g_d, priority=pr_ref)
+        pr_seg += m["priority_seg"]
         og += x
         osh += y
         mg[0] += m["grid"]
@@ -195,6 +197,13 @@ def test_train_step_against_oracle(h_ss):
         ms[1] += m["sh_seg"]
     compare_grads(ts.d_grid.cpu().numpy(), og, name="grid", mag=mg)
     compare_grads(ts.d_sh.cpu().numpy(), osh, name="sh", mag=ms)
+    # the subdivision priority gathered by the same backward (distortion term
+    # included), at the relative bar plus its grazing segments' rounding
+    p = ts.priority.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(p - pr_ref) / np.linalg.norm(pr_ref)
+    ratio = np.abs(p - pr_ref) / (1e-3 * (pr_ref + 1e-3 * pr_ref.max()) + SEG_REL * pr_seg)
+    print(f"PARITY priority train step: rel L2 {rel:.3e}, worst elementwise ratio {ratio.max():.3f}")
+    assert rel <= 1e-3 and (ratio <= 1.0).all(), (rel, ratio.max())
     # Adam on the GPU's own gradients against the FP64 update
     dg, ds = ts.d_grid.cpu().numpy().astype(np.float64), ts.d_sh.cpu().numpy().astype(np.float64)
     ts.optimize()

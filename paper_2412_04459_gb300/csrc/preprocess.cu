@@ -8,7 +8,9 @@
 //                 tile rectangle of the projected corners (Sec. 3.1.2), pair
 //                 count, conservative pixel box, view-dependent colour
 //                 (Eq. vox_color), gathered densities
-//                 and, per tile, the pairs it will hold (atomics)
+//                 and, per tile, the pairs it will hold (atomics);
+//                 k_preprocess_views does the same for a batch of views with
+//                 one thread per voxel, reading its densities and SH once
 //   k_scan_*      exclusive scan of the tiles' pair counts (block sums, then
 //                 each block scans its part after summing the earlier blocks;
 //                 kTileSub sub-buckets per tile, adjacent): each sub-bucket's
@@ -78,21 +80,13 @@ __device__ __forceinline__ void mark_invalid(Status *st, int64_t v) {
     atomicMin(reinterpret_cast<unsigned *>(&st->bad_voxel), (unsigned)v);
 }
 
-// grid.y = view
-__global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= f.n_vox) return;
-    const int view = blockIdx.y;
-    const DevCam &cam = f.views[view];
-    const int64_t iv = (int64_t)view * f.n_vox + v;
-    const float c0 = f.centre[3 * v + 0], c1 = f.centre[3 * v + 1], c2 = f.centre[3 * v + 2];
-    const int l = f.level[v];
-    const short4 empty = make_short4(0, -1, 0, -1);
-
-    // lattice index: centre = w_min + v_s (ijk + 1/2)
+// Lattice index of voxel v (centre = w_min + v_s (ijk + 1/2)) and the
+// validity of its level, centre and corner indices.
+__device__ __forceinline__ bool voxel_valid(const FrameDev &f, int64_t v, float c0, float c1, float c2, int l,
+                                            float &vs, int ijk[3], int4 &i0, int4 &i1) {
     bool ok = l >= 1 && l <= f.max_level;
-    const float vs = ldexpf(f.world_size, -l);
-    int ijk[3] = {0, 0, 0};
+    vs = ldexpf(f.world_size, -l);
+    ijk[0] = ijk[1] = ijk[2] = 0;
     if (ok) {
         const float cc[3] = {c0, c1, c2};
         const int n = 1 << l;
@@ -106,26 +100,19 @@ __global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
     }
     // corner indices must name grid points
     const int4 *ci = reinterpret_cast<const int4 *>(f.corner_idx + 8 * v);
-    const int4 i0 = __ldg(ci), i1 = __ldg(ci + 1);
-    {
-        const int64_t np = f.n_pts;
-        const int lo = min(min(min(i0.x, i0.y), min(i0.z, i0.w)), min(min(i1.x, i1.y), min(i1.z, i1.w)));
-        const int hi = max(max(max(i0.x, i0.y), max(i0.z, i0.w)), max(max(i1.x, i1.y), max(i1.z, i1.w)));
-        ok = ok && lo >= 0 && (int64_t)hi < np;
-    }
-    if (!ok) {
-        if (view == 0) mark_invalid(f.status, v);
-        f.count[iv] = 0;
-        f.rect[iv] = empty;
-        return;
-    }
-    if (view == 0) {
-        f.octpath[v] = ((spread3(ijk[0]) << 2) | (spread3(ijk[1]) << 1) | spread3(ijk[2]))
-                       << (3 * (kMaxLevel - l));
-    }
+    i0 = __ldg(ci);
+    i1 = __ldg(ci + 1);
+    const int64_t np = f.n_pts;
+    const int lo = min(min(min(i0.x, i0.y), min(i0.z, i0.w)), min(min(i1.x, i1.y), min(i1.z, i1.w)));
+    const int hi = max(max(max(i0.x, i0.y), max(i0.z, i0.w)), max(max(i1.x, i1.y), max(i1.z, i1.w)));
+    return ok && lo >= 0 && (int64_t)hi < np;
+}
 
-    // project the eight corners
-    const float h = 0.5f * vs;
+// Projection of voxel v in one view: tile rectangle, conservative pixel box
+// and pair count (the tiles' counts raised by atomics); writes rect and
+// count of (view, voxel) iv and returns the count.
+__device__ __forceinline__ uint32_t project_voxel(const FrameDev &f, const DevCam &cam, int64_t v, int64_t iv,
+                                                  float c0, float c1, float c2, float h, ushort4 &box) {
     float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
     int behind = 0;
 #pragma unroll
@@ -147,8 +134,8 @@ __global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
             vmax = fmaxf(vmax, w);
         }
     }
-    short4 rc = empty;
-    ushort4 box = make_ushort4(0, (unsigned short)(cam.W - 1), 0, (unsigned short)(cam.H - 1));
+    short4 rc = make_short4(0, -1, 0, -1);
+    box = make_ushort4(0, (unsigned short)(cam.W - 1), 0, (unsigned short)(cam.H - 1));
     if (behind == 8) {
         // culled
     } else if (behind > 0) {
@@ -182,33 +169,22 @@ __global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
     }
     f.rect[iv] = rc;
     f.count[iv] = cnt;
-    if (cnt == 0) return;
-    f.box[iv] = box;
+    return cnt;
+}
 
-    // record of this view: min corner relative to the ray origin, size,
-    // gathered raw densities, colour
-    Record r;
-    r.r0 = make_float4((c0 - h) - cam.ro[0], (c1 - h) - cam.ro[1], (c2 - h) - cam.ro[2], vs);
-    r.r1 = make_float4(__ldg(f.grid + i0.x), __ldg(f.grid + i0.y), __ldg(f.grid + i0.z), __ldg(f.grid + i0.w));
-    r.r2 = make_float4(__ldg(f.grid + i1.x), __ldg(f.grid + i1.y), __ldg(f.grid + i1.z), __ldg(f.grid + i1.w));
-
+// Colour of the voxel in one view (Eq. vox_color): degree-3 SH at the
+// direction from the view's ray origin to the centre, clamped at 0; bit c of
+// the w word set if channel c was > 0 before the clamp.
+__device__ __forceinline__ void view_basis(const DevCam &cam, float c0, float c1, float c2, float Y[16]) {
     float dx = c0 - cam.ro[0], dy = c1 - cam.ro[1], dz = c2 - cam.ro[2];
     const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
     dx *= inv;
     dy *= inv;
     dz *= inv;
-    float Y[16];
     sh_basis(dx, dy, dz, Y);
-    const float4 *shv = reinterpret_cast<const float4 *>(f.sh + 48 * v);
-    float sh[48];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) {
-        const float4 s4 = __ldg(shv + q);
-        sh[4 * q + 0] = s4.x;
-        sh[4 * q + 1] = s4.y;
-        sh[4 * q + 2] = s4.z;
-        sh[4 * q + 3] = s4.w;
-    }
+}
+
+__device__ __forceinline__ float4 voxel_colour(const float Y[16], const float sh[48]) {
     float col[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
@@ -217,9 +193,108 @@ __global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
         for (int n = 0; n < 16; ++n) acc = fmaf(Y[n], sh[3 * n + ch], acc);
         col[ch] = acc;
     }
-    unsigned bits = (col[0] > 0.f ? 1u : 0u) | (col[1] > 0.f ? 2u : 0u) | (col[2] > 0.f ? 4u : 0u);
-    r.r3 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), __uint_as_float(bits));
+    const unsigned bits = (col[0] > 0.f ? 1u : 0u) | (col[1] > 0.f ? 2u : 0u) | (col[2] > 0.f ? 4u : 0u);
+    return make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), __uint_as_float(bits));
+}
+
+__device__ __forceinline__ void load_sh(const FrameDev &f, int64_t v, float sh[48]) {
+    const float4 *shv = reinterpret_cast<const float4 *>(f.sh + 48 * v);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        const float4 s4 = __ldg(shv + q);
+        sh[4 * q + 0] = s4.x;
+        sh[4 * q + 1] = s4.y;
+        sh[4 * q + 2] = s4.z;
+        sh[4 * q + 3] = s4.w;
+    }
+}
+
+__device__ __forceinline__ void write_octpath(const FrameDev &f, int64_t v, int l, const int ijk[3]) {
+    f.octpath[v] = ((spread3(ijk[0]) << 2) | (spread3(ijk[1]) << 1) | spread3(ijk[2])) << (3 * (kMaxLevel - l));
+}
+
+// One view (grid.y = view): one thread per (view, voxel).
+__global__ void __launch_bounds__(128, 8) k_preprocess(FrameDev f) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= f.n_vox) return;
+    const int view = blockIdx.y;
+    const DevCam &cam = f.views[view];
+    const int64_t iv = (int64_t)view * f.n_vox + v;
+    const float c0 = f.centre[3 * v + 0], c1 = f.centre[3 * v + 1], c2 = f.centre[3 * v + 2];
+    const int l = f.level[v];
+    float vs;
+    int ijk[3];
+    int4 i0, i1;
+    if (!voxel_valid(f, v, c0, c1, c2, l, vs, ijk, i0, i1)) {
+        if (view == 0) mark_invalid(f.status, v);
+        f.count[iv] = 0;
+        f.rect[iv] = make_short4(0, -1, 0, -1);
+        return;
+    }
+    if (view == 0) write_octpath(f, v, l, ijk);
+    const float h = 0.5f * vs;
+    ushort4 box;
+    if (project_voxel(f, cam, v, iv, c0, c1, c2, h, box) == 0) return;
+    f.box[iv] = box;
+    // record of this view: min corner relative to the ray origin, size,
+    // gathered raw densities, colour
+    Record r;
+    r.r0 = make_float4((c0 - h) - cam.ro[0], (c1 - h) - cam.ro[1], (c2 - h) - cam.ro[2], vs);
+    r.r1 = make_float4(__ldg(f.grid + i0.x), __ldg(f.grid + i0.y), __ldg(f.grid + i0.z), __ldg(f.grid + i0.w));
+    r.r2 = make_float4(__ldg(f.grid + i1.x), __ldg(f.grid + i1.y), __ldg(f.grid + i1.z), __ldg(f.grid + i1.w));
+    float Y[16], sh[48];
+    view_basis(cam, c0, c1, c2, Y);
+    load_sh(f, v, sh);
+    r.r3 = voxel_colour(Y, sh);
     f.rec[iv] = r;
+}
+
+// Several views: one thread per voxel.  The voxel's validity, Morton code,
+// densities and SH coefficients are read once for all views (the SH only
+// while the views' colours are evaluated, which are written first, into the
+// records' colour words); then each view's projection, tile counts and the
+// rest of its record.
+__global__ void __launch_bounds__(128) k_preprocess_views(FrameDev f) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= f.n_vox) return;
+    const float c0 = f.centre[3 * v + 0], c1 = f.centre[3 * v + 1], c2 = f.centre[3 * v + 2];
+    const int l = f.level[v];
+    float vs;
+    int ijk[3];
+    int4 i0, i1;
+    if (!voxel_valid(f, v, c0, c1, c2, l, vs, ijk, i0, i1)) {
+        mark_invalid(f.status, v);
+        for (int view = 0; view < f.n_views; ++view) {
+            const int64_t iv = (int64_t)view * f.n_vox + v;
+            f.count[iv] = 0;
+            f.rect[iv] = make_short4(0, -1, 0, -1);
+        }
+        return;
+    }
+    write_octpath(f, v, l, ijk);
+    {
+        float sh[48];
+        load_sh(f, v, sh);
+        for (int view = 0; view < f.n_views; ++view) {
+            float Y[16];
+            view_basis(f.views[view], c0, c1, c2, Y);
+            f.rec[(int64_t)view * f.n_vox + v].r3 = voxel_colour(Y, sh);
+        }
+    }
+    const float4 g0 = make_float4(__ldg(f.grid + i0.x), __ldg(f.grid + i0.y), __ldg(f.grid + i0.z), __ldg(f.grid + i0.w));
+    const float4 g1 = make_float4(__ldg(f.grid + i1.x), __ldg(f.grid + i1.y), __ldg(f.grid + i1.z), __ldg(f.grid + i1.w));
+    const float h = 0.5f * vs;
+    for (int view = 0; view < f.n_views; ++view) {
+        const DevCam &cam = f.views[view];
+        const int64_t iv = (int64_t)view * f.n_vox + v;
+        ushort4 box;
+        if (project_voxel(f, cam, v, iv, c0, c1, c2, h, box) == 0) continue;
+        f.box[iv] = box;
+        Record *r = f.rec + iv;
+        r->r0 = make_float4((c0 - h) - cam.ro[0], (c1 - h) - cam.ro[1], (c2 - h) - cam.ro[2], vs);
+        r->r1 = g0;
+        r->r2 = g1;
+    }
 }
 
 // --------------------------------------------------------------------- scan
@@ -382,8 +457,11 @@ cudaError_t launch_tile_mask(const FrameDev &f, cudaStream_t s) {
 
 cudaError_t launch_preprocess(const FrameDev &f, cudaStream_t s) {
     if (f.n_vox == 0) return cudaSuccess;
-    const dim3 grid((unsigned)((f.n_vox + 127) / 128), (unsigned)f.n_views);
-    k_preprocess<<<grid, 128, 0, s>>>(f);
+    if (f.n_views == 1) {
+        k_preprocess<<<(unsigned)((f.n_vox + 127) / 128), 128, 0, s>>>(f);
+    } else {
+        k_preprocess_views<<<(unsigned)((f.n_vox + 127) / 128), 128, 0, s>>>(f);
+    }
     return cudaGetLastError();
 }
 

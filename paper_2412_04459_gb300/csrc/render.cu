@@ -55,7 +55,10 @@ namespace svr {
 
 constexpr int kWarps = 8;          // warps per CTA of the forward
 constexpr int kThreads = kWarps * 32;
-constexpr int kFwdMinBlocks = 3;   // resident CTAs per SM the forward's register budget is sized for
+#ifndef SVR_FWD_MIN_BLOCKS
+#define SVR_FWD_MIN_BLOCKS 3
+#endif
+constexpr int kFwdMinBlocks = SVR_FWD_MIN_BLOCKS;   // resident CTAs per SM the forward's register budget is sized for
 constexpr int kBwdWarps = 4;       // warps per CTA of the backward (more shared memory per warp)
 constexpr int kBwdThreads = kBwdWarps * 32;
 #ifndef SVR_BWD_MIN_BLOCKS
@@ -558,7 +561,10 @@ struct FwdSlot {
 
 // Hits of one batch handed to the lanes at a time by the hit-parallel
 // compositing (phase B of the plain and counting forwards).
-constexpr int kHitCap = 128;
+#ifndef SVR_FWD_HIT_CAP
+#define SVR_FWD_HIT_CAP 128
+#endif
+constexpr int kHitCap = SVR_FWD_HIT_CAP;
 // The hit-parallel pass is taken when kHpNum * (busiest pixel's hits) >
 // kHpDen * (rounds of 32 hits); measured on the 1M-voxel frame over 1/1,
 // 2/3, 1/2, 1/3 and never: 1/2 is fastest (0.205 vs 0.215 ms never, 0.244

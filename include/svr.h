@@ -73,7 +73,8 @@ extern "C" {
 #define SVR_FLAG_INVALID_VOXEL 1u
 #define SVR_FLAG_CAPACITY 2u
 #define SVR_FLAG_NO_FORWARD 4u /* svr_render_bwd ran before any svr_render_fwd of the sort (or, with
-                                  d_normal, before one that rendered normals) */
+                                  d_normal or d_distortion, before one that rendered normals or the
+                                  distortion loss: then the split tiles are skipped) */
 
 typedef struct svr_camera {
     float fx, fy, cx, cy;
@@ -247,10 +248,12 @@ SVR_API int svr_render_fwd(const svr_frame *frame, float *rgb, float *depth, flo
  * caller zeroes it) and writes dL/dsh into d_sh [N][48] (zero for voxels not
  * in view).  Requires svr_render_fwd's outputs for the same frame, and that
  * the frame's last svr_render_fwd (or svr_render_stats) ran after its last
- * svr_bin_sort on the same stream: tile lists longer than 1024 entries are
- * composited in segments, and the forward leaves each segment's transmittance
- * and the colour and depth sums behind it in the workspace, where the
- * backward starts from them.  Without such a forward those tiles are skipped
+ * svr_bin_sort on the same stream: the forward leaves in the workspace each
+ * pixel's hit masks over the batches of list entries it walked (the backward
+ * takes its hits from them instead of testing the rays again) and, for tile
+ * lists longer than 1024 entries, which are composited in segments, each
+ * segment's transmittance and the colour and depth sums behind it, where the
+ * backward starts from them.  Without such a forward every tile is skipped
  * and SVR_FLAG_NO_FORWARD is raised.
  */
 SVR_API int svr_render_bwd(const svr_frame *frame, const float *d_rgb, const float *d_depth,

@@ -29,7 +29,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 enum Slot {
     kStatus, kTileMask, kOctpath, kRect, kCount, kTileCount, kRecord, kScanBlocks,
     kKeys0, kKeys1, kVals0, kVals1, kRanges, kDcol, kBox, kTileOrder, kBlockList, kBlockLen,
-    kSegment, kTotal, kNumSlots
+    kHitMask, kSegment, kTotal, kNumSlots
 };
 
 struct Layout {
@@ -80,6 +80,7 @@ Layout make_layout(int64_t n_vox, int n_views, int64_t cap, int64_t ntiles, int 
     const size_t B = (size_t)tile * tile / 32;
     take(kBlockList, 8 * B * C);
     take(kBlockLen, 4 * B * (size_t)ntiles);
+    take(kHitMask, 4 * B * (C + 32 * (size_t)ntiles));   // the block lists' positions + 32 per (tile, block)
     take(kSegment, seg_bytes(ntiles, slots, B).total);
     L.off[kTotal] = o;
     return L;
@@ -213,6 +214,7 @@ svr::FrameDev frame_dev(const svr_frame *f) {
     d.order = (uint2 *)(ws + o[kTileOrder]);
     d.blist = (uint2 *)(ws + o[kBlockList]);
     d.blen = (uint32_t *)(ws + o[kBlockLen]);
+    d.hmask = (uint32_t *)(ws + o[kHitMask]);
     d.blocks_per_tile = f->params.tile * f->params.tile / 32;
     d.seg_slots = svr::seg_slot_capacity(f->pair_capacity);
     const SegBytes sb = seg_bytes(f->total_tiles, (size_t)d.seg_slots, (size_t)d.blocks_per_tile);

@@ -455,6 +455,14 @@ __device__ __forceinline__ void seg_range(const ItemList &L, int B, int sg, int 
     if (!SVR_IN_BOUNDS(L.dbg, kDbgBlockList, p1 - p0, kSegLen + 1)) p1 = p0;
 }
 
+// The hit masks of an item's block list (see FrameDev::hmask): word p of the
+// result belongs to block-list position p.  Only an item's first walk
+// writes them (the merge's second walk of a segment and the max-weight pass
+// leave them), so they hold every pixel's hits up to its stopping voxel.
+__device__ __forceinline__ uint32_t *hit_masks(const FrameDev &f, const ItemList &L, const Item &it) {
+    return f.hmask + (L.list - f.blist) + 32 * ((size_t)it.g * f.blocks_per_tile + it.blk);
+}
+
 // Segment sums of (segment slot, block): kSegFields rows of 32 pixels.
 __device__ __forceinline__ float *seg_fields(const FrameDev &f, unsigned slot, int blk) {
     slot = checked(f.debug, kDbgSegSlot, slot, f.seg_slots);
@@ -727,7 +735,7 @@ __device__ __forceinline__ void fwd_hits_parallel(const FwdSlot *st, const uint2
 template <int K, int MODE>
 __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0, int p1, const ViewData &vd,
                                          const PixelRay &p, const WarpBlock &wb, FwdSmem &ws, float t_stop,
-                                         FwdState &s, const FwdOut &out, bool true_weights) {
+                                         FwdState &s, const FwdOut &out, bool true_weights, uint32_t *hm) {
     constexpr bool STATS = MODE == kModeStats, FN = MODE == kModeExtra, FD = FN || MODE == kModeDist;
     constexpr bool EXTRA = FN || FD;
     const int lane = threadIdx.x & 31;
@@ -760,6 +768,8 @@ __device__ __forceinline__ void fwd_walk(const uint2 *__restrict__ list, int p0,
                 if (slab_slot(st[k], p, a, b)) hits |= 1u << k;
             }
         }
+        // this pixel's hits in the batch, for the backward
+        if (hm != nullptr) hm[base + lane] = hits;
         if constexpr (!EXTRA) {
             // hit-parallel when the hits fall unevenly enough on the pixels:
             // the per-pixel rounds cost the busiest pixel's hit count, the
@@ -880,7 +890,7 @@ __device__ __forceinline__ void fwd_merge(const FrameDev &f, const ItemList &L, 
             FwdState r = {Tb, 0.f, 0.f, 0.f, 0.f, -1, !need, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             int p0, p1;
             seg_range(L, B, sg, p0, p1);
-            fwd_walk<K, MODE>(L.list, p0, p1, vd, p, wb, ws, f.t_stop, r, out, true);
+            fwd_walk<K, MODE>(L.list, p0, p1, vd, p, wb, ws, f.t_stop, r, out, true, nullptr);
             if (need) {
                 c0 = r.C0;
                 c1 = r.C1;
@@ -1012,7 +1022,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
     const int lane = threadIdx.x & 31;
     FwdState s = {1.f, 0.f, 0.f, 0.f, 0.f, -1, !p.inside, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (L.ts.x <= 1) {
-        fwd_walk<K, MODE>(L.list, 0, L.n_list, iv.vd, p, wb, ws, f.t_stop, s, out, true);
+        fwd_walk<K, MODE>(L.list, 0, L.n_list, iv.vd, p, wb, ws, f.t_stop, s, out, true, hit_masks(f, L, it));
         fwd_write<MODE>(f, cam, p, s, s.last >= 0 ? s.last : L.end - 1, out);
         return;
     }
@@ -1020,7 +1030,7 @@ __device__ __forceinline__ void fwd_item(const FrameDev &f, const Item &it, FwdS
     const int B = f.blocks_per_tile;
     int p0, p1;
     seg_range(L, B, it.seg, p0, p1);
-    fwd_walk<K, MODE>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s, out, it.seg == 0);
+    fwd_walk<K, MODE>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s, out, it.seg == 0, hit_masks(f, L, it));
     float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
     q[0] = s.C0;
     q[32] = s.C1;
@@ -1115,7 +1125,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_maxw(FrameDe
                       0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int p0, p1;
         seg_range(L, f.blocks_per_tile, it.seg, p0, p1);
-        fwd_walk<K, kModeExtra>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s, out, true);
+        fwd_walk<K, kModeExtra>(L.list, p0, p1, iv.vd, p, wb, ws, f.t_stop, s, out, true, nullptr);
         __syncwarp();
     }
 }
@@ -1597,15 +1607,17 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     float SC0 = g.Tfin * f.bg[0], SC1 = g.Tfin * f.bg[1], SC2 = g.Tfin * f.bg[2], SD = 0.f;
     NrmSums SN = {0.f, 0.f, 0.f};
     DistSums DS = {0.f, 0.f, 0.f};
-    if (L.ts.x > 1) {
-        // a split tile starts from the segment sums of this sort's forward,
-        // which must include the normal image and the distortion sums when
-        // their gradients are asked for
+    // every tile takes the hit masks of this sort's forward; a split tile
+    // also starts from its segment sums, which must include the normal image
+    // and the distortion sums when their gradients are asked for
+    {
         const unsigned done = f.status->fwd_done;
-        if (done == 0 || (XN && in.d_normal && !(done & 2u)) || (XD && in.d_dist && !(done & 4u))) {
+        if (done == 0 || (L.ts.x > 1 && ((XN && in.d_normal && !(done & 2u)) || (XD && in.d_dist && !(done & 4u))))) {
             if (lane == 0) atomicOr(&f.status->flags, SVR_FLAG_NO_FORWARD);
             return;
         }
+    }
+    if (L.ts.x > 1) {
         seg_range(L, f.blocks_per_tile, it.seg, p0, p1);
         idx0 = beg + it.seg * kSegLen;
         const float *q = seg_fields(f, L.ts.y + it.seg, it.blk);
@@ -1631,30 +1643,46 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     const bool active = has && !fallback;
     float *prio_out = XS ? in.priority : nullptr;
 
-    // ---- back to front
+    // ---- back to front, over the forward's batches [p0 + 32 k, p0 + 32 k + 32):
+    // each pixel's hits in a batch are the forward's hit mask (which tested
+    // every candidate of the batch before the pixel stopped) restricted to
+    // the entries up to its last voxel
     {
         const int top_all = lower_pos(L.list, p0, p1, __reduce_max_sync(0xffffffffu, active ? last + 1 : idx0));
+        const uint32_t *hm = hit_masks(f, L, it);
+        int base = p0 + (((top_all - 1 - p0) >> 5) << 5);   // the batch of position top_all - 1
         Lookahead la;
-        fetch_vi(la, L.list, top_all - 1 - lane, top_all - 1 - lane >= p0);
-        fetch_box(la, vd);
+        unsigned m_next = 0u;
+        la.valid = false;
+        if (top_all > p0) {
+            fetch_vi(la, L.list, base + kBatch - 1 - lane, base + kBatch - 1 - lane < top_all);
+            m_next = __ldg(hm + base + lane);
+        }
         prefetch_record(la, vd);
-        for (int top = top_all; top > p0; top -= kBatch) {
+        for (; top_all > p0 && base >= p0; base -= kBatch) {
             const Lookahead cur = la;
-            const int npos = top - 1 - kBatch - lane;
-            fetch_vi(la, L.list, npos, npos >= p0);
-            const unsigned cand = warp_transpose(entry_pixels(cur.valid, cur.vi.x, cur.box, wb));
-            stage_ahead(st, vd, cur);              // lane j: list position top - 1 - j
-            fetch_box(la, vd);
+            const unsigned m = m_next;
+            if (base - kBatch >= p0) {
+                fetch_vi(la, L.list, base - 1 - lane, true);
+                m_next = __ldg(hm + base - kBatch + lane);
+            } else {
+                la.valid = false;
+            }
+            stage_ahead(st, vd, cur);              // lane j: list position base + 31 - j
             prefetch_record(la, vd);
-            unsigned hits = 0;
-            if (active) {
-                for (unsigned c = cand; c; c &= c - 1u) {
-                    const int k = __ffs(c) - 1;
-                    const Entry &e = st[k];
-                    float a, b;
-                    if (__float_as_int(e.c.w) <= last && slab(e, p, a, b)) hits |= 1u << k;
+            // staged indices fall with j: the first j whose index is <= last
+            const int idx_j = cur.valid ? (int)cur.vi.y : INT_MAX;
+            int lo = 0, hi = kBatch;
+#pragma unroll
+            for (int step = 0; step < 6; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const int v = __shfl_sync(0xffffffffu, idx_j, mid & 31);
+                if (lo < hi) {
+                    if (v > last) lo = mid + 1;
+                    else hi = mid;
                 }
             }
+            const unsigned hits = active && lo < kBatch ? __brev(m) & (0xffffffffu << lo) : 0u;
             int off, end;
             const int total = rec_layout(rs, hits, off, end);
             // runs of entries whose records fit; each lane takes its hits in

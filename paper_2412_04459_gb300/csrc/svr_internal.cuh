@@ -216,6 +216,10 @@ struct FrameDev {
     uint2 *blist;            // per (tile, 8x4 block) lists of (value, sorted index): block b of a tile
                              // whose list is [beg, end) owns [B beg + b (end - beg), ...)
     uint32_t *blen;          // [total_tiles * B] entries in each block list
+    uint32_t *hmask;         // the forward's hit masks: block b of tile g (list [beg, end)) owns the
+                             // words from B beg + b (end - beg) + 32 (g B + b); word p of it is, for
+                             // p in batch [32 k, 32 k + 32) of the block's walk, the mask of the
+                             // batch's entries (bit i: position 32 k + i) that pixel p mod 32 hit
     int blocks_per_tile;     // B = tile * tile / 32
     float *dcol;             // [V * N][3] colour gradient accumulator
     int64_t n_vox;

@@ -121,8 +121,9 @@ def test_repeated_forward_and_backward_are_stable():
 
 
 def test_backward_without_forward_is_flagged():
-    """A backward after a new sort but before its forward cannot know the
-    split tiles' segment sums: it skips them and raises the flag."""
+    """A backward after a new sort but before its forward has neither the
+    forward's hit masks nor the split tiles' segment sums: it skips every tile
+    and raises the flag; after the forward it runs."""
     import torch
     from paper_2412_04459_gb300 import _native as N
     sc = cached("dense5", lambda: synth.dense_scene(5, seed=0))
@@ -131,12 +132,14 @@ def test_backward_without_forward_is_flagged():
     fr.preprocess()
     fr.bin_sort()
     g = [torch.as_tensor(a, device="cuda") for a in synth.upstream_grads(3, cam.height, cam.width)]
-    fr.backward(*g, out)
+    d0, _ = fr.backward(*g, out)
     flags, _ = fr.status()
     assert flags & N.SVR_FLAG_NO_FORWARD
+    assert float(d0.abs().max()) == 0.0
     fr.forward(out)
-    fr.backward(*g, out)
+    d1, _ = fr.backward(*g, out)
     torch.cuda.synchronize()
+    assert float(d1.abs().max()) > 0.0
 
 
 def test_very_long_lists_sort_and_render():

@@ -1668,9 +1668,8 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
             } else {
                 la.valid = false;
             }
-            stage_ahead(st, vd, cur);              // lane j: list position base + 31 - j
-            prefetch_record(la, vd);
-            // staged indices fall with j: the first j whose index is <= last
+            // staged indices fall with j (lane j: list position base + 31 - j):
+            // the first j whose index is <= last
             const int idx_j = cur.valid ? (int)cur.vi.y : INT_MAX;
             int lo = 0, hi = kBatch;
 #pragma unroll
@@ -1683,6 +1682,13 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
                 }
             }
             const unsigned hits = active && lo < kBatch ? __brev(m) & (0xffffffffu << lo) : 0u;
+            // only the entries some pixel hits are staged (every lane takes
+            // part in the reduction)
+            const unsigned needed = __reduce_or_sync(0xffffffffu, hits);
+            if (cur.valid && ((needed >> lane) & 1u))
+                stage_entry(st[lane], (cur.vi.x & 0xE0000000u) | vid_of(vd, cur.vi.x), (int)cur.vi.y, vd.rec);
+            __syncwarp();
+            prefetch_record(la, vd);
             int off, end;
             const int total = rec_layout(rs, hits, off, end);
             // runs of entries whose records fit; each lane takes its hits in

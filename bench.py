@@ -324,7 +324,9 @@ def run_native(args, rank, world, local_rank):
     alu_peak = sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12          # T FP32 lane-ops/s
     ops = n_cand * OPS_CAND + n_hit * OPS_HIT[K]
     achieved = ops / (per_call["render_fwd"] * 1e-3) / 1e12
-    ops_bwd = n_cand * OPS_CAND + n_hit * OPS_HIT_BWD[K]
+    # the backward tests no candidates (it reads the forward's hit masks):
+    # per hit, the segment's slab test, the forward recompute and the gradient
+    ops_bwd = n_hit * (OPS_CAND + OPS_HIT_BWD[K])
     achieved_bwd = ops_bwd / (per_call["render_bwd"] * 1e-3) / 1e12
     hbm = (peaks or {}).get("hbm_gbs", 6800.0)
     frame_bytes = frame_algorithmic_bytes(scene, P, H, W)
@@ -341,8 +343,7 @@ def run_native(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "k_render_bwd", "achieved": achieved_bwd, "peak": alu_peak,
                      "unit": "T FP32 lane-ops/s", "frac": achieved_bwd / alu_peak, "traffic": traffic,
                      "traffic_from": traffic_from,
-                     "work": {"candidates": n_cand, "hits": n_hit, "ops_per_candidate": OPS_CAND,
-                              "ops_per_hit": OPS_HIT_BWD[K]},
+                     "work": {"hits": n_hit, "ops_per_hit": OPS_CAND + OPS_HIT_BWD[K]},
                      "timed": "svr_render_bwd call: k_render_bwd + k_voxel_bwd + 2 memsets",
                      "peak_from": f"{sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
         "roofline_fwd": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": alu_peak,

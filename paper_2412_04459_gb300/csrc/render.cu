@@ -212,8 +212,9 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 //
 // A warp renders one 8x4 block and needs only the entries of its tile's list
 // whose pixel box meets the block and whose sign pattern a pixel of the block
-// has.  k_block_lists extracts them once per frame, one CTA per entry of the
-// render work order (a tile, or one kSegLen-entry segment of a split tile):
+// has.  k_block_lists extracts them once per frame, one CTA at a time per
+// entry of the render work order (a tile, or one kSegLen-entry segment of a
+// split tile):
 // thread t loads entries t, t + kListThreads, ... of the segment (value and box) and
 // writes each one's mask of such blocks to shared memory (the box's block
 // rectangle AND the blocks holding a pixel with its sign bits, from the
@@ -224,18 +225,17 @@ __device__ __forceinline__ bool slab(const Entry &e, const PixelRay &p, float &a
 // no allocation scan; segment s of a split tile writes from offset s kSegLen
 // of that region (it keeps at most kSegLen entries) and records its count per
 // block.  The CTA of segment 0 also clears the tile's merge counters for the
-// next forward.
+// next forward.  The CTAs form a persistent grid that strides over the
+// entries.
 
 constexpr int kListThreads = 128;
 constexpr int kListWarps = kListThreads / 32;
 constexpr int kMaxBlocksPerWarp = 32 / kListWarps;  // tile 32: 32 blocks over the warps
 constexpr int kListChunk = kSegLen;
 
-__global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
-    __shared__ uint32_t sval[kListChunk];
-    __shared__ uint32_t smsk[kListChunk];
-    if (blockIdx.x >= f.status->n_queue) return;
-    const uint2 gs = f.order[blockIdx.x];
+__device__ __forceinline__ void block_lists_entry(const FrameDev &f, const uint32_t *__restrict__ vals, unsigned e,
+                                                  uint32_t *sval, uint32_t *smsk) {
+    const uint2 gs = f.order[e];
     const int g = (int)gs.x, sg = (int)gs.y;
     const int view = view_of_tile(f, g);
     const DevCam &cam = f.views[view];
@@ -318,6 +318,18 @@ __global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const 
 #pragma unroll
         for (int k = 0; k < kMaxBlocksPerWarp; ++k)
             if (warp + kListWarps * k < B) len[warp + kListWarps * k] = cnt[k];
+    }
+}
+
+// A persistent grid of CTAs takes the work-order entries in turn (the count
+// is the device's).
+__global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
+    __shared__ uint32_t sval[kListChunk];
+    __shared__ uint32_t smsk[kListChunk];
+    const unsigned nq = f.status->n_queue;
+    for (unsigned e = blockIdx.x; e < nq; e += gridDim.x) {
+        block_lists_entry(f, vals, e, sval, smsk);
+        __syncthreads();  // shared memory is reused by the next entry
     }
 }
 
@@ -1806,14 +1818,6 @@ __global__ void __launch_bounds__(kVoxBwdThreads) k_voxel_bwd(FrameDev f, float 
 
 // ---------------------------------------------------------------- launchers
 
-cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s) {
-    if (f.total_tiles == 0) return cudaSuccess;
-    // one CTA per entry of the work order; CTAs past the device-side count exit
-    const int64_t grid = (int64_t)f.total_tiles + f.seg_slots;
-    k_block_lists<<<(unsigned)grid, kListThreads, 0, s>>>(f, f.vals[sorted_alt]);
-    return cudaGetLastError();
-}
-
 // Persistent grid: as many CTAs as fit on the device at once.
 template <class Kern>
 static unsigned persistent_grid(Kern kernel, int threads) {
@@ -1824,6 +1828,17 @@ static unsigned persistent_grid(Kern kernel, int threads) {
     if (sms <= 0) sms = 1;
     if (per_sm <= 0) per_sm = 1;
     return (unsigned)(sms * per_sm);
+}
+
+cudaError_t launch_block_lists(const FrameDev &f, int sorted_alt, cudaStream_t s) {
+    if (f.total_tiles == 0) return cudaSuccess;
+    // at most one CTA per possible entry of the work order, at most as many as
+    // are resident at once; they stride over the device-side count
+    const int64_t grid = (int64_t)f.total_tiles + f.seg_slots;
+    static DeviceCache cache;
+    const unsigned resident = device_cached(cache, [] { return persistent_grid(k_block_lists, kListThreads); });
+    k_block_lists<<<(unsigned)tmin<int64_t>(grid, resident), kListThreads, 0, s>>>(f, f.vals[sorted_alt]);
+    return cudaGetLastError();
 }
 
 // Grid size from a lower bound on the work items (every tile has at least

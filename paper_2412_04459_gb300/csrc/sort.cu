@@ -8,9 +8,11 @@
 //   k_tile_order   the tiles' ranges from the scanned counts, and the render
 //                  work order: one entry per tile, or per 1024-entry segment
 //                  of a longer list, longest first
-//   k_sort_small   one CTA per list of at most 1024 pairs and per 1024-pair
-//                  chunk of a longer list: stable LSD radix passes of 8-bit
-//                  digits in shared memory
+//   k_sort_small   every list of at most 1024 pairs and every 1024-pair
+//                  chunk of a longer list, one at a time per CTA of a
+//                  persistent grid: lists of at most 256 pairs by rank, the
+//                  others by stable LSD radix passes of 8-bit digits, in
+//                  shared memory
 //   k_merge_runs   lists longer than 1024 pairs: their sorted chunks merged in
 //                  rounds of pairwise stable merges (merge-path partitioning
 //                  over the CTA's threads), in shared memory up to 8192 pairs
@@ -25,12 +27,17 @@ namespace svr {
 // their partial sums; a shorter list is one segment without a slot.  Entries
 // are grouped by floor(log2(list length)), longest lists first, so the
 // heaviest work starts early and short lists fill the tail (one CTA; the
-// order within a group is arbitrary and results do not depend on it).  Also
-// resets the frame's forward-done mark (the segment sums belong to the last
-// sort) and the long-list sort's work counter.
+// order within a group is arbitrary and results do not depend on it).  The
+// first segments of the split lists come before all other entries, so the
+// long-list merge takes its tiles from the head of the order (status n_long
+// of them).  Also resets the frame's forward-done mark (the segment sums
+// belong to the last sort) and the long-list sort's work counter.
 // Group of a list in the work order: floor(log2(length)) + 1, one more for a
 // split list, so that every split list (longer than kSegLen) precedes every
-// unsplit one.
+// unsplit one; a split list's first segment goes to group kFirstSeg + its
+// group, ahead of all others.
+constexpr int kOrderGroups = 34;
+constexpr int kFirstSeg = kOrderGroups;
 __device__ __forceinline__ int order_bucket(unsigned len, unsigned nseg) {
     return len ? 32 - __clz(len) + (nseg > 1 ? 1 : 0) : 0;
 }
@@ -38,13 +45,13 @@ __device__ __forceinline__ int order_bucket(unsigned len, unsigned nseg) {
 constexpr int kOrderUnroll = 8;  // tiles per thread whose loads are issued together
 
 __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
-    __shared__ unsigned cnt[34];
-    __shared__ unsigned start[34];
+    __shared__ unsigned cnt[2 * kOrderGroups];
+    __shared__ unsigned start[2 * kOrderGroups];
     __shared__ unsigned slot_next;
     const int t = threadIdx.x, nt = blockDim.x;
     const int ntiles = f.total_tiles;
     const bool over = (f.status->flags & SVR_FLAG_CAPACITY) != 0;
-    if (t < 34) cnt[t] = 0;
+    if (t < 2 * kOrderGroups) cnt[t] = 0;
     if (t == 0) slot_next = 0;
     __syncthreads();
     // ranges: a tile starts at its first sub-bucket; empty tiles, and all
@@ -71,16 +78,23 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
                 base = atomicAdd(&slot_next, nseg);
                 if ((int64_t)base + nseg > f.seg_slots) nseg = 1, base = 0;  // only past the pair capacity
             }
-            atomicAdd(&cnt[order_bucket(len, nseg)], nseg);
+            const int bk = order_bucket(len, nseg);
+            if (nseg > 1) {
+                atomicAdd(&cnt[kFirstSeg + bk], 1u);
+                atomicAdd(&cnt[bk], nseg - 1);
+            } else {
+                atomicAdd(&cnt[bk], 1u);
+            }
             f.tile_seg[i] = make_uint2(nseg, base);
         }
     }
     __syncthreads();
     if (t == 0) {
         unsigned acc = 0;
-        for (int b = 33; b >= 0; --b) {
+        for (int b = 2 * kOrderGroups - 1; b >= 0; --b) {
             start[b] = acc;
             acc += cnt[b];
+            if (b == kFirstSeg) f.status->n_long = acc;
         }
         f.status->n_queue = acc;
         f.status->slots_used = slot_next;
@@ -101,8 +115,14 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
         for (int u = 0; u < kOrderUnroll; ++u) {
             const int i = i0 + u * nt;
             if (i >= ntiles) break;
-            const unsigned pos = atomicAdd(&start[order_bucket(r[u].y - r[u].x, ts[u].x)], ts[u].x);
-            for (unsigned sg = 0; sg < ts[u].x; ++sg) f.order[pos + sg] = make_uint2((unsigned)i, sg);
+            const int bk = order_bucket(r[u].y - r[u].x, ts[u].x);
+            if (ts[u].x > 1) {
+                f.order[atomicAdd(&start[kFirstSeg + bk], 1u)] = make_uint2((unsigned)i, 0u);
+                const unsigned pos = atomicAdd(&start[bk], ts[u].x - 1) - 1;
+                for (unsigned sg = 1; sg < ts[u].x; ++sg) f.order[pos + sg] = make_uint2((unsigned)i, sg);
+            } else {
+                f.order[atomicAdd(&start[bk], 1u)] = make_uint2((unsigned)i, 0u);
+            }
         }
     }
 }
@@ -245,35 +265,82 @@ __device__ void tile_radix_sort(uint64_t *__restrict__ gk, uint32_t *__restrict_
     }
 }
 
-// A whole list of at most kSmallPairs pairs, or one kSegLen-pair chunk of a
-// longer list (merged afterwards); one CTA per work-order entry.
+// Sorts one tile's n <= kSmallThreads pairs (gk, gv) by rank: thread t
+// holds pair t and its sort word (Morton bits << kIdxBits | t, as the radix
+// passes build it), and its output position is the number of words below its
+// own.  The words are distinct (each holds its index), so this is the order
+// the stable radix passes give, without their fixed cost per pass; most tile
+// lists are this short.  Not for max level 16, whose words need the value.
+__device__ __forceinline__ void rank_sort(uint64_t *__restrict__ gk, uint32_t *__restrict__ gv, int n, int lo_bit,
+                                          uint64_t mask, uint64_t *w) {
+    const int t = threadIdx.x;
+    uint64_t k = 0ull, wt = 0ull;
+    uint32_t v = 0u;
+    if (t < n) {
+        k = gk[t];
+        v = gv[t];
+        wt = (((k >> lo_bit) & mask) << kIdxBits) | (uint64_t)t;
+        w[t] = wt;
+    }
+    __syncthreads();
+    if (t < n) {
+        int r = 0;
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) r += w[j] < wt ? 1 : 0;
+        gk[r] = k;
+        gv[r] = v;
+    }
+}
+
+constexpr int kRankPairs = kSmallThreads;  // lists up to this length: sorted by rank
+
+// Every list of at most kSmallPairs pairs, and every kSegLen-pair chunk of a
+// longer list (merged afterwards): a persistent grid of CTAs takes the
+// work-order entries in turn (the count is the device's, so no CTA is
+// launched for the entries the capacity allows but the frame does not have).
 __global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f, int lo_bit, int nbits, bool ties) {
     __shared__ uint64_t w[2][kSmallPairs];
     __shared__ uint64_t ok[kSmallPairs];
     __shared__ uint32_t ov[kSmallPairs];
     __shared__ RadixTables<kSmallThreads> tb;
     __shared__ uint16_t inv[kSmallPairs];
-    if (blockIdx.x >= f.status->n_queue) return;
-    const uint2 q = f.order[blockIdx.x];
-    const uint2 rg = f.ranges[q.x];
-    if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1)) return;
-    const int L = (int)(rg.y - rg.x);
-    int c0, n;
-    if (L <= kSmallPairs) {
-        c0 = (int)rg.x;
-        n = L;
-    } else if (f.tile_seg[q.x].x > 1) {
-        c0 = (int)rg.x + (int)q.y * kSegLen;
-        n = min(kSegLen, (int)rg.y - c0);
-    } else {
-        return;
+    const unsigned nq = f.status->n_queue, G = gridDim.x;
+    const uint64_t mask = nbits >= 64 ? ~0ull : (1ull << nbits) - 1ull;
+    // the next entry's range and the one after's order record are fetched
+    // one item ahead, so that only the first item waits for them
+    const uint2 zero = make_uint2(0u, 0u);
+    uint2 q_next = blockIdx.x < nq ? f.order[blockIdx.x] : zero;
+    uint2 rg_next = blockIdx.x < nq ? f.ranges[q_next.x] : zero;
+    uint2 q_after = blockIdx.x + G < nq ? f.order[blockIdx.x + G] : zero;
+    for (unsigned e = blockIdx.x; e < nq; e += G) {
+        const uint2 q = q_next, rg = rg_next;
+        q_next = q_after;
+        rg_next = e + G < nq ? f.ranges[q_next.x] : zero;
+        q_after = e + 2 * G < nq ? f.order[e + 2 * G] : zero;
+        if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1)) continue;
+        const int L = (int)(rg.y - rg.x);
+        int c0, n;
+        if (L <= kSmallPairs) {
+            c0 = (int)rg.x;
+            n = L;
+        } else if (f.tile_seg[q.x].x > 1) {
+            c0 = (int)rg.x + (int)q.y * kSegLen;
+            n = min(kSegLen, (int)rg.y - c0);
+        } else {
+            continue;
+        }
+        if (n < 2) continue;
+        uint64_t *gk = f.keys[0] + c0;
+        uint32_t *gv = f.vals[0] + c0;
+        if (!ties && n <= kRankPairs) {
+            rank_sort(gk, gv, n, lo_bit, mask, w[0]);
+        } else {
+            for (int i = threadIdx.x; i < n; i += kSmallThreads) ok[i] = gk[i], ov[i] = gv[i];
+            __syncthreads();
+            tile_radix_sort<kSmallThreads>(gk, gv, n, lo_bit, nbits, ties, w[0], w[1], ok, ov, inv, tb);
+        }
+        __syncthreads();  // shared memory is reused by the next entry
     }
-    if (n < 2) return;
-    uint64_t *gk = f.keys[0] + c0;
-    uint32_t *gv = f.vals[0] + c0;
-    for (int i = threadIdx.x; i < n; i += kSmallThreads) ok[i] = gk[i], ov[i] = gv[i];
-    __syncthreads();
-    tile_radix_sort<kSmallThreads>(gk, gv, n, lo_bit, nbits, ties, w[0], w[1], ok, ov, inv, tb);
 }
 
 __device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
@@ -319,22 +386,19 @@ __device__ void merge_round(const uint64_t *sk, const uint32_t *sv, uint64_t *dk
 
 // Lists longer than kSmallPairs: their sorted kSegLen-pair chunks merged in
 // place, in shared memory up to kMergePairs pairs, else through the second
-// key/value buffer.  CTAs take work-order entries from a counter; the split
-// lists come first in that order, longest first.
+// key/value buffer.  CTAs take the split tiles from a counter: the first
+// n_long work-order entries are their first segments, longest lists first.
 __global__ void __launch_bounds__(kMergeThreads) k_merge_runs(FrameDev f) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ unsigned entry;
-    const unsigned nq = f.status->n_queue;
+    const unsigned n_long = f.status->n_long;
     for (;;) {
         if (threadIdx.x == 0) entry = atomicAdd(&f.status->sort_next, 1u);
         __syncthreads();
         const unsigned e = entry;
         __syncthreads();
-        if (e >= nq) return;
-        const uint2 q = f.order[e];
-        const uint2 ts = f.tile_seg[q.x];
-        if (ts.x < 2) return;  // unsplit lists follow all split ones: nothing left to merge
-        if (q.y != 0) continue;
+        if (e >= n_long) return;
+        const uint2 q = f.order[e];  // a split tile's first segment
         const uint2 rg = f.ranges[q.x];
         if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1)) continue;
         const int L = (int)(rg.y - rg.x);
@@ -388,9 +452,16 @@ cudaError_t launch_order(const FrameDev &f, cudaStream_t s) {
 
 cudaError_t launch_tile_sort(const FrameDev &f, int lo_bit, int nbits, bool ties, cudaStream_t s) {
     if (f.capacity == 0) return cudaSuccess;
-    // one CTA per possible work-order entry; those past the device-side count exit
+    // at most one CTA per possible work-order entry, at most as many as are
+    // resident at once; they stride over the device-side count
     const unsigned grid = (unsigned)((int64_t)f.total_tiles + f.seg_slots);
-    k_sort_small<<<grid, kSmallThreads, 0, s>>>(f, lo_bit, nbits, ties);
+    static DeviceCache small_cache;
+    const unsigned resident = device_cached(small_cache, [] {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_small, kSmallThreads, 0);
+        return sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);
+    });
+    k_sort_small<<<tmin(grid, resident), kSmallThreads, 0, s>>>(f, lo_bit, nbits, ties);
     // the shared-memory opt-in is a per-device function attribute
     static DeviceCache attr_set;
     cudaError_t e = cudaSuccess;

@@ -70,7 +70,8 @@ struct Status {
     unsigned sort_next;   // next work-order entry of the long-list sort
     unsigned fwd_exit;    // warps of the running forward launch that ran out of work
     unsigned maxw_next;   // next work item of the maximum-weight pass over split lists (reset before it)
-    unsigned pad[4];
+    unsigned n_long;      // split tiles: the first n_long work-order entries are their first segments
+    unsigned pad[3];
 };
 
 // Index checks of the SVR_DEBUG build (compiled out otherwise).  A failed

@@ -1214,8 +1214,10 @@ __device__ __forceinline__ void hit_grad(const Entry &e, const PixelRay &p, cons
         t += step;
     }
     if (B2F) {
+        // T_known >= 1e-30 here (smaller goes front to back) and T_i <= 1, so
+        // trans >= 1e-30 lies in the fast division's 2-ulp range
         T_after = T_known;
-        T_i = T_known / trans;
+        T_i = __fdividef(T_known, trans);
     } else {
         T_i = T_known;
         T_after = T_known * trans;

@@ -326,7 +326,7 @@ __device__ __forceinline__ void block_lists_entry(const FrameDev &f, const uint3
 __global__ void __launch_bounds__(kListThreads) k_block_lists(FrameDev f, const uint32_t *__restrict__ vals) {
     __shared__ uint32_t sval[kListChunk];
     __shared__ uint32_t smsk[kListChunk];
-    const unsigned nq = f.status->n_queue;
+    const unsigned nq = f.status->n_listed;  // empty lists have no block lists
     for (unsigned e = blockIdx.x; e < nq; e += gridDim.x) {
         block_lists_entry(f, vals, e, sval, smsk);
         __syncthreads();  // shared memory is reused by the next entry
@@ -451,7 +451,9 @@ __device__ __forceinline__ ItemList item_list(const FrameDev &f, int g, int blk)
     if (!SVR_IN_BOUNDS(f.debug, kDbgRange, rg.y, f.capacity + 1) || !SVR_IN_BOUNDS(f.debug, kDbgRange, rg.x, rg.y + 1))
         L.beg = L.end = 0;
     L.list = f.blist + (size_t)B * L.beg + (size_t)blk * (L.end - L.beg);
-    L.n_list = (int)f.blen[(size_t)g * B + blk];   // unsplit tiles (split ones count per segment)
+    // unsplit tiles (split ones count per segment); an empty tile's block
+    // lengths are not written (k_block_lists skips empty lists)
+    L.n_list = L.end > L.beg ? (int)f.blen[(size_t)g * B + blk] : 0;
     L.ts = f.tile_seg[g];
     if (L.ts.x <= 1 && !SVR_IN_BOUNDS(f.debug, kDbgBlockList, L.n_list, L.end - L.beg + 1)) L.n_list = 0;
     L.seg_len = f.seg_len + (size_t)L.ts.y * B + blk;
@@ -1121,7 +1123,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_render_maxw(FrameDe
     __shared__ FwdSmem smem[kWarps];
     FwdSmem &ws = smem[threadIdx.x >> 5];
     const unsigned bpt = (unsigned)f.blocks_per_tile;
-    const unsigned n_items = f.status->n_queue * bpt;
+    const unsigned n_items = f.status->n_listed * bpt;  // split tiles are among the listed
     Item it;
     while (next_item(&f.status->maxw_next, n_items, bpt, f.order, it)) {
         if (it.seg == 0) continue;
@@ -1761,7 +1763,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_render_bwd(Frame
     const int warp = threadIdx.x >> 5;
     Entry *st = stage[warp];
     const unsigned bpt = (unsigned)f.blocks_per_tile;
-    const unsigned n_items = f.status->n_queue * bpt;
+    const unsigned n_items = f.status->n_listed * bpt;  // an empty tile has no gradient
     Item it;
     while (next_item(&f.status->bwd_next, n_items, bpt, f.order, it)) {
         bwd_item<K, XM>(f, it, st, recs[warp], in);

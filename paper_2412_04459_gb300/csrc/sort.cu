@@ -30,7 +30,9 @@ namespace svr {
 // order within a group is arbitrary and results do not depend on it).  The
 // first segments of the split lists come before all other entries, so the
 // long-list merge takes its tiles from the head of the order (status n_long
-// of them).  Also resets the frame's forward-done mark (the segment sums
+// of them); the empty tiles' entries come last (status n_listed entries
+// precede them), so the kernels with nothing to do for an empty list stop
+// there.  Also resets the frame's forward-done mark (the segment sums
 // belong to the last sort) and the long-list sort's work counter.
 // Group of a list in the work order: floor(log2(length)) + 1, one more for a
 // split list, so that every split list (longer than kSegLen) precedes every
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(FrameDev f) {
             if (b == kFirstSeg) f.status->n_long = acc;
         }
         f.status->n_queue = acc;
+        f.status->n_listed = acc - cnt[0];  // group 0 (the empty lists) is last
         f.status->slots_used = slot_next;
         f.status->fwd_done = 0;
         f.status->sort_next = 0;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(FrameDev f, int lo
     __shared__ uint32_t ov[kSmallPairs];
     __shared__ RadixTables<kSmallThreads> tb;
     __shared__ uint16_t inv[kSmallPairs];
-    const unsigned nq = f.status->n_queue, G = gridDim.x;
+    const unsigned nq = f.status->n_listed, G = gridDim.x;  // empty lists need no sort
     const uint64_t mask = nbits >= 64 ? ~0ull : (1ull << nbits) - 1ull;
     // the next entry's range and the one after's order record are fetched
     // one item ahead, so that only the first item waits for them

@@ -71,7 +71,8 @@ struct Status {
     unsigned fwd_exit;    // warps of the running forward launch that ran out of work
     unsigned maxw_next;   // next work item of the maximum-weight pass over split lists (reset before it)
     unsigned n_long;      // split tiles: the first n_long work-order entries are their first segments
-    unsigned pad[3];
+    unsigned n_listed;    // work-order entries of non-empty lists (the empty tiles' entries come last)
+    unsigned pad[2];
 };
 
 // Index checks of the SVR_DEBUG build (compiled out otherwise).  A failed

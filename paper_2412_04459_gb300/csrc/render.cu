@@ -1584,6 +1584,12 @@ __device__ __forceinline__ void bwd_item(const FrameDev &f, const Item &it, Entr
     const PixelRay p = pixel_ray(cam, iv.tile, it.blk, wb);
     if (wb.smask == 0) return;
     const ItemList L = item_list(f, it.g, it.blk);
+    {
+        // a block with no entries in this item's part of the list has no hit
+        int q0 = 0, q1 = L.n_list;
+        if (L.ts.x > 1) seg_range(L, f.blocks_per_tile, it.seg, q0, q1);
+        if (q1 <= q0) return;
+    }
     const int beg = L.beg;
     const int lane = threadIdx.x & 31;
     const size_t HW = (size_t)cam.W * cam.H;
